@@ -1,0 +1,170 @@
+/*
+ * mcf.h -- C ABI of libmcf: Monte Carlo evaluation of matrix functions of a
+ * sparse graph adjacency matrix on one NVIDIA GB300 (sm_103a).
+ *
+ * The library implements the randomized method of Guidotti, Acebron and
+ * Monteiro (arXiv 2308.01037): a power series f(A') = sum_k zeta_k A'^k
+ * (Eq. power_series) of the scaled adjacency matrix A' = scale * A is
+ * estimated from random walks that sample a whole row or column of A' per
+ * step (Lemma 2, Eq. random_walk_realization), with
+ *   - f(A')v     by RandFunmAction (Algorithm 3, Section 3.4),
+ *   - f(A')1     total communicability (Eq. total_comm),
+ *   - diag f(A') subgraph centrality by RandFunmDiag (Section 3.3,
+ *                Eq. rand_funm_formula_diag),
+ *   - (I - gamma A)^{-1} 1, Katz centrality as the truncated Neumann series
+ *                (Section 4.5).
+ *
+ * Conventions shared by every entry point
+ *   - Matrices are symmetric (the paper's Section 2.1 class: undirected
+ *     graphs; a digraph enters through its symmetrisation B = [0 A; A^T 0]),
+ *     given in CSR: row_ptr int64[n+1] (row_ptr[0] = 0, non-decreasing),
+ *     col_idx int32[nnz] strictly increasing within each row, optional
+ *     values float32[nnz] (NULL = binary matrix, every entry 1).
+ *   - Pointer arguments may point to host or device memory unless stated
+ *     otherwise; the library tells them apart with cudaPointerGetAttributes.
+ *     The caller keeps ownership of every array it passes.
+ *   - Work is enqueued on params->stream (a cudaStream_t; NULL = the legacy
+ *     default stream).  A call returns once its work is enqueued when every
+ *     output is in device memory and `stats` is NULL; otherwise it waits for
+ *     the stream before returning.
+ *   - Every call returns an mcf_status; nothing aborts or throws across the
+ *     ABI.  mcf_last_error() returns a thread-local message for the last
+ *     failing call of this thread.
+ *   - Random numbers: one Philox4x32-10 block (Salmon et al., SC'11) per walk
+ *     transition, key = (seed low, seed high), counter = (step, walk id low,
+ *     walk id high, request_id).  The same seed gives the same walks on every
+ *     run and every launch configuration.
+ */
+#ifndef MCF_H
+#define MCF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mcf_graph* mcf_graph_t;
+
+typedef enum {
+    MCF_OK = 0,
+    MCF_ERR_INVALID_ARG = 1,      /* a NULL, negative or out-of-range argument */
+    MCF_ERR_INVALID_GRAPH = 2,    /* CSR not sorted / out of range / duplicate / not symmetric / non-finite */
+    MCF_ERR_OOM = 3,              /* device or host allocation failed */
+    MCF_ERR_CUDA = 4,             /* a CUDA runtime call failed; see mcf_last_error() */
+    MCF_ERR_ADMISSION = 5,        /* a request does not fit the caller's memory budget */
+    MCF_ERR_TIMEOUT = 6,          /* a bounded device-side wait gave up */
+    MCF_ERR_CANCELLED = 7,
+    MCF_ERR_ACCURACY_BUDGET = 8,
+    MCF_WARN_OVERFLOW = 9,        /* a walk weight overflowed float32; result flagged */
+    MCF_ERR_UNSUPPORTED = 10      /* a valid request this build does not implement */
+} mcf_status;
+
+/* Arithmetic of the walk (Section 3.2's weights W^(k) and the sums of
+ * Eq. rand_funm_Q):
+ *   MCF_F64          every quantity in float64;
+ *   MCF_F32W_F64ACC  W, zeta, r and the row-sum multipliers in float32
+ *                    (round to nearest, no fused multiply-add), every
+ *                    contribution widened to float64 before it is summed. */
+typedef enum { MCF_F64 = 0, MCF_F32W_F64ACC = 1 } mcf_precision;
+
+/* mcf_create_graph flags */
+#define MCF_GRAPH_DEVICE_PTRS 1u   /* row_ptr/col_idx/values are device pointers (copied device to device) */
+
+typedef struct {
+    const double* coeffs;   /* zeta_0..zeta_K of Eq. power_series (host memory), K = n_coeffs - 1;
+                               a walk makes at most K - 2 transitions                          */
+    int32_t n_coeffs;       /* 1 .. MCF_MAX_COEFFS                                              */
+    double scale;           /* A' = scale * A (the gamma of f(gamma A), Section 2.2); 0 means 1 */
+    int64_t n_walks;        /* N_s: total walks, N_i = max(1, llround(N_s p_i)) for every
+                               non-empty column i, p_i of Eq. initial_prob                      */
+    int64_t walks_per_node; /* > 0: N_i = walks_per_node for every non-empty column instead     */
+    double w_cutoff;        /* W_c of Eq. weight_cutoff (relative; W^(0) = 1); 0 = truncation only */
+    uint64_t seed;          /* Philox key                                                        */
+    uint32_t request_id;    /* fourth Philox counter word: independent streams per request       */
+    int32_t precision;      /* mcf_precision                                                     */
+    int32_t deterministic;  /* reserved, must be 0                                               */
+    void* stream;           /* cudaStream_t                                                      */
+} mcf_params;
+
+#define MCF_MAX_COEFFS 256
+
+typedef struct {
+    int64_t walks;          /* walks run (sum of N_i over the start nodes used) */
+    int64_t walk_steps;     /* transitions l_k -> l_{k+1} taken by all walks    */
+    double kernel_ms;       /* device time of the walk kernel (CUDA events)     */
+    uint32_t flags;         /* bit 0: float32 weight overflow seen              */
+} mcf_stats;
+
+/* ------------------------------------------------------------------ graphs */
+
+/* Copies the CSR of a symmetric n x n matrix to the device, validates it
+ * (sorted, in-range, duplicate-free columns; finite values; symmetric
+ * pattern and values) and precomputes its per-row sums (the row sums of
+ * Definition 1 before scaling) and, for a weighted matrix, the per-row alias
+ * tables of the transition probabilities t_ij = |a_ij| / sum_k |a_ik|
+ * (Eq. definition1).  Loops (a_ii != 0) are accepted.  n may be 0.
+ * On success *out owns device memory until mcf_destroy_graph.
+ * Errors: MCF_ERR_INVALID_ARG, MCF_ERR_INVALID_GRAPH, MCF_ERR_OOM, MCF_ERR_CUDA. */
+mcf_status mcf_create_graph(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const float* values,
+                            uint32_t flags, mcf_graph_t* out);
+
+/* Releases the graph's device memory (after synchronising the device). NULL is a no-op. */
+mcf_status mcf_destroy_graph(mcf_graph_t g);
+
+/* n, nnz, maximum degree and number of loops of the graph (any output may be NULL). */
+mcf_status mcf_graph_info(mcf_graph_t g, int64_t* n, int64_t* nnz, int64_t* max_degree, int64_t* n_loops);
+
+/* Largest eigenvalue of the symmetric matrix A (unscaled) by power iteration
+ * on A + I in float64 on the device, until the Rayleigh quotient changes by
+ * at most tol (relative) or max_iter iterations; used to set
+ * scale = 1/lambda_max (the configurations of Section 4 scale A by gamma).
+ * Cached on the graph.  Errors: MCF_ERR_INVALID_ARG, MCF_ERR_CUDA. */
+mcf_status mcf_spectral_radius(mcf_graph_t g, double tol, int32_t max_iter, double* lambda_max);
+
+/* Gershgorin bound max_i sum_k |a_ik| on the spectral radius of A (Section 4.5). */
+mcf_status mcf_gershgorin(mcf_graph_t g, double* bound);
+
+/* ------------------------------------------------------------------ solves */
+
+/* RandFunmAction (Algorithm 3): y = zeta_0 v + zeta_1 r + A' q with r = A' v
+ * and q_i the mean over the N_i walks from column i of
+ * sum_k zeta_{k+2} W^(k) r_{l_k} (Eq. rand_funm_action_formula).
+ * v, y: float64[n], host or device.  stats may be NULL.
+ * Errors: MCF_ERR_INVALID_ARG (bad params, NULL arrays), MCF_ERR_OOM, MCF_ERR_CUDA. */
+mcf_status mcf_action(mcf_graph_t g, const mcf_params* params, const double* v, double* y, mcf_stats* stats);
+
+/* Total communicability f(A')1 (Eq. total_comm): mcf_action with v = 1. */
+mcf_status mcf_total_communicability(mcf_graph_t g, const mcf_params* params, double* y, mcf_stats* stats);
+
+/* Subgraph centrality diag f(A') by RandFunmDiag (Eq. rand_funm_formula_diag):
+ * d_i = zeta_0 + zeta_1 a'_ii + sum_k a'_ik <Q_k, C'_i>, with row Q_k built
+ * from the N_k walks started at column k (Eq. rand_funm_Q).  nodes: int64
+ * indices (host or device) of the requested entries, or NULL for all n;
+ * only the columns k adjacent to a requested node are walked (Section 3.3's
+ * skip of Q_k when a_ik = 0), with the walk ids of the full run, so a subset
+ * reproduces the corresponding entries of the full result.
+ * d: float64[n_nodes] (or [n]), host or device.
+ * Errors: MCF_ERR_INVALID_ARG (node out of range), MCF_ERR_OOM, MCF_ERR_CUDA. */
+mcf_status mcf_subgraph_centrality(mcf_graph_t g, const mcf_params* params, const int64_t* nodes, int64_t n_nodes,
+                                   double* d, mcf_stats* stats);
+
+/* Katz centrality (I - gamma A)^{-1} 1 as the Neumann series sum_{k<=K} (gamma A)^k 1
+ * (Section 4.5) through RandFunmAction with zeta_k = 1 and scale = gamma;
+ * params->coeffs and params->scale are ignored.  K = 0 picks the smallest K
+ * with rho^(K+1) / (1 - rho) <= 1e-4, rho = gamma * lambda_max (computed
+ * with mcf_spectral_radius if not cached); the series needs rho < 1.
+ * Errors: MCF_ERR_INVALID_ARG (gamma <= 0, rho >= 1, K too large), as mcf_action. */
+mcf_status mcf_katz(mcf_graph_t g, double gamma, int32_t K, const mcf_params* params, double* y, mcf_stats* stats);
+
+/* Thread-local description of the last error of this thread ("" if none). */
+const char* mcf_last_error(void);
+
+/* Library version string. */
+const char* mcf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MCF_H */

@@ -1,0 +1,531 @@
+// Graph residency and preprocessing (the first step of the method's path):
+// CSR upload and validation, per-row sums of Definition 1 (unscaled), Vose
+// alias tables for weighted rows (Eq. definition1), the largest eigenvalue by
+// power iteration for scale = 1/lambda_max, the Gershgorin bound
+// (Section 4.5), and the library's shared device utilities (scan, SpMV).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "mcf_internal.cuh"
+
+namespace mcf {
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+const char* get_error() { return g_last_error.c_str(); }
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int num_sms() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return sms;
+}
+
+// ------------------------------------------------------------------ scan
+// Three-phase exclusive scan: per-block totals, a single-block scan of the
+// totals, then per-block scans offset by the scanned totals.  The partition
+// is fixed, so the result does not depend on timing.
+constexpr int SCAN_THREADS = 512;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+__device__ __forceinline__ int64_t warp_incl_scan(int64_t v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        int64_t o = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane >= d) v += o;
+    }
+    return v;
+}
+
+// Block-wide exclusive scan of one value per thread; returns the exclusive
+// prefix and writes the block total to *total.
+__device__ int64_t block_excl_scan(int64_t v, int64_t* total) {
+    __shared__ int64_t warp_tot[SCAN_THREADS / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int64_t inc = warp_incl_scan(v);
+    if (lane == 31) warp_tot[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        int64_t t = lane < SCAN_THREADS / 32 ? warp_tot[lane] : 0;
+        t = warp_incl_scan(t);
+        if (lane < SCAN_THREADS / 32) warp_tot[lane] = t;
+    }
+    __syncthreads();
+    int64_t base = wid ? warp_tot[wid - 1] : 0;
+    *total = warp_tot[SCAN_THREADS / 32 - 1];
+    __syncthreads();
+    return base + inc - v;
+}
+
+__global__ void scan_block_totals(const int64_t* __restrict__ in, int64_t n, int64_t* __restrict__ tot) {
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    int64_t s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k)
+        if (base + k < n) s += in[base + k];
+    int64_t total;
+    block_excl_scan(s, &total);
+    if (threadIdx.x == 0) tot[blockIdx.x] = total;
+}
+
+__global__ void scan_totals_single(int64_t* __restrict__ tot, int64_t nb, int64_t* __restrict__ total_out) {
+    int64_t carry = 0;
+    for (int64_t b0 = 0; b0 < nb; b0 += SCAN_THREADS) {
+        int64_t i = b0 + threadIdx.x;
+        int64_t v = i < nb ? tot[i] : 0;
+        int64_t chunk;
+        int64_t ex = block_excl_scan(v, &chunk);
+        if (i < nb) tot[i] = carry + ex;
+        carry += chunk;
+    }
+    if (threadIdx.x == 0 && total_out) *total_out = carry;
+}
+
+__global__ void scan_apply(const int64_t* __restrict__ in, int64_t* __restrict__ out, int64_t n,
+                           const int64_t* __restrict__ tot) {
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    int64_t v[SCAN_ITEMS];
+    int64_t s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        v[k] = base + k < n ? in[base + k] : 0;
+        s += v[k];
+    }
+    int64_t total;
+    int64_t ex = block_excl_scan(s, &total) + tot[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        if (base + k < n) out[base + k] = ex;
+        ex += v[k];
+    }
+}
+
+size_t scan_tmp_bytes(int64_t n) { return (size_t)((n + SCAN_TILE - 1) / SCAN_TILE + 1) * sizeof(int64_t); }
+
+mcf_status scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* total_dev, void* tmp, size_t tmp_bytes,
+                    cudaStream_t st) {
+    int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+    if (tmp_bytes < scan_tmp_bytes(n)) return fail(MCF_ERR_INVALID_ARG, "scan scratch too small");
+    int64_t* tot = static_cast<int64_t*>(tmp);
+    if (nb > 0) scan_block_totals<<<(unsigned)nb, SCAN_THREADS, 0, st>>>(in, n, tot);
+    scan_totals_single<<<1, SCAN_THREADS, 0, st>>>(tot, nb, total_dev);
+    if (nb > 0) scan_apply<<<(unsigned)nb, SCAN_THREADS, 0, st>>>(in, out, n, tot);
+    MCF_CUDA_TRY(cudaGetLastError());
+    return MCF_OK;
+}
+
+// ------------------------------------------------------------------ validation
+enum : uint32_t {
+    BAD_ROWPTR = 1u,
+    BAD_COLUMN = 2u,
+    BAD_ORDER = 4u,
+    BAD_VALUE = 8u,
+    BAD_SYMMETRY = 16u,
+};
+
+__device__ __forceinline__ int64_t find_in_row(const int32_t* __restrict__ col, int64_t b, int64_t e, int32_t key) {
+    while (b < e) {
+        int64_t m = b + ((e - b) >> 1);
+        int32_t c = col[m];
+        if (c < key) b = m + 1;
+        else e = m;
+    }
+    return b;
+}
+
+// Warp per row: checks order, range, finiteness and the symmetric partner of
+// every entry; records loops, the diagonal (zeroed beforehand) and the
+// maximum degree.
+__global__ void validate_rows(int64_t n, int64_t nnz, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                              const float* __restrict__ val, uint32_t* __restrict__ bad,
+                              unsigned long long* __restrict__ maxdeg, unsigned long long* __restrict__ loops,
+                              double* __restrict__ diag) {
+    const int lane = threadIdx.x & 31;
+    int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = warp; i < n; i += nwarps) {
+        int64_t b = rp[i], e = rp[i + 1];
+        if (b > e || b < 0 || e > nnz) {
+            if (lane == 0) atomicOr(bad, BAD_ROWPTR);
+            continue;
+        }
+        if (lane == 0) atomicMax(maxdeg, (unsigned long long)(e - b));
+        uint32_t flags = 0;
+        for (int64_t p = b + lane; p < e; p += 32) {
+            int32_t j = col[p];
+            if (j < 0 || j >= n) { flags |= BAD_COLUMN; continue; }
+            if (p > b && col[p - 1] >= j) flags |= BAD_ORDER;
+            float a = val ? val[p] : 1.0f;
+            if (!isfinite(a)) flags |= BAD_VALUE;
+            if (j == i) {
+                atomicAdd(loops, 1ull);
+                diag[i] = (double)a;
+                continue;
+            }
+            int64_t jb = rp[j], je = rp[j + 1];
+            if (jb > je || jb < 0 || je > nnz) { flags |= BAD_ROWPTR; continue; }
+            int64_t q = find_in_row(col, jb, je, (int32_t)i);
+            if (q >= je || col[q] != (int32_t)i) flags |= BAD_SYMMETRY;
+            else if (val && val[q] != a) flags |= BAD_SYMMETRY;
+        }
+        if (flags) atomicOr(bad, flags);
+    }
+}
+
+// Thread per row, in CSR order (the same order as the oracle's definition):
+// sum |a_ij|, sum a_ij^2, and Vose's alias table of t_ij = |a_ij| / sum_k |a_ik|
+// with stack work lists filled in column order.  Every product and sum is
+// rounded on its own (no contraction), so the tables are bit-reproducible.
+__global__ void weighted_rows(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                              const float* __restrict__ val, double* __restrict__ row_abs,
+                              double* __restrict__ row_sq, WEntry* __restrict__ went, double* __restrict__ s_buf,
+                              int32_t* __restrict__ small_buf, int32_t* __restrict__ large_buf) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t b = rp[i], e = rp[i + 1];
+    int64_t d = e - b;
+    double sa = 0.0, sq = 0.0;
+    for (int64_t p = b; p < e; ++p) {
+        double a = (double)val[p];
+        sa = __dadd_rn(sa, fabs(a));
+        sq = __dadd_rn(sq, __dmul_rn(a, a));
+    }
+    row_abs[i] = sa;
+    row_sq[i] = sq;
+    if (d == 0) return;
+    double* s = s_buf + b;
+    int32_t* sm = small_buf + b;
+    int32_t* lg = large_buf + b;
+    int64_t ns = 0, nl = 0;
+    for (int64_t j = 0; j < d; ++j) {
+        s[j] = __ddiv_rn(__dmul_rn((double)d, fabs((double)val[b + j])), sa);
+        if (s[j] < 1.0) sm[ns++] = (int32_t)j;
+        else lg[nl++] = (int32_t)j;
+    }
+    while (ns > 0 && nl > 0) {
+        int32_t l = sm[--ns];
+        int32_t gg = lg[--nl];
+        went[b + l].prob = __double2float_rn(s[l]);
+        went[b + l].alias = gg;
+        s[gg] = __dadd_rn(__dadd_rn(s[gg], s[l]), -1.0);
+        if (s[gg] < 1.0) sm[ns++] = gg;
+        else lg[nl++] = gg;
+    }
+    while (nl > 0) { int32_t gg = lg[--nl]; went[b + gg].prob = 1.0f; went[b + gg].alias = gg; }
+    while (ns > 0) { int32_t l = sm[--ns]; went[b + l].prob = 1.0f; went[b + l].alias = l; }
+    for (int64_t j = 0; j < d; ++j) {
+        went[b + j].col = col[b + j];
+        went[b + j].val = val[b + j];
+    }
+}
+
+// ------------------------------------------------------------------ SpMV and reductions
+// VEC lanes per row; the row loop is uniform across the warp so that every
+// lane reaches the shuffles.
+template <int VEC>
+__global__ void spmv_f64_kernel(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                const float* __restrict__ val, const double* __restrict__ x, double* __restrict__ y,
+                                double beta) {
+    constexpr int GROUPS = 32 / VEC;
+    const int lane = threadIdx.x & 31, sub = lane % VEC;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = warp * GROUPS; base < n; base += nwarps * GROUPS) {
+        const int64_t row = base + lane / VEC;
+        double s = 0.0;
+        if (row < n)
+            for (int64_t p = rp[row] + sub; p < rp[row + 1]; p += VEC) s += (val ? (double)val[p] : 1.0) * x[col[p]];
+#pragma unroll
+        for (int d = VEC / 2; d > 0; d >>= 1) s += __shfl_down_sync(0xffffffffu, s, d, VEC);
+        if (sub == 0 && row < n) y[row] = beta * s;
+    }
+}
+
+mcf_status spmv_f64(const mcf_graph* g, const double* x, double* y, double beta, cudaStream_t st) {
+    if (g->n == 0) return MCF_OK;
+    double avg = (double)g->nnz / (double)g->n;
+    int blocks = num_sms() * 8;
+    if (avg <= 4) spmv_f64_kernel<4><<<blocks, 256, 0, st>>>(g->n, g->row_ptr, g->col_idx, g->values, x, y, beta);
+    else if (avg <= 12) spmv_f64_kernel<8><<<blocks, 256, 0, st>>>(g->n, g->row_ptr, g->col_idx, g->values, x, y, beta);
+    else if (avg <= 48) spmv_f64_kernel<16><<<blocks, 256, 0, st>>>(g->n, g->row_ptr, g->col_idx, g->values, x, y, beta);
+    else spmv_f64_kernel<32><<<blocks, 256, 0, st>>>(g->n, g->row_ptr, g->col_idx, g->values, x, y, beta);
+    MCF_CUDA_TRY(cudaGetLastError());
+    return MCF_OK;
+}
+
+constexpr int RED_THREADS = 256;
+constexpr int RED_BLOCKS = 256;
+
+// Deterministic two-level reductions: fixed grid, per-block partials, then one block.
+__device__ double block_sum(double v) {
+    __shared__ double part[RED_THREADS / 32];
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < RED_THREADS / 32; ++w) s += part[w];
+    __syncthreads();
+    return s;
+}
+
+// part[b] = (x . y, (x + y) . (x + y)) over block b's grid-stride share
+__global__ void power_partials(int64_t n, const double* __restrict__ x, const double* __restrict__ y,
+                               double* __restrict__ part) {
+    double d = 0.0, q = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double xi = x[i], yi = y[i];
+        d += xi * yi;
+        double z = xi + yi;
+        q += z * z;
+    }
+    double sd = block_sum(d);
+    double sq = block_sum(q);
+    if (threadIdx.x == 0) { part[2 * blockIdx.x] = sd; part[2 * blockIdx.x + 1] = sq; }
+}
+
+__global__ void power_finish(const double* __restrict__ part, int nb, double* __restrict__ out) {
+    double d = 0.0, q = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) { d += part[2 * b]; q += part[2 * b + 1]; }
+    d = block_sum(d);
+    q = block_sum(q);
+    if (threadIdx.x == 0) { out[0] = d; out[1] = q; }
+}
+
+// x <- (x + y) / norm
+__global__ void power_update(int64_t n, double* __restrict__ x, const double* __restrict__ y,
+                             const double* __restrict__ stats) {
+    double inv = 1.0 / sqrt(stats[1]);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = (x[i] + y[i]) * inv;
+}
+
+__global__ void fill_f64(int64_t n, double* __restrict__ x, double v) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = v;
+}
+
+__global__ void max_f64(int64_t n, const double* __restrict__ x, unsigned long long* __restrict__ out) {
+    double m = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = fmax(m, x[i]);
+    // non-negative doubles order like their bit patterns
+    atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+}  // namespace mcf
+
+using namespace mcf;
+
+// ====================================================================== C ABI
+extern "C" {
+
+const char* mcf_last_error(void) { return get_error(); }
+const char* mcf_version(void) { return "mcf 0.1 (sm_103a)"; }
+
+mcf_status mcf_create_graph(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const float* values,
+                            uint32_t flags, mcf_graph_t* out) {
+    set_error("");
+    if (!out) return fail(MCF_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 0 || n > INT32_MAX) return fail(MCF_ERR_INVALID_ARG, "n must be in [0, 2^31)");
+    if (!row_ptr) return fail(MCF_ERR_INVALID_ARG, "row_ptr is NULL");
+    const bool dev_in = (flags & MCF_GRAPH_DEVICE_PTRS) != 0;
+    int64_t ends[2];
+    if (dev_in) {
+        MCF_CUDA_TRY(cudaMemcpy(&ends[0], row_ptr, sizeof(int64_t), cudaMemcpyDeviceToHost));
+        MCF_CUDA_TRY(cudaMemcpy(&ends[1], row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost));
+    } else {
+        ends[0] = row_ptr[0];
+        ends[1] = row_ptr[n];
+    }
+    if (ends[0] != 0 || ends[1] < 0) return fail(MCF_ERR_INVALID_GRAPH, "row_ptr[0] must be 0 and row_ptr[n] >= 0");
+    const int64_t nnz = ends[1];
+    if (nnz > 0 && !col_idx) return fail(MCF_ERR_INVALID_ARG, "col_idx is NULL");
+    mcf_graph* g = new (std::nothrow) mcf_graph();
+    if (!g) return fail(MCF_ERR_OOM, "host allocation failed");
+    cudaGetDevice(&g->device);
+    g->n = n;
+    g->nnz = nnz;
+    g->weighted = values != nullptr;
+    auto cleanup = [&](mcf_status s) {
+        mcf_destroy_graph(g);
+        return s;
+    };
+    const cudaMemcpyKind kind = dev_in ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (cudaMalloc(&g->row_ptr, (size_t)(n + 1) * sizeof(int64_t)) != cudaSuccess ||
+        cudaMalloc(&g->col_idx, (size_t)std::max<int64_t>(nnz, 1) * sizeof(int32_t)) != cudaSuccess ||
+        cudaMalloc(&g->diag, (size_t)std::max<int64_t>(n, 1) * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return cleanup(fail(MCF_ERR_OOM, "device allocation of the CSR failed"));
+    }
+    if (cudaMemcpy(g->row_ptr, row_ptr, (size_t)(n + 1) * sizeof(int64_t), kind) != cudaSuccess ||
+        (nnz > 0 && cudaMemcpy(g->col_idx, col_idx, (size_t)nnz * sizeof(int32_t), kind) != cudaSuccess))
+        return cleanup(fail(MCF_ERR_CUDA, std::string("CSR copy failed: ") + cudaGetErrorString(cudaGetLastError())));
+    if (g->weighted) {
+        if (cudaMalloc(&g->values, (size_t)std::max<int64_t>(nnz, 1) * sizeof(float)) != cudaSuccess) {
+            cudaGetLastError();
+            return cleanup(fail(MCF_ERR_OOM, "device allocation of the values failed"));
+        }
+        if (nnz > 0 && cudaMemcpy(g->values, values, (size_t)nnz * sizeof(float), kind) != cudaSuccess)
+            return cleanup(fail(MCF_ERR_CUDA, "values copy failed"));
+    }
+    // validation
+    struct Flags { uint32_t bad; uint32_t pad; unsigned long long maxdeg; unsigned long long loops; };
+    Flags* dflags = nullptr;
+    if (cudaMalloc(&dflags, sizeof(Flags)) != cudaSuccess) { cudaGetLastError(); return cleanup(fail(MCF_ERR_OOM, "alloc")); }
+    cudaMemset(dflags, 0, sizeof(Flags));
+    cudaMemset(g->diag, 0, (size_t)std::max<int64_t>(n, 1) * sizeof(double));
+    if (n > 0) {
+        int blocks = (int)std::min<int64_t>((n + 7) / 8, (int64_t)num_sms() * 16);
+        validate_rows<<<blocks, 256>>>(n, nnz, g->row_ptr, g->col_idx, g->values, &dflags->bad, &dflags->maxdeg,
+                                       &dflags->loops, g->diag);
+    }
+    Flags hf;
+    cudaError_t e = cudaMemcpy(&hf, dflags, sizeof(Flags), cudaMemcpyDeviceToHost);
+    cudaFree(dflags);
+    if (e != cudaSuccess) return cleanup(fail(MCF_ERR_CUDA, std::string("validation: ") + cudaGetErrorString(e)));
+    if (hf.bad) {
+        std::string why;
+        if (hf.bad & BAD_ROWPTR) why += " row_ptr not non-decreasing within [0, nnz];";
+        if (hf.bad & BAD_COLUMN) why += " column index out of range;";
+        if (hf.bad & BAD_ORDER) why += " columns not strictly increasing within a row (unsorted or duplicate);";
+        if (hf.bad & BAD_VALUE) why += " non-finite value;";
+        if (hf.bad & BAD_SYMMETRY) why += " matrix not symmetric;";
+        return cleanup(fail(MCF_ERR_INVALID_GRAPH, "invalid graph:" + why));
+    }
+    g->max_degree = (int64_t)hf.maxdeg;
+    g->n_loops = (int64_t)hf.loops;
+    g->gershgorin = (double)g->max_degree;
+    if (g->weighted && n > 0) {
+        double* s_buf = nullptr;
+        int32_t *sm = nullptr, *lg = nullptr;
+        size_t m = (size_t)std::max<int64_t>(nnz, 1);
+        if (cudaMalloc(&g->row_abs, (size_t)n * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&g->row_sq, (size_t)n * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&g->went, m * sizeof(WEntry)) != cudaSuccess || cudaMalloc(&s_buf, m * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&sm, m * sizeof(int32_t)) != cudaSuccess || cudaMalloc(&lg, m * sizeof(int32_t)) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(s_buf); cudaFree(sm); cudaFree(lg);
+            return cleanup(fail(MCF_ERR_OOM, "device allocation of the alias tables failed"));
+        }
+        weighted_rows<<<(unsigned)((n + 127) / 128), 128>>>(n, g->row_ptr, g->col_idx, g->values, g->row_abs, g->row_sq,
+                                                             g->went, s_buf, sm, lg);
+        unsigned long long* dm = nullptr;
+        cudaMalloc(&dm, sizeof(unsigned long long));
+        cudaMemset(dm, 0, sizeof(unsigned long long));
+        max_f64<<<num_sms(), 256>>>(n, g->row_abs, dm);
+        unsigned long long hm = 0;
+        e = cudaMemcpy(&hm, dm, sizeof(hm), cudaMemcpyDeviceToHost);
+        cudaFree(dm); cudaFree(s_buf); cudaFree(sm); cudaFree(lg);
+        if (e != cudaSuccess) return cleanup(fail(MCF_ERR_CUDA, std::string("alias tables: ") + cudaGetErrorString(e)));
+        double gm;
+        memcpy(&gm, &hm, sizeof(gm));
+        g->gershgorin = gm;
+    }
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cleanup(fail(MCF_ERR_CUDA, std::string("create_graph: ") + cudaGetErrorString(e)));
+    *out = g;
+    return MCF_OK;
+}
+
+mcf_status mcf_destroy_graph(mcf_graph_t g) {
+    if (!g) return MCF_OK;
+    cudaDeviceSynchronize();
+    cudaFree(g->row_ptr);
+    cudaFree(g->col_idx);
+    cudaFree(g->values);
+    cudaFree(g->row_abs);
+    cudaFree(g->row_sq);
+    cudaFree(g->diag);
+    cudaFree(g->went);
+    delete g;
+    return MCF_OK;
+}
+
+mcf_status mcf_graph_info(mcf_graph_t g, int64_t* n, int64_t* nnz, int64_t* max_degree, int64_t* n_loops) {
+    if (!g) return fail(MCF_ERR_INVALID_ARG, "graph is NULL");
+    if (n) *n = g->n;
+    if (nnz) *nnz = g->nnz;
+    if (max_degree) *max_degree = g->max_degree;
+    if (n_loops) *n_loops = g->n_loops;
+    return MCF_OK;
+}
+
+mcf_status mcf_gershgorin(mcf_graph_t g, double* bound) {
+    if (!g || !bound) return fail(MCF_ERR_INVALID_ARG, "NULL argument");
+    *bound = g->gershgorin;
+    return MCF_OK;
+}
+
+mcf_status mcf_spectral_radius(mcf_graph_t g, double tol, int32_t max_iter, double* lambda_max) {
+    set_error("");
+    if (!g || !lambda_max) return fail(MCF_ERR_INVALID_ARG, "NULL argument");
+    if (!(tol > 0.0) || max_iter < 1) return fail(MCF_ERR_INVALID_ARG, "tol must be > 0 and max_iter >= 1");
+    if (g->n == 0 || g->nnz == 0) {
+        *lambda_max = 0.0;
+        g->lambda_max = 0.0;
+        return MCF_OK;
+    }
+    cudaStream_t st = 0;
+    double *x = nullptr, *y = nullptr, *part = nullptr, *hst = nullptr;
+    const int64_t n = g->n;
+    if (cudaMalloc(&x, n * sizeof(double)) != cudaSuccess || cudaMalloc(&y, n * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&part, (2 * RED_BLOCKS + 2) * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&hst, 2 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(x); cudaFree(y); cudaFree(part); cudaFreeHost(hst);
+        return fail(MCF_ERR_OOM, "power iteration scratch");
+    }
+    mcf_status rc = MCF_OK;
+    fill_f64<<<num_sms() * 4, 256, 0, st>>>(n, x, 1.0 / sqrt((double)n));
+    double lam = 0.0, prev = 0.0;
+    for (int it = 0; it < max_iter; ++it) {
+        rc = spmv_f64(g, x, y, 1.0, st);
+        if (rc != MCF_OK) break;
+        power_partials<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, x, y, part);
+        power_finish<<<1, RED_THREADS, 0, st>>>(part, RED_BLOCKS, part + 2 * RED_BLOCKS);
+        power_update<<<num_sms() * 4, 256, 0, st>>>(n, x, y, part + 2 * RED_BLOCKS);
+        if (cudaMemcpy(hst, part + 2 * RED_BLOCKS, 2 * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            rc = fail(MCF_ERR_CUDA, std::string("power iteration: ") + cudaGetErrorString(cudaGetLastError()));
+            break;
+        }
+        lam = hst[0];   // Rayleigh quotient x^T A x with ||x|| = 1
+        if (it > 0 && fabs(lam - prev) <= tol * fabs(lam)) break;
+        prev = lam;
+    }
+    cudaFree(x); cudaFree(y); cudaFree(part); cudaFreeHost(hst);
+    if (rc != MCF_OK) return rc;
+    g->lambda_max = lam;
+    *lambda_max = lam;
+    return MCF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,922 @@
+// The sampling path of the method: per-solve preparation of the Markov chain
+// (Definition 1), walk allocation, the walk kernels of RandFunmAction
+// (Algorithm 3) and RandFunmDiag (Section 3.3), and their epilogues.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <string>
+#include <type_traits>
+
+#include "mcf_internal.cuh"
+
+namespace mcf {
+
+// ====================================================================== RNG
+// Philox4x32-10 (Salmon, Moraes, Dror and Shaw, SC'11): ten rounds of two
+// 32x32 -> 64-bit products by 0xD2511F53 and 0xCD9E8D57; between rounds the
+// key is advanced by the Weyl constants 0x9E3779B9 and 0xBB67AE85.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+// ====================================================================== node records
+// What one walk step reads about the state l it leaves: CSR offset, degree,
+// r_l (the contracted row <R_l, v>, Section 3.4) and the weight multiplier
+// sum_j |a'_lj| (Eq. weights: a/t = sign(a) * row sum).  One 16-byte (float)
+// or 32-byte (double) load per step.
+template <bool F64>
+struct Rec;
+template <>
+struct __align__(16) Rec<false> {
+    uint32_t off;
+    uint32_t deg;
+    float r;
+    float mult;
+};
+template <>
+struct __align__(16) Rec<true> {
+    int64_t off;
+    uint32_t deg;
+    uint32_t pad;
+    double r;
+    double mult;
+};
+
+constexpr int RED_BLOCKS = 256;
+constexpr int RED_THREADS = 256;
+constexpr int WARP_CHUNK = 32;      // walks per chunk (one per lane)
+constexpr int CHUNKS_PER_GRAB = 4;  // chunks a warp takes per atomic
+
+enum Counter { C_NEXT = 0, C_STEPS = 1, C_WALKS = 2, C_FLAGS = 3, C_TOTAL = 4, C_STARTS = 5, N_COUNTERS = 8 };
+
+__device__ double block_sum_d(double v) {
+    __shared__ double part[32];
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += part[w];
+    __syncthreads();
+    return s;
+}
+
+// r = A' v evaluated as gamma * sum_j (a_ij v_j), the sum in CSR order with
+// every product and sum rounded on its own (thread per row); v == nullptr
+// means v = 1, where a binary row gives gamma * deg exactly.
+__global__ void r_kernel(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                         const float* __restrict__ val, const double* __restrict__ v, double gamma,
+                         double* __restrict__ r) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t b = rp[i], e = rp[i + 1];
+    double s;
+    if (!val && !v) {
+        s = (double)(e - b);
+    } else {
+        s = 0.0;
+        for (int64_t p = b; p < e; ++p) {
+            const double a = val ? (double)val[p] : 1.0;
+            const double x = v ? v[col[p]] : 1.0;
+            s = __dadd_rn(s, __dmul_rn(a, x));
+        }
+    }
+    r[i] = __dmul_rn(gamma, s);
+}
+
+// colnorm_i = ||C'_i||_2 (Eq. initial_prob; symmetric A: column = row) and
+// fixed-partition partial sums of it.
+__global__ void colnorm_kernel(int64_t n, const int64_t* __restrict__ rp, const double* __restrict__ row_sq,
+                               double gamma, double* __restrict__ colnorm, double* __restrict__ part) {
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double sq = row_sq ? row_sq[i] : (double)(rp[i + 1] - rp[i]);
+        const double c = __dmul_rn(gamma, sqrt(sq));
+        colnorm[i] = c;
+        s += c;
+    }
+    s = block_sum_d(s);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void sum_partials(const double* __restrict__ part, int nb, double* __restrict__ out) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) s += part[b];
+    s = block_sum_d(s);
+    if (threadIdx.x == 0) *out = s;
+}
+
+// N_i of Definition 1: 0 for an empty column, walks_per_node when given, else
+// max(1, llround(N_s * (||C_i|| / sum_k ||C_k||))).  flag_i marks the start
+// nodes this solve walks from.
+__global__ void alloc_kernel(int64_t n, const double* __restrict__ colnorm, const double* __restrict__ tot,
+                             int64_t n_walks, int64_t wpn, const uint8_t* __restrict__ need, int64_t* __restrict__ nw,
+                             int64_t* __restrict__ flag) {
+    const double T = *tot;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double c = colnorm[i];
+        int64_t w = 0;
+        if (c > 0.0) {
+            if (wpn > 0) w = wpn;
+            else {
+                const long long q = llround(__dmul_rn((double)n_walks, __ddiv_rn(c, T)));
+                w = q < 1 ? 1 : (int64_t)q;
+            }
+        }
+        nw[i] = w;
+        flag[i] = (w > 0 && (!need || need[i])) ? 1 : 0;
+    }
+}
+
+// Compacts the start nodes: starts[s] = i, soff[s] = first walk id of i.
+__global__ void compact_starts(int64_t n, const int64_t* __restrict__ flag, const int64_t* __restrict__ spos,
+                               const int64_t* __restrict__ woff, int32_t* __restrict__ starts,
+                               int64_t* __restrict__ soff, const unsigned long long* __restrict__ counters) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (flag[i]) {
+            starts[spos[i]] = (int32_t)i;
+            soff[spos[i]] = woff[i];
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) soff[counters[C_STARTS]] = (int64_t)counters[C_TOTAL];
+}
+
+// chunk_s0[c] = index s of the start whose walk range holds walk 32c.
+__global__ void chunk_table(const int64_t* __restrict__ soff, const unsigned long long* __restrict__ counters,
+                            uint32_t* __restrict__ chunk_s0) {
+    const int64_t S = (int64_t)counters[C_STARTS];
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < S; s += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c0 = (soff[s] + WARP_CHUNK - 1) / WARP_CHUNK;
+        const int64_t c1 = (soff[s + 1] + WARP_CHUNK - 1) / WARP_CHUNK;
+        for (int64_t c = c0; c < c1; ++c) chunk_s0[c] = (uint32_t)s;
+    }
+}
+
+template <bool F64>
+__global__ void build_records(int64_t n, const int64_t* __restrict__ rp, const double* __restrict__ row_abs,
+                              double gamma, const double* __restrict__ r, Rec<F64>* __restrict__ rec) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = rp[i];
+        const int64_t d = rp[i + 1] - b;
+        const double mult = __dmul_rn(gamma, row_abs ? row_abs[i] : (double)d);
+        Rec<F64> x;
+        if constexpr (F64) {
+            x.off = b;
+            x.deg = (uint32_t)d;
+            x.pad = 0;
+            x.r = r[i];
+            x.mult = mult;
+        } else {
+            x.off = (uint32_t)b;
+            x.deg = (uint32_t)d;
+            x.r = __double2float_rn(r[i]);
+            x.mult = __double2float_rn(mult);
+        }
+        rec[i] = x;
+    }
+}
+
+// SelectNextState (Section 3.1) for the state whose record is x: position
+// within the row from the Philox block u; returns the next state and the
+// signed multiplier sign(a_{l l'}) * sum_j |a'_lj|.
+template <bool F64, bool WEIGHTED>
+__device__ __forceinline__ uint32_t next_state(const Rec<F64>& x, uint4 u, const int32_t* __restrict__ col,
+                                               const WEntry* __restrict__ went,
+                                               typename std::conditional<F64, double, float>::type& mult) {
+    const uint32_t b = __umulhi(u.x, x.deg);
+    mult = x.mult;
+    if constexpr (!WEIGHTED) {
+        return (uint32_t)__ldg(col + (int64_t)x.off + b);
+    } else {
+        const float xr = __fmul_rn(__uint2float_rn(u.y >> 8), 5.9604644775390625e-08f);
+        WEntry e = went[(int64_t)x.off + b];
+        if (!(xr < e.prob)) e = went[(int64_t)x.off + e.alias];
+        if (e.val < 0.0f) mult = -mult;
+        return (uint32_t)e.col;
+    }
+}
+
+// ====================================================================== RandFunmAction walks
+// Persistent kernel.  A warp takes CHUNKS_PER_GRAB chunks of 32 consecutive
+// walk ids at a time; lane t runs walk 32c + t.  Walks of one start node are
+// contiguous, so lanes sharing a start combine their sums with a segmented
+// warp reduction and issue one float64 atomic per (chunk, start).
+template <bool F64, bool WEIGHTED>
+__global__ void __launch_bounds__(256) walk_action_kernel(
+    const Rec<F64>* __restrict__ rec, const int32_t* __restrict__ col, const WEntry* __restrict__ went,
+    const int32_t* __restrict__ starts, const int64_t* __restrict__ soff, const uint32_t* __restrict__ chunk_s0,
+    const double* __restrict__ zeta_g, int K, double wc, uint2 key, uint32_t req, double* __restrict__ acc,
+    unsigned long long* __restrict__ counters) {
+    using real = typename std::conditional<F64, double, float>::type;
+    __shared__ real zeta[MCF_MAX_COEFFS];
+    for (int k = threadIdx.x; k <= K; k += blockDim.x) zeta[k] = (real)zeta_g[k];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t n_total = (int64_t)counters[C_TOTAL];
+    const int64_t S = (int64_t)counters[C_STARTS];
+    const int64_t n_chunks = (n_total + WARP_CHUNK - 1) / WARP_CHUNK;
+    unsigned long long my_steps = 0, my_walks = 0;
+    uint32_t flags = 0;
+    for (;;) {
+        int64_t c0 = 0;
+        if (lane == 0) c0 = (int64_t)atomicAdd(&counters[C_NEXT], (unsigned long long)CHUNKS_PER_GRAB) ;
+        c0 = __shfl_sync(0xffffffffu, c0, 0);
+        if (c0 >= n_chunks) break;
+        const int64_t c1 = min(c0 + CHUNKS_PER_GRAB, n_chunks);
+        for (int64_t c = c0; c < c1; ++c) {
+            const int64_t g = c * WARP_CHUNK + lane;
+            const bool active = g < n_total;
+            // which start holds walk g: count the start boundaries <= g in the
+            // window of 32 starts beginning at the chunk's first start
+            const int64_t s0 = chunk_s0[c];
+            const int64_t bnd = (s0 + 1 + lane <= S) ? soff[s0 + 1 + lane] : INT64_MAX;
+            int cnt = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int64_t bv = __shfl_sync(0xffffffffu, bnd, cnt + step - 1);
+                if (bv <= g) cnt += step;
+            }
+            const int64_t sidx = active ? s0 + cnt : -1;
+            double sum = 0.0;
+            if (active) {
+                uint32_t l = (uint32_t)starts[sidx];
+                real W = (real)1;
+                const uint32_t glo = (uint32_t)g, ghi = (uint32_t)((uint64_t)g >> 32);
+                for (int k = 0; k <= K; ++k) {
+                    if (!((double)fabs(W) > wc)) break;  // Eq. weight_cutoff, W^(0) = 1
+                    const uint4 u = philox4x32_10(make_uint4((uint32_t)k, glo, ghi, req), key);
+                    const Rec<F64> x = rec[l];
+                    if constexpr (F64) sum += __dmul_rn(__dmul_rn(zeta[k + 2], W), x.r);
+                    else sum += (double)__fmul_rn(__fmul_rn(zeta[k + 2], W), x.r);
+                    if (k + 2 >= K || x.deg == 0) break;
+                    real mult;
+                    const uint32_t nl = next_state<F64, WEIGHTED>(x, u, col, went, mult);
+                    if constexpr (F64) W = __dmul_rn(W, mult);
+                    else W = __fmul_rn(W, mult);
+                    l = nl;
+                    ++my_steps;
+                }
+                if constexpr (!F64) if (!isfinite(W) || !isfinite(sum)) flags |= 1u;
+                ++my_walks;
+            }
+            // segmented suffix sums over lanes with equal sidx (contiguous runs)
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const double o = __shfl_down_sync(0xffffffffu, sum, d);
+                const int64_t os = __shfl_down_sync(0xffffffffu, sidx, d);
+                if (lane + d < 32 && os == sidx) sum += o;
+            }
+            const int64_t prev = __shfl_up_sync(0xffffffffu, sidx, 1);
+            if (active && (lane == 0 || prev != sidx)) atomicAdd(&acc[starts[sidx]], sum);
+        }
+    }
+    // per-warp totals
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        my_steps += __shfl_down_sync(0xffffffffu, my_steps, d);
+        my_walks += __shfl_down_sync(0xffffffffu, my_walks, d);
+        flags |= __shfl_down_sync(0xffffffffu, flags, d);
+    }
+    if (lane == 0) {
+        atomicAdd(&counters[C_STEPS], my_steps);
+        atomicAdd(&counters[C_WALKS], my_walks);
+        if (flags) atomicOr(&counters[C_FLAGS], (unsigned long long)flags);
+    }
+}
+
+// q_i = acc_i / N_i (Eq. rand_funm_action_formula, the 1/N_i factor of W^(0)).
+__global__ void finalize_q(int64_t n, double* __restrict__ acc, const int64_t* __restrict__ nw) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        acc[i] = nw[i] > 0 ? acc[i] / (double)nw[i] : 0.0;
+}
+
+// y = zeta_0 v + zeta_1 r + A' q (Algorithm 3, last step); VEC lanes per row,
+// the row loop uniform across the warp so every lane reaches the shuffles.
+template <int VEC>
+__global__ void action_epilogue(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                const float* __restrict__ val, double gamma, double z0, double z1,
+                                const double* __restrict__ v, const double* __restrict__ r,
+                                const double* __restrict__ q, double* __restrict__ y) {
+    constexpr int GROUPS = 32 / VEC;
+    const int lane = threadIdx.x & 31, sub = lane % VEC;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = warp * GROUPS; base < n; base += nwarps * GROUPS) {
+        const int64_t row = base + lane / VEC;
+        double s = 0.0;
+        if (row < n)
+            for (int64_t p = rp[row] + sub; p < rp[row + 1]; p += VEC) s += (val ? (double)val[p] : 1.0) * q[col[p]];
+#pragma unroll
+        for (int d = VEC / 2; d > 0; d >>= 1) s += __shfl_down_sync(0xffffffffu, s, d, VEC);
+        if (sub == 0 && row < n) y[row] = z0 * (v ? v[row] : 1.0) + z1 * r[row] + gamma * s;
+    }
+}
+
+// ====================================================================== RandFunmDiag walks
+// One CTA per start column k at a time (taken from an atomic counter).  Its
+// threads run the N_k walks and add zeta_{m+2} W^(m) into row Q_k held in
+// shared memory (a dense array when n is small, else an open-addressing hash
+// keyed by node id).  Then d_i += a'_ik <Q_k, C'_i> / N_k for every neighbour
+// i of k (warp per neighbour, float64 atomics).  A hash that reaches its fill
+// limit stops the inserting walk; the CTA applies and clears Q_k, and the walk
+// is replayed from its first unrecorded visit (walks are deterministic in
+// their Philox counters, and Q_k enters d linearly).
+struct DiagTable {
+    double* val;
+    int32_t* key;
+    int32_t cap_log2;
+    int32_t limit;
+    int* count;
+};
+
+__device__ __forceinline__ uint32_t hash_slot(uint32_t x, int cap_log2) {
+    return (x * 0x9E3779B1u) >> (32 - cap_log2);
+}
+
+template <bool DENSE>
+__device__ __forceinline__ bool q_add(const DiagTable& t, uint32_t l, double v) {
+    if constexpr (DENSE) {
+        atomicAdd(&t.val[l], v);
+        return true;
+    } else {
+        const uint32_t mask = (1u << t.cap_log2) - 1u;
+        uint32_t h = hash_slot(l, t.cap_log2);
+        for (uint32_t probe = 0; probe <= mask; ++probe, h = (h + 1) & mask) {
+            int32_t k = t.key[h];
+            if (k == (int32_t)l) {
+                atomicAdd(&t.val[h], v);
+                return true;
+            }
+            if (k == -1) {
+                if (*(volatile int*)t.count >= t.limit) return false;
+                const int32_t prev = atomicCAS(&t.key[h], -1, (int32_t)l);
+                if (prev == -1) atomicAdd(t.count, 1);
+                if (prev == -1 || prev == (int32_t)l) {
+                    atomicAdd(&t.val[h], v);
+                    return true;
+                }
+            }
+        }
+        return false;
+    }
+}
+
+template <bool DENSE>
+__device__ __forceinline__ double q_get(const DiagTable& t, uint32_t l) {
+    if constexpr (DENSE) {
+        return t.val[l];
+    } else {
+        const uint32_t mask = (1u << t.cap_log2) - 1u;
+        uint32_t h = hash_slot(l, t.cap_log2);
+        for (uint32_t probe = 0; probe <= mask; ++probe, h = (h + 1) & mask) {
+            const int32_t k = t.key[h];
+            if (k == (int32_t)l) return t.val[h];
+            if (k == -1) return 0.0;
+        }
+        return 0.0;
+    }
+}
+
+// Runs walk g from column k, recording the visits of steps >= from.  Returns
+// -1 when the walk is complete, else the step whose visit could not be stored.
+template <bool F64, bool WEIGHTED, bool DENSE>
+__device__ int diag_walk(const DiagTable& t, uint32_t k0, int64_t g, int from, const Rec<F64>* __restrict__ rec,
+                         const int32_t* __restrict__ col, const WEntry* __restrict__ went,
+                         const typename std::conditional<F64, double, float>::type* zeta, int K, double wc,
+                         uint2 key, uint32_t req, unsigned long long& steps, uint32_t& flags) {
+    using real = typename std::conditional<F64, double, float>::type;
+    uint32_t l = k0;
+    real W = (real)1;
+    const uint32_t glo = (uint32_t)g, ghi = (uint32_t)((uint64_t)g >> 32);
+    for (int k = 0; k <= K; ++k) {
+        if (!((double)fabs(W) > wc)) break;
+        const uint4 u = philox4x32_10(make_uint4((uint32_t)k, glo, ghi, req), key);
+        const Rec<F64> x = rec[l];
+        if (k >= from) {
+            double term;
+            if constexpr (F64) term = __dmul_rn(zeta[k + 2], W);
+            else term = (double)__fmul_rn(zeta[k + 2], W);
+            if (!q_add<DENSE>(t, l, term)) return k;
+        }
+        if (k + 2 >= K || x.deg == 0) break;
+        real mult;
+        const uint32_t nl = next_state<F64, WEIGHTED>(x, u, col, went, mult);
+        if constexpr (F64) W = __dmul_rn(W, mult);
+        else W = __fmul_rn(W, mult);
+        l = nl;
+        if (k >= from) ++steps;
+    }
+    if constexpr (!F64) if (!isfinite(W)) flags |= 1u;
+    return -1;
+}
+
+template <bool F64, bool WEIGHTED, bool DENSE>
+__global__ void __launch_bounds__(256) walk_diag_kernel(
+    const Rec<F64>* __restrict__ rec, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+    const float* __restrict__ val, const WEntry* __restrict__ went, const int32_t* __restrict__ starts,
+    const int64_t* __restrict__ woff, const int64_t* __restrict__ nw, const uint8_t* __restrict__ want, double gamma,
+    const double* __restrict__ zeta_g, int K, double wc, uint2 key, uint32_t req, int64_t n, int cap_log2,
+    double* __restrict__ dacc, unsigned long long* __restrict__ counters) {
+    using real = typename std::conditional<F64, double, float>::type;
+    extern __shared__ double smem_d[];
+    __shared__ real zeta[MCF_MAX_COEFFS];
+    __shared__ int64_t cur;
+    __shared__ int count;
+    for (int k = threadIdx.x; k <= K; k += blockDim.x) zeta[k] = (real)zeta_g[k];
+    DiagTable t;
+    const int cap = DENSE ? (int)n : (1 << cap_log2);
+    t.val = smem_d;
+    t.key = reinterpret_cast<int32_t*>(smem_d + cap);
+    t.cap_log2 = cap_log2;
+    t.limit = DENSE ? cap : (cap - cap / 4 - (int)blockDim.x);
+    t.count = &count;
+    for (int i = threadIdx.x; i < cap; i += blockDim.x) {
+        t.val[i] = 0.0;
+        if (!DENSE) t.key[i] = -1;
+    }
+    if (threadIdx.x == 0) count = 0;
+    const int64_t S = (int64_t)counters[C_STARTS];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    unsigned long long steps = 0, walks = 0;
+    uint32_t flags = 0;
+    __syncthreads();
+    for (;;) {
+        if (threadIdx.x == 0) cur = (int64_t)atomicAdd(&counters[C_NEXT], 1ull);
+        __syncthreads();
+        const int64_t s = cur;
+        if (s >= S) break;
+        const uint32_t k0 = (uint32_t)starts[s];
+        const int64_t Nk = nw[k0];
+        const int64_t g0 = woff[k0];
+        for (int64_t w0 = 0; w0 < Nk; w0 += blockDim.x) {
+            const int64_t w = w0 + threadIdx.x;
+            bool pending = w < Nk;
+            int from = 0;
+            if (pending) ++walks;
+            for (;;) {
+                if (pending) {
+                    const int f = diag_walk<F64, WEIGHTED, DENSE>(t, k0, g0 + w, from, rec, col, went, zeta, K, wc,
+                                                                  key, req, steps, flags);
+                    if (f < 0) pending = false;
+                    else from = f;
+                }
+                if (!__syncthreads_or(pending)) break;
+                // table full: apply the partial row Q_k, clear it, resume
+                for (int64_t p = rp[k0] + wid; p < rp[k0 + 1]; p += nwarp) {
+                    const int32_t i = col[p];
+                    if (want && !want[i]) continue;
+                    double dot = 0.0;
+                    for (int64_t q = rp[i] + lane; q < rp[i + 1]; q += 32)
+                        dot += __dmul_rn(gamma * (val ? (double)val[q] : 1.0), q_get<DENSE>(t, (uint32_t)col[q]));
+#pragma unroll
+                    for (int d = 16; d > 0; d >>= 1) dot += __shfl_down_sync(0xffffffffu, dot, d);
+                    if (lane == 0) atomicAdd(&dacc[i], (gamma * (val ? (double)val[p] : 1.0) * dot) / (double)Nk);
+                }
+                __syncthreads();
+                for (int i = threadIdx.x; i < cap; i += blockDim.x) {
+                    t.val[i] = 0.0;
+                    if (!DENSE) t.key[i] = -1;
+                }
+                if (threadIdx.x == 0) count = 0;
+                __syncthreads();
+            }
+        }
+        __syncthreads();
+        // d_i += a'_ik <Q_k, C'_i> / N_k for the neighbours i of k
+        for (int64_t p = rp[k0] + wid; p < rp[k0 + 1]; p += nwarp) {
+            const int32_t i = col[p];
+            if (want && !want[i]) continue;
+            double dot = 0.0;
+            for (int64_t q = rp[i] + lane; q < rp[i + 1]; q += 32)
+                dot += __dmul_rn(gamma * (val ? (double)val[q] : 1.0), q_get<DENSE>(t, (uint32_t)col[q]));
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) dot += __shfl_down_sync(0xffffffffu, dot, d);
+            if (lane == 0) atomicAdd(&dacc[i], (gamma * (val ? (double)val[p] : 1.0) * dot) / (double)Nk);
+        }
+        __syncthreads();
+        if (DENSE) {
+            // clear only what this start touched: the visited nodes are the
+            // rows read above plus k itself; a full clear is cheap for small n
+            for (int i = threadIdx.x; i < cap; i += blockDim.x) t.val[i] = 0.0;
+        } else {
+            for (int i = threadIdx.x; i < cap; i += blockDim.x) {
+                t.val[i] = 0.0;
+                t.key[i] = -1;
+            }
+        }
+        if (threadIdx.x == 0) count = 0;
+        __syncthreads();
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        steps += __shfl_down_sync(0xffffffffu, steps, d);
+        walks += __shfl_down_sync(0xffffffffu, walks, d);
+        flags |= __shfl_down_sync(0xffffffffu, flags, d);
+    }
+    if (lane == 0) {
+        atomicAdd(&counters[C_STEPS], steps);
+        atomicAdd(&counters[C_WALKS], walks);
+        if (flags) atomicOr(&counters[C_FLAGS], (unsigned long long)flags);
+    }
+}
+
+// need[j] = 1 for every column j adjacent to a requested node; want[i] = 1 for requested nodes.
+__global__ void mark_nodes(int64_t m, const int64_t* __restrict__ nodes, const int64_t* __restrict__ rp,
+                           const int32_t* __restrict__ col, uint8_t* __restrict__ need, uint8_t* __restrict__ want) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = nodes[t];
+        want[i] = 1;
+        for (int64_t p = rp[i]; p < rp[i + 1]; ++p) need[col[p]] = 1;
+    }
+}
+
+__global__ void check_nodes(int64_t m, const int64_t* __restrict__ nodes, int64_t n,
+                            unsigned long long* __restrict__ counters) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x)
+        if (nodes[t] < 0 || nodes[t] >= n) atomicOr(&counters[C_FLAGS], 2ull);
+}
+
+// d_t = zeta_0 + zeta_1 a'_ii + (sum_k a'_ik <Q_k, C'_i>) for i = nodes[t] (or t).
+__global__ void diag_finish(int64_t m, const int64_t* __restrict__ nodes, const double* __restrict__ dacc,
+                            const double* __restrict__ diag, double gamma, double z0, double z1, int K,
+                            double* __restrict__ d) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = nodes ? nodes[t] : t;
+        double v = z0;
+        if (K >= 1) v += z1 * (gamma * diag[i]);
+        d[t] = v + dacc[i];
+    }
+}
+
+// ====================================================================== host side
+static mcf_status check_params(const mcf_graph* g, const mcf_params* p) {
+    if (!g) return fail(MCF_ERR_INVALID_ARG, "graph is NULL");
+    if (!p) return fail(MCF_ERR_INVALID_ARG, "params is NULL");
+    if (!p->coeffs || p->n_coeffs < 1 || p->n_coeffs > MCF_MAX_COEFFS)
+        return fail(MCF_ERR_INVALID_ARG, "coeffs must hold 1.." + std::to_string(MCF_MAX_COEFFS) + " values");
+    if (p->n_walks < 0 || p->walks_per_node < 0) return fail(MCF_ERR_INVALID_ARG, "walk counts must be >= 0");
+    if (p->n_coeffs > 2 && p->n_walks == 0 && p->walks_per_node == 0)
+        return fail(MCF_ERR_INVALID_ARG, "n_walks or walks_per_node must be > 0");
+    if (!(p->w_cutoff >= 0.0)) return fail(MCF_ERR_INVALID_ARG, "w_cutoff must be >= 0");
+    if (p->precision != MCF_F64 && p->precision != MCF_F32W_F64ACC)
+        return fail(MCF_ERR_INVALID_ARG, "unknown precision");
+    if (p->deterministic != 0) return fail(MCF_ERR_INVALID_ARG, "deterministic is reserved and must be 0");
+    if (!(p->scale >= 0.0) || !isfinite(p->scale)) return fail(MCF_ERR_INVALID_ARG, "scale must be finite and >= 0");
+    for (int k = 0; k < p->n_coeffs; ++k)
+        if (!isfinite(p->coeffs[k])) return fail(MCF_ERR_INVALID_ARG, "coefficients must be finite");
+    if (p->precision == MCF_F32W_F64ACC && g->nnz >= ((int64_t)1 << 32))
+        return fail(MCF_ERR_UNSUPPORTED, "float32 walk records need nnz < 2^32");
+    return MCF_OK;
+}
+
+static int grid_for(int64_t work, int threads) {
+    int64_t b = (work + threads - 1) / threads;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)num_sms() * 32));
+}
+
+template <class KernelT>
+static int persistent_grid(KernelT kernel, int threads, size_t smem) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+    if (per_sm < 1) per_sm = 1;
+    return per_sm * num_sms();
+}
+
+// Everything a solve prepares before its walks: r, the chain's allocation,
+// the compacted start list and the per-node records.
+struct Prep {
+    double* r = nullptr;
+    double* colnorm = nullptr;
+    double* part = nullptr;
+    int64_t* nw = nullptr;
+    int64_t* flag = nullptr;
+    int64_t* woff = nullptr;
+    int64_t* spos = nullptr;
+    int32_t* starts = nullptr;
+    int64_t* soff = nullptr;
+    unsigned long long* counters = nullptr;
+    void* rec = nullptr;
+    double* zeta = nullptr;
+    void* scan_tmp = nullptr;
+    size_t scan_bytes = 0;
+};
+
+static mcf_status prepare(const mcf_graph* g, const mcf_params* p, double gamma, const double* v_dev,
+                          const uint8_t* need, Scratch& sc, Prep& P, cudaStream_t st) {
+    const int64_t n = g->n;
+    const bool f64 = p->precision == MCF_F64;
+    MCF_TRY(sc.get(&P.r, n));
+    MCF_TRY(sc.get(&P.colnorm, n));
+    MCF_TRY(sc.get(&P.part, RED_BLOCKS + 1));
+    MCF_TRY(sc.get(&P.nw, n));
+    MCF_TRY(sc.get(&P.flag, n));
+    MCF_TRY(sc.get(&P.woff, n));
+    MCF_TRY(sc.get(&P.spos, n));
+    MCF_TRY(sc.get(&P.starts, n));
+    MCF_TRY(sc.get(&P.soff, n + 1));
+    MCF_TRY(sc.get(&P.counters, N_COUNTERS));
+    MCF_TRY(sc.get(&P.zeta, MCF_MAX_COEFFS));
+    P.scan_bytes = scan_tmp_bytes(n);
+    MCF_TRY(sc.get((char**)&P.scan_tmp, P.scan_bytes));
+    if (f64) MCF_TRY(sc.get((Rec<true>**)&P.rec, n));
+    else MCF_TRY(sc.get((Rec<false>**)&P.rec, n));
+    MCF_CUDA_TRY(cudaMemsetAsync(P.counters, 0, N_COUNTERS * sizeof(unsigned long long), st));
+    MCF_CUDA_TRY(cudaMemcpyAsync(P.zeta, p->coeffs, p->n_coeffs * sizeof(double), cudaMemcpyHostToDevice, st));
+    if (n == 0) return MCF_OK;
+    r_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, g->row_ptr, g->col_idx, g->values, v_dev, gamma, P.r);
+    colnorm_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, g->row_ptr, g->row_sq, gamma, P.colnorm, P.part);
+    sum_partials<<<1, RED_THREADS, 0, st>>>(P.part, RED_BLOCKS, P.part + RED_BLOCKS);
+    alloc_kernel<<<grid_for(n, 256), 256, 0, st>>>(n, P.colnorm, P.part + RED_BLOCKS, p->n_walks, p->walks_per_node,
+                                                   need, P.nw, P.flag);
+    MCF_TRY(scan_i64(P.nw, P.woff, n, (int64_t*)&P.counters[C_TOTAL], P.scan_tmp, P.scan_bytes, st));
+    MCF_TRY(scan_i64(P.flag, P.spos, n, (int64_t*)&P.counters[C_STARTS], P.scan_tmp, P.scan_bytes, st));
+    compact_starts<<<grid_for(n, 256), 256, 0, st>>>(n, P.flag, P.spos, P.woff, P.starts, P.soff, P.counters);
+    if (f64)
+        build_records<true><<<grid_for(n, 256), 256, 0, st>>>(n, g->row_ptr, g->row_abs, gamma, P.r, (Rec<true>*)P.rec);
+    else
+        build_records<false><<<grid_for(n, 256), 256, 0, st>>>(n, g->row_ptr, g->row_abs, gamma, P.r,
+                                                               (Rec<false>*)P.rec);
+    MCF_CUDA_TRY(cudaGetLastError());
+    return MCF_OK;
+}
+
+// Keeps freed stream-ordered scratch in the device's default pool instead of
+// returning it to the driver at every synchronisation.
+static void keep_pool_memory() {
+    static bool done[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || done[dev]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+    done[dev] = true;
+}
+
+static uint2 philox_key(uint64_t seed) { return make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)); }
+
+static mcf_status finish_stats(mcf_stats* stats, const unsigned long long* counters, cudaEvent_t e0, cudaEvent_t e1,
+                               cudaStream_t st) {
+    if (!stats) return MCF_OK;
+    unsigned long long h[N_COUNTERS];
+    MCF_CUDA_TRY(cudaMemcpyAsync(h, counters, sizeof(h), cudaMemcpyDeviceToHost, st));
+    MCF_CUDA_TRY(cudaStreamSynchronize(st));
+    stats->walks = (int64_t)h[C_WALKS];
+    stats->walk_steps = (int64_t)h[C_STEPS];
+    stats->flags = (uint32_t)h[C_FLAGS];
+    float ms = 0.f;
+    if (e0 && e1) cudaEventElapsedTime(&ms, e0, e1);
+    stats->kernel_ms = ms;
+    return MCF_OK;
+}
+
+template <bool F64, bool WEIGHTED>
+static void launch_action_walks(const mcf_graph* g, const Prep& P, uint32_t* chunk_s0, int K, double wc, uint2 key,
+                                uint32_t req, double* acc, cudaStream_t st) {
+    auto kern = walk_action_kernel<F64, WEIGHTED>;
+    const int grid = persistent_grid(kern, 256, 0);
+    kern<<<grid, 256, 0, st>>>((const Rec<F64>*)P.rec, g->col_idx, g->went, P.starts, P.soff, chunk_s0, P.zeta, K,
+                               wc, key, req, acc, P.counters);
+}
+
+static mcf_status solve_action(mcf_graph* g, const mcf_params* p, const double* v, double* y, mcf_stats* stats,
+                               bool ones) {
+    set_error("");
+    MCF_TRY(check_params(g, p));
+    if (!y) return fail(MCF_ERR_INVALID_ARG, "y is NULL");
+    if (!ones && !v) return fail(MCF_ERR_INVALID_ARG, "v is NULL");
+    cudaStream_t st = (cudaStream_t)p->stream;
+    const int64_t n = g->n;
+    const double gamma = p->scale == 0.0 ? 1.0 : p->scale;
+    const int K = p->n_coeffs - 1;
+    const bool f64 = p->precision == MCF_F64;
+    keep_pool_memory();
+    Scratch sc(st);
+    const double* v_dev = nullptr;
+    if (!ones) {
+        if (is_device_ptr(v)) v_dev = v;
+        else {
+            double* vd;
+            MCF_TRY(sc.get(&vd, n));
+            MCF_CUDA_TRY(cudaMemcpyAsync(vd, v, n * sizeof(double), cudaMemcpyHostToDevice, st));
+            v_dev = vd;
+        }
+    }
+    const bool y_on_dev = is_device_ptr(y);
+    double* y_dev = y;
+    if (!y_on_dev) MCF_TRY(sc.get(&y_dev, n));
+    Prep P;
+    MCF_TRY(prepare(g, p, gamma, v_dev, nullptr, sc, P, st));
+    double* acc;
+    MCF_TRY(sc.get(&acc, n));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (n > 0) {
+        MCF_CUDA_TRY(cudaMemsetAsync(acc, 0, n * sizeof(double), st));
+        if (K >= 2) {
+            // walk ids are bounded by N_s + n (rounding) or walks_per_node * n
+            const int64_t max_walks = p->walks_per_node > 0 ? p->walks_per_node * n : p->n_walks + n;
+            const int64_t max_chunks = max_walks / WARP_CHUNK + 2;
+            uint32_t* chunk_s0;
+            MCF_TRY(sc.get(&chunk_s0, max_chunks));
+            chunk_table<<<grid_for(n, 256), 256, 0, st>>>(P.soff, P.counters, chunk_s0);
+            if (stats) {
+                cudaEventCreate(&e0);
+                cudaEventCreate(&e1);
+                cudaEventRecord(e0, st);
+            }
+            const uint2 key = philox_key(p->seed);
+            if (f64 && g->weighted) launch_action_walks<true, true>(g, P, chunk_s0, K, p->w_cutoff, key, p->request_id, acc, st);
+            else if (f64) launch_action_walks<true, false>(g, P, chunk_s0, K, p->w_cutoff, key, p->request_id, acc, st);
+            else if (g->weighted) launch_action_walks<false, true>(g, P, chunk_s0, K, p->w_cutoff, key, p->request_id, acc, st);
+            else launch_action_walks<false, false>(g, P, chunk_s0, K, p->w_cutoff, key, p->request_id, acc, st);
+            if (stats) cudaEventRecord(e1, st);
+        }
+        finalize_q<<<grid_for(n, 256), 256, 0, st>>>(n, acc, P.nw);
+        const double avg = (double)g->nnz / (double)n;
+        const double z0 = p->coeffs[0], z1 = K >= 1 ? p->coeffs[1] : 0.0;
+        const int blocks = num_sms() * 8;
+        if (avg <= 6)
+            action_epilogue<4><<<blocks, 256, 0, st>>>(n, g->row_ptr, g->col_idx, g->values, gamma, z0, z1, v_dev, P.r, acc, y_dev);
+        else if (avg <= 24)
+            action_epilogue<8><<<blocks, 256, 0, st>>>(n, g->row_ptr, g->col_idx, g->values, gamma, z0, z1, v_dev, P.r, acc, y_dev);
+        else
+            action_epilogue<32><<<blocks, 256, 0, st>>>(n, g->row_ptr, g->col_idx, g->values, gamma, z0, z1, v_dev, P.r, acc, y_dev);
+        MCF_CUDA_TRY(cudaGetLastError());
+    }
+    if (!y_on_dev && n > 0) MCF_CUDA_TRY(cudaMemcpyAsync(y, y_dev, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    mcf_status rc = finish_stats(stats, P.counters, e0, e1, st);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (rc != MCF_OK) return rc;
+    if (!y_on_dev) MCF_CUDA_TRY(cudaStreamSynchronize(st));
+    return MCF_OK;
+}
+
+constexpr int DIAG_THREADS = 256;
+constexpr int DIAG_HASH_LOG2 = 13;                       // 8192 slots = 96 KB of shared memory
+constexpr int64_t DIAG_DENSE_MAX = 12288;                // dense row Q_k up to 96 KB
+
+template <bool F64, bool WEIGHTED, bool DENSE>
+static mcf_status launch_diag(const mcf_graph* g, const Prep& P, const uint8_t* want, double gamma, int K, double wc,
+                              uint2 key, uint32_t req, double* dacc, cudaStream_t st) {
+    auto kern = walk_diag_kernel<F64, WEIGHTED, DENSE>;
+    const int cap = DENSE ? (int)g->n : (1 << DIAG_HASH_LOG2);
+    const size_t smem = (size_t)cap * (DENSE ? sizeof(double) : sizeof(double) + sizeof(int32_t));
+    MCF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int grid = persistent_grid(kern, DIAG_THREADS, smem);
+    kern<<<grid, DIAG_THREADS, smem, st>>>((const Rec<F64>*)P.rec, g->row_ptr, g->col_idx, g->values, g->went,
+                                           P.starts, P.woff, P.nw, want, gamma, P.zeta, K, wc, key, req, g->n,
+                                           DIAG_HASH_LOG2, dacc, P.counters);
+    MCF_CUDA_TRY(cudaGetLastError());
+    return MCF_OK;
+}
+
+static mcf_status solve_diag(mcf_graph* g, const mcf_params* p, const int64_t* nodes, int64_t n_nodes, double* d,
+                             mcf_stats* stats) {
+    set_error("");
+    MCF_TRY(check_params(g, p));
+    if (!d) return fail(MCF_ERR_INVALID_ARG, "d is NULL");
+    if (nodes && n_nodes < 0) return fail(MCF_ERR_INVALID_ARG, "n_nodes must be >= 0");
+    cudaStream_t st = (cudaStream_t)p->stream;
+    const int64_t n = g->n;
+    const int64_t m = nodes ? n_nodes : n;
+    const double gamma = p->scale == 0.0 ? 1.0 : p->scale;
+    const int K = p->n_coeffs - 1;
+    const bool f64 = p->precision == MCF_F64;
+    keep_pool_memory();
+    Scratch sc(st);
+    const int64_t* nodes_dev = nullptr;
+    uint8_t *need = nullptr, *want = nullptr;
+    if (nodes && m > 0) {
+        if (is_device_ptr(nodes)) nodes_dev = nodes;
+        else {
+            for (int64_t t = 0; t < m; ++t)
+                if (nodes[t] < 0 || nodes[t] >= n) return fail(MCF_ERR_INVALID_ARG, "node index out of range");
+            int64_t* nd;
+            MCF_TRY(sc.get(&nd, m));
+            MCF_CUDA_TRY(cudaMemcpyAsync(nd, nodes, m * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+            nodes_dev = nd;
+        }
+        MCF_TRY(sc.get(&need, n));
+        MCF_TRY(sc.get(&want, n));
+        MCF_CUDA_TRY(cudaMemsetAsync(need, 0, n, st));
+        MCF_CUDA_TRY(cudaMemsetAsync(want, 0, n, st));
+    }
+    const bool d_on_dev = is_device_ptr(d);
+    double* d_dev = d;
+    if (!d_on_dev) MCF_TRY(sc.get(&d_dev, m));
+    if (nodes && m == 0) return MCF_OK;
+    if (nodes_dev && is_device_ptr(nodes)) {
+        // device-resident indices are checked on the device before use
+        unsigned long long* chk;
+        MCF_TRY(sc.get(&chk, N_COUNTERS));
+        MCF_CUDA_TRY(cudaMemsetAsync(chk, 0, N_COUNTERS * sizeof(unsigned long long), st));
+        check_nodes<<<grid_for(m, 256), 256, 0, st>>>(m, nodes_dev, n, chk);
+        unsigned long long h = 0;
+        MCF_CUDA_TRY(cudaMemcpyAsync(&h, &chk[C_FLAGS], sizeof(h), cudaMemcpyDeviceToHost, st));
+        MCF_CUDA_TRY(cudaStreamSynchronize(st));
+        if (h & 2ull) return fail(MCF_ERR_INVALID_ARG, "node index out of range");
+    }
+    if (nodes_dev) mark_nodes<<<grid_for(m, 256), 256, 0, st>>>(m, nodes_dev, g->row_ptr, g->col_idx, need, want);
+    Prep P;
+    MCF_TRY(prepare(g, p, gamma, nullptr, need, sc, P, st));
+    double* dacc;
+    MCF_TRY(sc.get(&dacc, n));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (n > 0) {
+        MCF_CUDA_TRY(cudaMemsetAsync(dacc, 0, n * sizeof(double), st));
+        if (K >= 2) {
+            if (stats) {
+                cudaEventCreate(&e0);
+                cudaEventCreate(&e1);
+                cudaEventRecord(e0, st);
+            }
+            const uint2 key = philox_key(p->seed);
+            const bool dense = n <= DIAG_DENSE_MAX;
+            mcf_status rc;
+#define MCF_DIAG(F, W, D) rc = launch_diag<F, W, D>(g, P, want, gamma, K, p->w_cutoff, key, p->request_id, dacc, st)
+            if (f64) {
+                if (g->weighted) { if (dense) MCF_DIAG(true, true, true); else MCF_DIAG(true, true, false); }
+                else { if (dense) MCF_DIAG(true, false, true); else MCF_DIAG(true, false, false); }
+            } else {
+                if (g->weighted) { if (dense) MCF_DIAG(false, true, true); else MCF_DIAG(false, true, false); }
+                else { if (dense) MCF_DIAG(false, false, true); else MCF_DIAG(false, false, false); }
+            }
+#undef MCF_DIAG
+            if (rc != MCF_OK) return rc;
+            if (stats) cudaEventRecord(e1, st);
+        }
+        const double z0 = p->coeffs[0], z1 = K >= 1 ? p->coeffs[1] : 0.0;
+        diag_finish<<<grid_for(m, 256), 256, 0, st>>>(m, nodes_dev, dacc, g->diag, gamma, z0, z1, K, d_dev);
+        MCF_CUDA_TRY(cudaGetLastError());
+    }
+    if (!d_on_dev && m > 0) MCF_CUDA_TRY(cudaMemcpyAsync(d, d_dev, m * sizeof(double), cudaMemcpyDeviceToHost, st));
+    mcf_status rc = finish_stats(stats, P.counters, e0, e1, st);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (rc != MCF_OK) return rc;
+    if (!d_on_dev) MCF_CUDA_TRY(cudaStreamSynchronize(st));
+    return MCF_OK;
+}
+
+}  // namespace mcf
+
+using namespace mcf;
+
+extern "C" {
+
+mcf_status mcf_action(mcf_graph_t g, const mcf_params* params, const double* v, double* y, mcf_stats* stats) {
+    return solve_action(g, params, v, y, stats, false);
+}
+
+mcf_status mcf_total_communicability(mcf_graph_t g, const mcf_params* params, double* y, mcf_stats* stats) {
+    return solve_action(g, params, nullptr, y, stats, true);
+}
+
+mcf_status mcf_subgraph_centrality(mcf_graph_t g, const mcf_params* params, const int64_t* nodes, int64_t n_nodes,
+                                   double* d, mcf_stats* stats) {
+    return solve_diag(g, params, nodes, n_nodes, d, stats);
+}
+
+mcf_status mcf_katz(mcf_graph_t g, double gamma, int32_t K, const mcf_params* params, double* y, mcf_stats* stats) {
+    set_error("");
+    if (!g || !params) return fail(MCF_ERR_INVALID_ARG, "NULL argument");
+    if (!(gamma > 0.0) || !isfinite(gamma)) return fail(MCF_ERR_INVALID_ARG, "gamma must be > 0");
+    if (K < 0 || K + 1 > MCF_MAX_COEFFS) return fail(MCF_ERR_INVALID_ARG, "K out of range");
+    if (K == 0) {
+        if (g->lambda_max <= 0.0 && g->nnz > 0) {
+            double lam;
+            MCF_TRY(mcf_spectral_radius(g, 1e-10, 100000, &lam));
+        }
+        const double rho = gamma * g->lambda_max;
+        if (!(rho < 1.0)) return fail(MCF_ERR_INVALID_ARG, "the Neumann series needs gamma * lambda_max < 1");
+        if (rho <= 0.0) K = 2;
+        else K = std::max(2, (int)ceil(log(1e-4 * (1.0 - rho)) / log(rho) - 1.0));
+        if (K + 1 > MCF_MAX_COEFFS) return fail(MCF_ERR_INVALID_ARG, "rho too close to 1 for the coefficient limit");
+    }
+    double ones[MCF_MAX_COEFFS];
+    for (int k = 0; k <= K; ++k) ones[k] = 1.0;
+    mcf_params p = *params;
+    p.coeffs = ones;
+    p.n_coeffs = K + 1;
+    p.scale = gamma;
+    return solve_action(g, &p, nullptr, y, stats, true);
+}
+
+}  // extern "C"

@@ -1,0 +1,255 @@
+"""Thin ctypes binding of libmcf (``include/mcf.h``): argument marshalling only.
+
+The functions carry the C entry points' names.  Arrays may be numpy arrays
+(host memory) or torch tensors (host or CUDA memory); every computation runs
+in the library's CUDA kernels.  Importing this module does not load the
+library; the first call does, and raises if ``libmcf.so`` has not been built
+(``__graft_entry__.build()`` or ``python paper_2308_01037_gb300/build.py``).
+There is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+MCF_OK = 0
+MCF_F64 = 0
+MCF_F32W_F64ACC = 1
+MCF_GRAPH_DEVICE_PTRS = 1
+MCF_MAX_COEFFS = 256
+
+STATUS_NAMES = {
+    0: "MCF_OK", 1: "MCF_ERR_INVALID_ARG", 2: "MCF_ERR_INVALID_GRAPH", 3: "MCF_ERR_OOM", 4: "MCF_ERR_CUDA",
+    5: "MCF_ERR_ADMISSION", 6: "MCF_ERR_TIMEOUT", 7: "MCF_ERR_CANCELLED", 8: "MCF_ERR_ACCURACY_BUDGET",
+    9: "MCF_WARN_OVERFLOW", 10: "MCF_ERR_UNSUPPORTED",
+}
+
+
+class McfError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class mcf_params(ctypes.Structure):
+    _fields_ = [("coeffs", ctypes.c_void_p), ("n_coeffs", ctypes.c_int32), ("scale", ctypes.c_double),
+                ("n_walks", ctypes.c_int64), ("walks_per_node", ctypes.c_int64), ("w_cutoff", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("request_id", ctypes.c_uint32), ("precision", ctypes.c_int32),
+                ("deterministic", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+
+
+class mcf_stats(ctypes.Structure):
+    _fields_ = [("walks", ctypes.c_int64), ("walk_steps", ctypes.c_int64), ("kernel_ms", ctypes.c_double),
+                ("flags", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {"walks": self.walks, "walk_steps": self.walk_steps, "kernel_ms": self.kernel_ms, "flags": self.flags}
+
+
+# Every entry point declared in include/mcf.h, with its ctypes signature.
+_P, _I64, _I32, _U32, _D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32, ctypes.c_double
+SIGNATURES = {
+    "mcf_create_graph": ([_I64, _P, _P, _P, _U32, _P], ctypes.c_int),
+    "mcf_destroy_graph": ([_P], ctypes.c_int),
+    "mcf_graph_info": ([_P, _P, _P, _P, _P], ctypes.c_int),
+    "mcf_spectral_radius": ([_P, _D, _I32, _P], ctypes.c_int),
+    "mcf_gershgorin": ([_P, _P], ctypes.c_int),
+    "mcf_action": ([_P, _P, _P, _P, _P], ctypes.c_int),
+    "mcf_total_communicability": ([_P, _P, _P, _P], ctypes.c_int),
+    "mcf_subgraph_centrality": ([_P, _P, _P, _I64, _P, _P], ctypes.c_int),
+    "mcf_katz": ([_P, _D, _I32, _P, _P, _P], ctypes.c_int),
+    "mcf_last_error": ([], ctypes.c_char_p),
+    "mcf_version": ([], ctypes.c_char_p),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Loads libmcf.so (must already be built) and declares its prototypes."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = library_path()
+            if not os.path.exists(path):
+                raise RuntimeError(f"libmcf.so is not built ({path}); run __graft_entry__.build()")
+            lib = ctypes.CDLL(path)
+            for name, (args, res) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = lib
+    return _lib
+
+
+def _check(status: int):
+    if status != MCF_OK:
+        raise McfError(status, (load().mcf_last_error() or b"").decode())
+
+
+# ---------------------------------------------------------------- marshalling helpers
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x, dtype):
+    """(pointer, keep-alive object) of a numpy array or torch tensor in the given dtype."""
+    if x is None:
+        return None, None
+    if _is_torch(x):
+        import torch
+
+        tdt = {np.int64: torch.int64, np.int32: torch.int32, np.float32: torch.float32,
+               np.float64: torch.float64}[dtype]
+        if x.dtype != tdt or not x.is_contiguous():
+            x = x.to(tdt).contiguous()
+        return x.data_ptr(), x
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return a.ctypes.data, a
+
+
+def _stream_of(*arrays):
+    for a in arrays:
+        if a is not None and _is_torch(a) and a.is_cuda:
+            import torch
+
+            return torch.cuda.current_stream(a.device).cuda_stream
+    return None
+
+
+def _params(coeffs, scale=0.0, n_walks=0, walks_per_node=0, w_cutoff=0.0, seed=0, request_id=0,
+            precision=MCF_F32W_F64ACC, stream=None):
+    c = np.ascontiguousarray(coeffs, dtype=np.float64)
+    p = mcf_params(c.ctypes.data, len(c), float(scale), int(n_walks), int(walks_per_node), float(w_cutoff),
+                   int(seed) & 0xFFFFFFFFFFFFFFFF, int(request_id) & 0xFFFFFFFF, int(precision), 0,
+                   stream if stream else None)
+    return p, c
+
+
+class GraphHandle:
+    """Owns an mcf_graph_t; released by mcf_destroy_graph when collected or closed."""
+
+    def __init__(self, handle: int, n: int, nnz: int):
+        self.handle = handle
+        self.n = n
+        self.nnz = nnz
+
+    def close(self):
+        if self.handle:
+            load().mcf_destroy_graph(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- entry points
+def mcf_create_graph(n, row_ptr, col_idx, values=None) -> GraphHandle:
+    """Uploads a symmetric CSR matrix (numpy or torch; device tensors copied device to device)."""
+    lib = load()
+    rp, krp = _ptr(row_ptr, np.int64)
+    ci, kci = _ptr(col_idx if len(col_idx) else np.zeros(1, np.int32), np.int32)
+    va, kva = _ptr(values, np.float32)
+    dev = 1 if (_is_torch(row_ptr) and row_ptr.is_cuda) else 0
+    h = ctypes.c_void_p()
+    _check(lib.mcf_create_graph(int(n), rp, ci, va, MCF_GRAPH_DEVICE_PTRS if dev else 0, ctypes.byref(h)))
+    nnz = int(krp[-1])
+    return GraphHandle(h.value, int(n), nnz)
+
+
+def mcf_destroy_graph(g: GraphHandle):
+    g.close()
+
+
+def mcf_graph_info(g: GraphHandle) -> dict:
+    vals = [ctypes.c_int64() for _ in range(4)]
+    _check(load().mcf_graph_info(g.handle, *[ctypes.byref(v) for v in vals]))
+    return dict(zip(("n", "nnz", "max_degree", "n_loops"), (v.value for v in vals)))
+
+
+def mcf_spectral_radius(g: GraphHandle, tol=1e-10, max_iter=10000) -> float:
+    out = ctypes.c_double()
+    _check(load().mcf_spectral_radius(g.handle, float(tol), int(max_iter), ctypes.byref(out)))
+    return out.value
+
+
+def mcf_gershgorin(g: GraphHandle) -> float:
+    out = ctypes.c_double()
+    _check(load().mcf_gershgorin(g.handle, ctypes.byref(out)))
+    return out.value
+
+
+def _output(out, m, like):
+    if out is not None:
+        return out
+    if like is not None and _is_torch(like) and like.is_cuda:
+        import torch
+
+        return torch.empty(max(m, 0), dtype=torch.float64, device=like.device)
+    return np.zeros(max(m, 0), dtype=np.float64)
+
+
+def mcf_action(g: GraphHandle, v, coeffs, out=None, device_out=None, stats=False, **kw):
+    """f(A')v by RandFunmAction; keyword arguments fill mcf_params."""
+    y = _output(out, g.n, device_out if device_out is not None else v)
+    vp, kv = _ptr(v, np.float64)
+    yp, ky = _ptr(y, np.float64)
+    st = mcf_stats()
+    p, kc = _params(coeffs, stream=kw.pop("stream", None) or _stream_of(v, y), **kw)
+    _check(load().mcf_action(g.handle, ctypes.byref(p), vp, yp, ctypes.byref(st) if stats else None))
+    return (y, st.as_dict()) if stats else y
+
+
+def mcf_total_communicability(g: GraphHandle, coeffs, out=None, device_out=None, stats=False, **kw):
+    """f(A')1 (total communicability)."""
+    y = _output(out, g.n, device_out)
+    yp, ky = _ptr(y, np.float64)
+    st = mcf_stats()
+    p, kc = _params(coeffs, stream=kw.pop("stream", None) or _stream_of(y), **kw)
+    _check(load().mcf_total_communicability(g.handle, ctypes.byref(p), yp, ctypes.byref(st) if stats else None))
+    return (y, st.as_dict()) if stats else y
+
+
+def mcf_subgraph_centrality(g: GraphHandle, coeffs, nodes=None, out=None, device_out=None, stats=False, **kw):
+    """diag f(A') by RandFunmDiag, all nodes or ``nodes``."""
+    m = g.n if nodes is None else len(nodes)
+    d = _output(out, m, device_out if device_out is not None else nodes)
+    npt, kn = _ptr(nodes, np.int64)
+    dp, kd = _ptr(d, np.float64)
+    st = mcf_stats()
+    p, kc = _params(coeffs, stream=kw.pop("stream", None) or _stream_of(nodes, d), **kw)
+    _check(load().mcf_subgraph_centrality(g.handle, ctypes.byref(p), npt, int(m), dp,
+                                          ctypes.byref(st) if stats else None))
+    return (d, st.as_dict()) if stats else d
+
+
+def mcf_katz(g: GraphHandle, gamma, K=0, out=None, device_out=None, stats=False, **kw):
+    """(I - gamma A)^{-1} 1 as the truncated Neumann series (K = 0: from the tail bound)."""
+    y = _output(out, g.n, device_out)
+    yp, ky = _ptr(y, np.float64)
+    st = mcf_stats()
+    p, kc = _params([1.0], stream=kw.pop("stream", None) or _stream_of(y), **kw)
+    _check(load().mcf_katz(g.handle, float(gamma), int(K), ctypes.byref(p), yp,
+                           ctypes.byref(st) if stats else None))
+    return (y, st.as_dict()) if stats else y
+
+
+def mcf_last_error() -> str:
+    return (load().mcf_last_error() or b"").decode()
+
+
+def mcf_version() -> str:
+    return (load().mcf_version() or b"").decode()
