@@ -158,6 +158,37 @@ mcf_status mcf_subgraph_centrality(mcf_graph_t g, const mcf_params* params, cons
  * Errors: MCF_ERR_INVALID_ARG (gamma <= 0, rho >= 1, K too large), as mcf_action. */
 mcf_status mcf_katz(mcf_graph_t g, double gamma, int32_t K, const mcf_params* params, double* y, mcf_stats* stats);
 
+/* ---------------------------------------------------------- allocation-free */
+
+/* Size limits of mcf_total_communicability_noalloc (its fixed scratch array). */
+#define MCF_NOALLOC_MAX_NODES (1LL << 17)
+#define MCF_NOALLOC_MAX_WALKS (1LL << 25)
+
+/* Total communicability f(A')1 for callers that cannot allocate device
+ * memory -- for example code running inside a memory pool or a framework that
+ * owns every device allocation, a pre-captured CUDA graph, or a process whose
+ * allocator is already exhausted.  The paper has no counterpart: this is the
+ * same computation as mcf_total_communicability (same walks, same result),
+ * but the library allocates nothing.  Its scratch is one file-scope device
+ * array of about 17 MB that every GPU loading libmcf holds until the process
+ * exits; the caller passes inputs and output:
+ *   n, nnz           matrix size, n <= MCF_NOALLOC_MAX_NODES, nnz < 2^32;
+ *   row_ptr, col_idx device pointers to a binary symmetric CSR (int64[n+1],
+ *                    int32[nnz]); range and order are checked on the device
+ *                    (MCF_ERR_INVALID_GRAPH), symmetry is the caller's duty;
+ *   params           as for mcf_total_communicability; the walk count (N_s + n,
+ *                    or walks_per_node * n) must not exceed MCF_NOALLOC_MAX_WALKS;
+ *   y                device pointer to float64[n].
+ * Sizes beyond the limits return MCF_ERR_INVALID_ARG with the limit in
+ * mcf_last_error().  The first call on a device looks up the array's device
+ * address (with that device current), so make it before any stream capture.
+ * Every call uses the same array and clears what must start at zero; calls
+ * that overlap on the GPU (other streams, other threads) race on it and must
+ * be serialised by the caller.  The call returns after its work is enqueued
+ * on params->stream (after one short synchronisation for the CSR check). */
+mcf_status mcf_total_communicability_noalloc(int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
+                                             const mcf_params* params, double* y);
+
 /* Thread-local description of the last error of this thread ("" if none). */
 const char* mcf_last_error(void);
 

@@ -875,6 +875,183 @@ static mcf_status solve_diag(mcf_graph* g, const mcf_params* p, const int64_t* n
     return MCF_OK;
 }
 
+// ====================================================================== allocation-free entry
+// mcf_total_communicability_noalloc runs the same kernels as
+// mcf_total_communicability, but every scratch buffer is carved from one
+// file-scope device array of fixed size instead of being allocated, for
+// callers that cannot allocate device memory.  Every GPU that loads the
+// library holds this array until the process exits.
+constexpr int64_t NOALLOC_MAX_NODES = MCF_NOALLOC_MAX_NODES;
+constexpr int64_t NOALLOC_MAX_WALKS = MCF_NOALLOC_MAX_WALKS;
+
+constexpr size_t na_align(size_t b) { return (b + 255) & ~(size_t)255; }
+constexpr size_t NOALLOC_BYTES =
+    na_align(8 * NOALLOC_MAX_NODES) * 7 +                      // r, colnorm, nw, flag, woff, spos, acc
+    na_align(4 * NOALLOC_MAX_NODES) +                          // starts
+    na_align(8 * (NOALLOC_MAX_NODES + 1)) +                    // soff
+    na_align(sizeof(Rec<true>) * NOALLOC_MAX_NODES) +          // node records (largest variant)
+    na_align(4 * (NOALLOC_MAX_WALKS / WARP_CHUNK + 2)) +       // chunk table
+    na_align(8 * ((NOALLOC_MAX_NODES + 4095) / 4096 + 1)) +    // scan block totals
+    na_align(8 * (RED_BLOCKS + 1)) + na_align(8 * N_COUNTERS) + na_align(8 * MCF_MAX_COEFFS) +
+    na_align(8 * 4);                                           // partials, counters, coefficients, check flags
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+// Device address of g_noalloc_scratch, looked up once per device (the host
+// symbol is only a stand-in and must never be handed to a kernel).
+static void* g_noalloc_base[64] = {};
+
+static mcf_status noalloc_base(void** out) {
+    int dev = 0;
+    MCF_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(MCF_ERR_UNSUPPORTED, "device ordinal above 63");
+    if (!g_noalloc_base[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(MCF_ERR_CUDA, std::string("cudaGetSymbolAddress(g_noalloc_scratch): ") + cudaGetErrorString(e));
+        g_noalloc_base[dev] = p;
+    }
+    *out = g_noalloc_base[dev];
+    return MCF_OK;
+}
+
+struct Carve {
+    char* p;
+    template <class T>
+    T* take(size_t count) {
+        T* r = reinterpret_cast<T*>(p);
+        p += na_align(count * sizeof(T));
+        return r;
+    }
+};
+
+// Memory-safety checks of a caller's device CSR (the walks index with these
+// values): row_ptr[0] = 0, row_ptr[n] = nnz, rows non-decreasing inside
+// [0, nnz], columns in [0, n) and strictly increasing within a row.
+__global__ void noalloc_check_csr(int64_t n, int64_t nnz, const int64_t* __restrict__ rp,
+                                  const int32_t* __restrict__ col, unsigned long long* __restrict__ bad) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = rp[i], e = rp[i + 1];
+        if ((i == 0 && b != 0) || (i == n - 1 && e != nnz) || b < 0 || b > e || e > nnz) {
+            atomicOr(bad, 1ull);
+            continue;
+        }
+        for (int64_t p = b; p < e; ++p) {
+            const int32_t j = col[p];
+            if (j < 0 || j >= n || (p > b && col[p - 1] >= j)) {
+                atomicOr(bad, 2ull);
+                break;
+            }
+        }
+    }
+}
+
+static mcf_status solve_tc_noalloc(int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
+                                   const mcf_params* p, double* y) {
+    set_error("");
+    if (!p) return fail(MCF_ERR_INVALID_ARG, "params is NULL");
+    if (n < 0 || nnz < 0) return fail(MCF_ERR_INVALID_ARG, "n and nnz must be >= 0");
+    if (n > NOALLOC_MAX_NODES)
+        return fail(MCF_ERR_INVALID_ARG, "n = " + std::to_string(n) + " exceeds the allocation-free limit of " +
+                                             std::to_string(NOALLOC_MAX_NODES) + " nodes");
+    if (nnz >= ((int64_t)1 << 32)) return fail(MCF_ERR_INVALID_ARG, "nnz must be below 2^32");
+    if (!p->coeffs || p->n_coeffs < 1 || p->n_coeffs > MCF_MAX_COEFFS)
+        return fail(MCF_ERR_INVALID_ARG, "coeffs must hold 1.." + std::to_string(MCF_MAX_COEFFS) + " values");
+    if (p->n_walks < 0 || p->walks_per_node < 0) return fail(MCF_ERR_INVALID_ARG, "walk counts must be >= 0");
+    if (p->n_coeffs > 2 && p->n_walks == 0 && p->walks_per_node == 0)
+        return fail(MCF_ERR_INVALID_ARG, "n_walks or walks_per_node must be > 0");
+    const int64_t bound = p->walks_per_node > 0 ? p->walks_per_node * n : p->n_walks + n;
+    if (p->walks_per_node > NOALLOC_MAX_WALKS || bound > NOALLOC_MAX_WALKS)
+        return fail(MCF_ERR_INVALID_ARG, "the walk count (up to " + std::to_string(bound) +
+                                             ") exceeds the allocation-free limit of " +
+                                             std::to_string(NOALLOC_MAX_WALKS) + " walks");
+    if (!(p->w_cutoff >= 0.0)) return fail(MCF_ERR_INVALID_ARG, "w_cutoff must be >= 0");
+    if (p->precision != MCF_F64 && p->precision != MCF_F32W_F64ACC)
+        return fail(MCF_ERR_INVALID_ARG, "unknown precision");
+    if (p->deterministic != 0) return fail(MCF_ERR_INVALID_ARG, "deterministic is reserved and must be 0");
+    if (!(p->scale >= 0.0) || !isfinite(p->scale)) return fail(MCF_ERR_INVALID_ARG, "scale must be finite and >= 0");
+    for (int k = 0; k < p->n_coeffs; ++k)
+        if (!isfinite(p->coeffs[k])) return fail(MCF_ERR_INVALID_ARG, "coefficients must be finite");
+    if (!row_ptr || !y || (nnz > 0 && !col_idx)) return fail(MCF_ERR_INVALID_ARG, "NULL array");
+    if (!is_device_ptr(row_ptr) || (nnz > 0 && !is_device_ptr(col_idx)) || !is_device_ptr(y))
+        return fail(MCF_ERR_INVALID_ARG, "row_ptr, col_idx and y must be device pointers");
+    if (n == 0) return MCF_OK;
+    void* base = nullptr;
+    MCF_TRY(noalloc_base(&base));
+    cudaStream_t st = (cudaStream_t)p->stream;
+    const double gamma = p->scale == 0.0 ? 1.0 : p->scale;
+    const int K = p->n_coeffs - 1;
+    const bool f64 = p->precision == MCF_F64;
+    Carve cv{static_cast<char*>(base)};
+    Prep P;
+    P.r = cv.take<double>(NOALLOC_MAX_NODES);
+    P.colnorm = cv.take<double>(NOALLOC_MAX_NODES);
+    P.nw = cv.take<int64_t>(NOALLOC_MAX_NODES);
+    P.flag = cv.take<int64_t>(NOALLOC_MAX_NODES);
+    P.woff = cv.take<int64_t>(NOALLOC_MAX_NODES);
+    P.spos = cv.take<int64_t>(NOALLOC_MAX_NODES);
+    double* acc = cv.take<double>(NOALLOC_MAX_NODES);
+    P.starts = cv.take<int32_t>(NOALLOC_MAX_NODES);
+    P.soff = cv.take<int64_t>(NOALLOC_MAX_NODES + 1);
+    P.rec = cv.take<Rec<true>>(NOALLOC_MAX_NODES);
+    uint32_t* chunk_s0 = cv.take<uint32_t>(NOALLOC_MAX_WALKS / WARP_CHUNK + 2);
+    P.scan_bytes = 8 * ((NOALLOC_MAX_NODES + 4095) / 4096 + 1);
+    P.scan_tmp = cv.take<char>(P.scan_bytes);
+    P.part = cv.take<double>(RED_BLOCKS + 1);
+    P.counters = cv.take<unsigned long long>(N_COUNTERS);
+    P.zeta = cv.take<double>(MCF_MAX_COEFFS);
+    unsigned long long* bad = cv.take<unsigned long long>(4);
+    if ((size_t)(cv.p - static_cast<char*>(base)) > NOALLOC_BYTES)
+        return fail(MCF_ERR_UNSUPPORTED, "internal: allocation-free scratch layout exceeds its array");
+    // The array keeps the previous call's contents: clear what must start at zero.
+    MCF_CUDA_TRY(cudaMemsetAsync(bad, 0, 4 * sizeof(unsigned long long), st));
+    MCF_CUDA_TRY(cudaMemsetAsync(P.counters, 0, N_COUNTERS * sizeof(unsigned long long), st));
+    MCF_CUDA_TRY(cudaMemsetAsync(acc, 0, n * sizeof(double), st));
+    noalloc_check_csr<<<grid_for(n, 256), 256, 0, st>>>(n, nnz, row_ptr, col_idx, bad);
+    unsigned long long hbad = 0;
+    MCF_CUDA_TRY(cudaMemcpyAsync(&hbad, bad, sizeof(hbad), cudaMemcpyDeviceToHost, st));
+    MCF_CUDA_TRY(cudaStreamSynchronize(st));
+    if (hbad) return fail(MCF_ERR_INVALID_GRAPH, "invalid CSR: row_ptr or column indices out of range or unsorted");
+    MCF_CUDA_TRY(cudaMemcpyAsync(P.zeta, p->coeffs, p->n_coeffs * sizeof(double), cudaMemcpyHostToDevice, st));
+    // the same kernel sequence as prepare() + solve_action(), binary matrix, v = 1
+    r_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, row_ptr, col_idx, nullptr, nullptr, gamma, P.r);
+    colnorm_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, row_ptr, nullptr, gamma, P.colnorm, P.part);
+    sum_partials<<<1, RED_THREADS, 0, st>>>(P.part, RED_BLOCKS, P.part + RED_BLOCKS);
+    alloc_kernel<<<grid_for(n, 256), 256, 0, st>>>(n, P.colnorm, P.part + RED_BLOCKS, p->n_walks, p->walks_per_node,
+                                                   nullptr, P.nw, P.flag);
+    MCF_TRY(scan_i64(P.nw, P.woff, n, (int64_t*)&P.counters[C_TOTAL], P.scan_tmp, P.scan_bytes, st));
+    MCF_TRY(scan_i64(P.flag, P.spos, n, (int64_t*)&P.counters[C_STARTS], P.scan_tmp, P.scan_bytes, st));
+    compact_starts<<<grid_for(n, 256), 256, 0, st>>>(n, P.flag, P.spos, P.woff, P.starts, P.soff, P.counters);
+    if (f64)
+        build_records<true><<<grid_for(n, 256), 256, 0, st>>>(n, row_ptr, nullptr, gamma, P.r, (Rec<true>*)P.rec);
+    else
+        build_records<false><<<grid_for(n, 256), 256, 0, st>>>(n, row_ptr, nullptr, gamma, P.r, (Rec<false>*)P.rec);
+    if (K >= 2) {
+        chunk_table<<<grid_for(n, 256), 256, 0, st>>>(P.soff, P.counters, chunk_s0);
+        mcf_graph view;
+        view.n = n;
+        view.nnz = nnz;
+        view.row_ptr = const_cast<int64_t*>(row_ptr);
+        view.col_idx = const_cast<int32_t*>(col_idx);
+        const uint2 key = philox_key(p->seed);
+        if (f64) launch_action_walks<true, false>(&view, P, chunk_s0, K, p->w_cutoff, key, p->request_id, acc, st);
+        else launch_action_walks<false, false>(&view, P, chunk_s0, K, p->w_cutoff, key, p->request_id, acc, st);
+    }
+    finalize_q<<<grid_for(n, 256), 256, 0, st>>>(n, acc, P.nw);
+    const double avg = (double)nnz / (double)n;
+    const double z0 = p->coeffs[0], z1 = K >= 1 ? p->coeffs[1] : 0.0;
+    const int blocks = num_sms() * 8;
+    if (avg <= 6)
+        action_epilogue<4><<<blocks, 256, 0, st>>>(n, row_ptr, col_idx, nullptr, gamma, z0, z1, nullptr, P.r, acc, y);
+    else if (avg <= 24)
+        action_epilogue<8><<<blocks, 256, 0, st>>>(n, row_ptr, col_idx, nullptr, gamma, z0, z1, nullptr, P.r, acc, y);
+    else
+        action_epilogue<32><<<blocks, 256, 0, st>>>(n, row_ptr, col_idx, nullptr, gamma, z0, z1, nullptr, P.r, acc, y);
+    MCF_CUDA_TRY(cudaGetLastError());
+    return MCF_OK;
+}
+
 }  // namespace mcf
 
 using namespace mcf;
@@ -917,6 +1094,11 @@ mcf_status mcf_katz(mcf_graph_t g, double gamma, int32_t K, const mcf_params* pa
     p.n_coeffs = K + 1;
     p.scale = gamma;
     return solve_action(g, &p, nullptr, y, stats, true);
+}
+
+mcf_status mcf_total_communicability_noalloc(int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
+                                             const mcf_params* params, double* y) {
+    return solve_tc_noalloc(n, nnz, row_ptr, col_idx, params, y);
 }
 
 }  // extern "C"

@@ -63,6 +63,7 @@ SIGNATURES = {
     "mcf_total_communicability": ([_P, _P, _P, _P], ctypes.c_int),
     "mcf_subgraph_centrality": ([_P, _P, _P, _I64, _P, _P], ctypes.c_int),
     "mcf_katz": ([_P, _D, _I32, _P, _P, _P], ctypes.c_int),
+    "mcf_total_communicability_noalloc": ([_I64, _I64, _P, _P, _P, _P], ctypes.c_int),
     "mcf_last_error": ([], ctypes.c_char_p),
     "mcf_version": ([], ctypes.c_char_p),
 }
@@ -245,6 +246,17 @@ def mcf_katz(g: GraphHandle, gamma, K=0, out=None, device_out=None, stats=False,
     _check(load().mcf_katz(g.handle, float(gamma), int(K), ctypes.byref(p), yp,
                            ctypes.byref(st) if stats else None))
     return (y, st.as_dict()) if stats else y
+
+
+def mcf_total_communicability_noalloc(n, row_ptr, col_idx, coeffs, out, **kw):
+    """f(A')1 with no device allocation by the library; CSR and ``out`` must be CUDA tensors."""
+    rp, krp = _ptr(row_ptr, np.int64)
+    ci, kci = _ptr(col_idx, np.int32)
+    yp, ky = _ptr(out, np.float64)
+    nnz = int(col_idx.numel()) if _is_torch(col_idx) else len(col_idx)
+    p, kc = _params(coeffs, stream=kw.pop("stream", None) or _stream_of(out), **kw)
+    _check(load().mcf_total_communicability_noalloc(int(n), nnz, rp, ci, ctypes.byref(p), yp))
+    return out
 
 
 def mcf_last_error() -> str:
