@@ -37,12 +37,20 @@ WORKLOADS = {
                       n_walks=100_000_000, walks_per_node=0, w_cutoff=1e-6, K=30,
                       label="total communicability exp(A/lambda_max)1, R-MAT scale 22 ef16 (0.57,0.19,0.19), "
                             "1e8 walks, K=30, W_c=1e-6"),
+    "rmat21_tc": dict(gen=("rmat", dict(scale=21, edge_factor=16, seed=1)), query="tc",
+                      n_walks=25_000_000, walks_per_node=0, w_cutoff=1e-6, K=30,
+                      label="total communicability exp(A/lambda_max)1, R-MAT scale 21 ef16 (0.57,0.19,0.19), "
+                            "2.5e7 walks, K=30, W_c=1e-6 (profiling case)"),
     "ba1000_tc": dict(gen=("barabasi_albert", dict(n=1000, m=3, seed=0)), query="tc",
                       n_walks=0, walks_per_node=100_000, w_cutoff=0.0, K=30,
                       label="total communicability exp(A/lambda_max)1, BA n=1000 m=3, 1e5 walks per node, K=30"),
     "ba1000_sc": dict(gen=("barabasi_albert", dict(n=1000, m=3, seed=0)), query="sc",
                       n_walks=0, walks_per_node=100_000, w_cutoff=0.0, K=30,
                       label="subgraph centrality diag exp(A/lambda_max), BA n=1000 m=3, 1e5 walks per node, K=30"),
+    "cm2m_sc_w100": dict(gen=("config_powerlaw", dict(n=2_000_000, exponent=2.5, mean_degree=20.0, seed=2)),
+                         query="sc", n_walks=0, walks_per_node=100, w_cutoff=1e-6, K=30,
+                         label="subgraph centrality diag exp(A/lambda_max), configuration model n=2e6 k^-2.5 mean 20, "
+                               "100 walks per node (timing case), K=30, W_c=1e-6"),
     "cm2m_sc": dict(gen=("config_powerlaw", dict(n=2_000_000, exponent=2.5, mean_degree=20.0, seed=2)), query="sc",
                     n_walks=0, walks_per_node=2000, w_cutoff=1e-6, K=30,
                     label="subgraph centrality diag exp(A/lambda_max), configuration model n=2e6 k^-2.5 mean 20, "
@@ -73,7 +81,7 @@ def exp_coeffs(K):
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle samples every 200 ms while running."""
+    """nvidia-smi clock/throttle samples every 100 ms while running."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -87,7 +95,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -195,7 +203,7 @@ def run_reference(args, w):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mcf", choices=["mcf", "reference"])
     ap.add_argument("--workload", default="rmat22_tc", choices=sorted(WORKLOADS))

@@ -23,10 +23,13 @@
  *    number of walks per node when the caller asks for one.
  *  - The series is truncated at K = n_coeffs - 1: a walk makes at most K - 2
  *    transitions; the paper's cutoff test |W| <= W_c stops it earlier.
- *  - SelectNextState draws one Philox4x32-10 block per transition, keyed by
- *    the 64-bit seed, counter (step, walk id low, walk id high, request id).
- *    A uniform row takes j = (u0 * deg) >> 32; a weighted row uses Vose's
- *    alias table with bucket b = (u0 * deg) >> 32 and x = (u1 >> 8) * 2^-24.
+ *  - SelectNextState takes its random words from Philox4x32-10 blocks keyed
+ *    by the 64-bit seed, counter (block, walk id low, walk id high, request
+ *    id).  A uniform row uses one 32-bit word per transition: transition k
+ *    reads word k % 4 of block k / 4, and takes j = (w0 * deg) >> 32.  A
+ *    weighted row uses two words per transition: words 2(k % 2) and
+ *    2(k % 2) + 1 of block k / 2, bucket b = (w0 * deg) >> 32 and
+ *    x = (w1 >> 8) * 2^-24 for Vose's alias table.
  *  - For a binary A the row sums and column norms are evaluated in closed
  *    form: sum_j |a'_ij| = gamma * deg_i, ||C_i||_2 = gamma * sqrt(deg_i).
  *    For a weighted A: gamma * (sum_j |a_ij|) and gamma * sqrt(sum_j a_ij^2),
@@ -175,12 +178,29 @@ static int chain_build(chain_t* c, int64_t n, const int64_t* rp, const int32_t* 
     return 0;
 }
 
-/* SelectNextState: position j within row l, drawn from the Philox block u. */
-static int64_t select_next(const chain_t* c, int64_t l, const uint32_t u[4]) {
+/* The random words of transition k of walk g: one word (w[0]) for a uniform
+ * row, two (w[0], w[1]) for a weighted row. */
+static void draw_words(int weighted, uint64_t g, int k, const uint32_t key[2], uint32_t req, uint32_t w[2]) {
+    uint32_t u[4];
+    if (!weighted) {
+        uint32_t ctr[4] = {(uint32_t)(k / 4), (uint32_t)g, (uint32_t)(g >> 32), req};
+        orc_philox4x32_10(ctr, key, u);
+        w[0] = u[k % 4];
+        w[1] = 0;
+    } else {
+        uint32_t ctr[4] = {(uint32_t)(k / 2), (uint32_t)g, (uint32_t)(g >> 32), req};
+        orc_philox4x32_10(ctr, key, u);
+        w[0] = u[2 * (k % 2)];
+        w[1] = u[2 * (k % 2) + 1];
+    }
+}
+
+/* SelectNextState: position j within row l, drawn from the words w. */
+static int64_t select_next(const chain_t* c, int64_t l, const uint32_t w[2]) {
     int64_t d = c->rp[l + 1] - c->rp[l];
-    int64_t b = (int64_t)(((uint64_t)u[0] * (uint64_t)d) >> 32);
+    int64_t b = (int64_t)(((uint64_t)w[0] * (uint64_t)d) >> 32);
     if (!c->val) return b;
-    float x = (float)(u[1] >> 8) * 5.9604644775390625e-08f; /* 2^-24 */
+    float x = (float)(w[1] >> 8) * 5.9604644775390625e-08f; /* 2^-24 */
     int64_t p = c->rp[l] + b;
     return x < c->prob[p] ? b : (int64_t)c->alias[p];
 }
@@ -215,10 +235,9 @@ static int64_t run_walk(const chain_t* c, int64_t i, int64_t g, const double* ze
         if (k + 2 >= K) break;                           /* truncation of the series */
         int64_t d = c->rp[l + 1] - c->rp[l];
         if (d == 0) break;
-        uint32_t ctr[4] = {(uint32_t)k, (uint32_t)(uint64_t)g, (uint32_t)((uint64_t)g >> 32), req};
-        uint32_t u[4];
-        orc_philox4x32_10(ctr, key, u);
-        int64_t pos = c->rp[l] + select_next(c, l, u);
+        uint32_t w[2];
+        draw_words(c->val != NULL, (uint64_t)g, k, key, req, w);
+        int64_t pos = c->rp[l] + select_next(c, l, w);
         double ratio = weight_ratio(c, l, pos);          /* Eq. weights */
         if (precision == 0) W = W * ratio;
         else W32 = W32 * (float)ratio;
@@ -485,10 +504,9 @@ int orc_mc_classic_action(int64_t n, const int64_t* rp, const int32_t* ci, const
                 if (k >= K) break;
                 int64_t d = rp[l + 1] - rp[l];
                 if (d == 0) break;
-                uint32_t ctr[4] = {(uint32_t)k, (uint32_t)g, (uint32_t)(g >> 32), req};
-                uint32_t u[4];
-                orc_philox4x32_10(ctr, key, u);
-                int64_t p = rp[l] + select_next(&c, l, u);
+                uint32_t w[2];
+                draw_words(val != NULL, g, k, key, req, w);
+                int64_t p = rp[l] + select_next(&c, l, w);
                 W = W * weight_ratio(&c, l, p);
                 l = ci[p];
             }

@@ -1,0 +1,226 @@
+// Device building blocks shared by the walk kernels of libmcf.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mcf_internal.cuh"
+
+namespace mcf {
+
+// ====================================================================== RNG
+// Philox4x32-10 (Salmon, Moraes, Dror and Shaw, SC'11): ten rounds of two
+// 32x32 -> 64-bit products by 0xD2511F53 and 0xCD9E8D57; between rounds the
+// key is advanced by the Weyl constants 0x9E3779B9 and 0xBB67AE85.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+// Random words of transition k of a walk (ids glo/ghi): a uniform row uses
+// word k % 4 of block k / 4; a weighted row uses words 2(k % 2), 2(k % 2) + 1
+// of block k / 2 (bucket and alias test).  u caches the current block and is
+// refilled when k enters a new block, so consecutive transitions of a walk
+// share one Philox4x32-10 evaluation.
+template <bool WEIGHTED>
+__device__ __forceinline__ void walk_words(uint4& u, int k, uint32_t glo, uint32_t ghi, uint32_t req, uint2 key,
+                                           uint32_t& w0, uint32_t& w1) {
+    if constexpr (!WEIGHTED) {
+        if ((k & 3) == 0) u = philox4x32_10(make_uint4((uint32_t)(k >> 2), glo, ghi, req), key);
+        const int s = k & 3;
+        w0 = s == 0 ? u.x : (s == 1 ? u.y : (s == 2 ? u.z : u.w));
+        w1 = 0u;
+    } else {
+        if ((k & 1) == 0) u = philox4x32_10(make_uint4((uint32_t)(k >> 1), glo, ghi, req), key);
+        w0 = (k & 1) ? u.z : u.x;
+        w1 = (k & 1) ? u.w : u.y;
+    }
+}
+
+// ====================================================================== node records
+// What one walk step reads about the state l it leaves: CSR offset, degree,
+// r_l (the contracted row <R_l, v>, Section 3.4) and the weight multiplier
+// sum_j |a'_lj| (Eq. weights: a/t = sign(a) * row sum).  One 16-byte (float)
+// or 32-byte (double) load per step.
+template <bool F64>
+struct Rec;
+template <>
+struct __align__(16) Rec<false> {
+    uint32_t off;
+    uint32_t deg;
+    float r;
+    float mult;
+};
+template <>
+struct __align__(16) Rec<true> {
+    int64_t off;
+    uint32_t deg;
+    uint32_t pad;
+    double r;
+    double mult;
+};
+
+constexpr int RED_BLOCKS = 256;
+constexpr int RED_THREADS = 256;
+constexpr int WARP_CHUNK = 32;      // walks per chunk (one per lane)
+constexpr int CHUNKS_PER_GRAB = 4;  // chunks a warp takes per atomic
+
+enum Counter { C_NEXT = 0, C_STEPS = 1, C_WALKS = 2, C_FLAGS = 3, C_TOTAL = 4, C_STARTS = 5, N_COUNTERS = 8 };
+
+__device__ double block_sum_d(double v) {
+    __shared__ double part[32];
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += part[w];
+    __syncthreads();
+    return s;
+}
+
+// L2 eviction-priority policies: node records are re-read by every walk that
+// passes through a node and should stay in L2; column-index reads are spread
+// uniformly over all nnz entries and should not displace them.
+__device__ __forceinline__ uint64_t policy_evict_last() {
+    uint64_t pol;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t pol;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ Rec<false> load_rec(const Rec<false>* p, uint64_t pol) {
+    uint4 v;
+    asm("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+        : "l"(p), "l"(pol));
+    Rec<false> x;
+    x.off = v.x;
+    x.deg = v.y;
+    x.r = __uint_as_float(v.z);
+    x.mult = __uint_as_float(v.w);
+    return x;
+}
+__device__ __forceinline__ Rec<true> load_rec(const Rec<true>* p, uint64_t) { return *p; }
+__device__ __forceinline__ int32_t load_col(const int32_t* p, uint64_t pol) {
+    int32_t v;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
+
+// Compensated float32 accumulator: the pair (hi, lo) carries about 48 bits;
+// each addition is Knuth's TwoSum followed by a renormalisation, so a walk's
+// sum of at most MCF_MAX_COEFFS float32 terms is exact to a few units of
+// 2^-48 relative, and no float64 instruction runs per step.
+struct F2Acc {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float t) {
+        const float s = __fadd_rn(hi, t);
+        const float bp = __fsub_rn(s, hi);
+        const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(t, bp));
+        const float l = __fadd_rn(lo, e);
+        hi = __fadd_rn(s, l);
+        lo = __fsub_rn(l, __fsub_rn(hi, s));
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+__device__ __forceinline__ uint2 load_od(const uint2* p, uint64_t pol) {
+    uint2 v;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;"
+        : "=r"(v.x), "=r"(v.y)
+        : "l"(p), "l"(pol));
+    return v;
+}
+
+// Per-warp buffer of finished walks (start node, walk sum).  Lanes that
+// finish a walk in the same loop iteration append in lane order; when 32 or
+// more results are waiting the whole warp flushes them together: each lane
+// converts one result to float64, the warp sorts the 32 (node, value) pairs by
+// node (bitonic network over shuffles), sums runs of equal nodes with a
+// segmented scan, and the first lane of each run adds the run to acc[node].
+// The float64 work of walk completion thus runs with full warps, and walks of
+// one start node -- thousands of them on a small graph -- share one atomic.
+__device__ __forceinline__ double walk_value(float2 v) { return (double)v.x + (double)v.y; }
+__device__ __forceinline__ double walk_value(double v) { return v; }
+
+__device__ __forceinline__ void warp_merge_add(uint32_t nd, double v, bool valid, int lane, double* __restrict__ acc) {
+    const unsigned FULL = 0xffffffffu;
+    uint32_t key = valid ? nd : 0xffffffffu;
+    // bitonic sort of (key, v) across the 32 lanes, ascending keys
+#pragma unroll
+    for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            const uint32_t ok = __shfl_xor_sync(FULL, key, stride);
+            const double ov = __shfl_xor_sync(FULL, v, stride);
+            const bool up = ((lane & size) == 0);
+            const bool lower = (lane & stride) == 0;
+            const bool take_min = (lower == up);
+            const bool swap = take_min ? (ok < key) : (ok > key);
+            if (swap) {
+                key = ok;
+                v = ov;
+            }
+        }
+    }
+    // runs of equal keys are now contiguous; run ids from the run heads
+    const uint32_t prev = __shfl_up_sync(FULL, key, 1);
+    const bool head = lane == 0 || prev != key;
+    const unsigned heads = __ballot_sync(FULL, head);
+    const int run = __popc(heads & ((2u << lane) - 1u));
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const double o = __shfl_down_sync(FULL, v, d);
+        const int orun = __shfl_down_sync(FULL, run, d);
+        if (lane + d < 32 && orun == run) v += o;
+    }
+    if (head && key != 0xffffffffu) atomicAdd(&acc[key], v);
+}
+
+template <class T>
+struct WalkResults {
+    uint32_t node[64];
+    T val[64];
+    __device__ __forceinline__ void flush(int n, int lane, double* __restrict__ acc) {
+        __syncwarp();
+        for (int r = 0; r < n; r += 32) {
+            const int e = r + lane;
+            const bool valid = e < n;
+            warp_merge_add(valid ? node[e] : 0u, valid ? walk_value(val[e]) : 0.0, valid, lane, acc);
+        }
+        __syncwarp();
+    }
+    // Appends the results of the lanes with done set; returns the new count.
+    __device__ __forceinline__ int push(bool done, uint32_t nd, T v, int n, int lane, unsigned lt_mask,
+                                        double* __restrict__ acc) {
+        const unsigned dm = __ballot_sync(0xffffffffu, done);
+        if (!dm) return n;
+        if (done) {
+            const int pos = n + __popc(dm & lt_mask);
+            node[pos] = nd;
+            val[pos] = v;
+        }
+        n += __popc(dm);
+        if (n >= 32) {
+            flush(n, lane, acc);
+            n = 0;
+        }
+        return n;
+    }
+};
+
+}  // namespace mcf

@@ -246,35 +246,23 @@ __global__ void weighted_rows(int64_t n, const int64_t* __restrict__ rp, const i
 }
 
 // ------------------------------------------------------------------ SpMV and reductions
-// VEC lanes per row; the row loop is uniform across the warp so that every
-// lane reaches the shuffles.
-template <int VEC>
+// A warp covers 32 consecutive rows (warp_row_sums).
 __global__ void spmv_f64_kernel(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                                 const float* __restrict__ val, const double* __restrict__ x, double* __restrict__ y,
                                 double beta) {
-    constexpr int GROUPS = 32 / VEC;
-    const int lane = threadIdx.x & 31, sub = lane % VEC;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t base = warp * GROUPS; base < n; base += nwarps * GROUPS) {
-        const int64_t row = base + lane / VEC;
-        double s = 0.0;
-        if (row < n)
-            for (int64_t p = rp[row] + sub; p < rp[row + 1]; p += VEC) s += (val ? (double)val[p] : 1.0) * x[col[p]];
-#pragma unroll
-        for (int d = VEC / 2; d > 0; d >>= 1) s += __shfl_down_sync(0xffffffffu, s, d, VEC);
-        if (sub == 0 && row < n) y[row] = beta * s;
+    for (int64_t base = warp * 32; base < n; base += nwarps * 32) {
+        const double s = warp_row_sums<32>(base, n, rp, col, val, x);
+        const int64_t row = base + (threadIdx.x & 31);
+        if (row < n) y[row] = beta * s;
     }
 }
 
 mcf_status spmv_f64(const mcf_graph* g, const double* x, double* y, double beta, cudaStream_t st) {
     if (g->n == 0) return MCF_OK;
-    double avg = (double)g->nnz / (double)g->n;
-    int blocks = num_sms() * 8;
-    if (avg <= 4) spmv_f64_kernel<4><<<blocks, 256, 0, st>>>(g->n, g->row_ptr, g->col_idx, g->values, x, y, beta);
-    else if (avg <= 12) spmv_f64_kernel<8><<<blocks, 256, 0, st>>>(g->n, g->row_ptr, g->col_idx, g->values, x, y, beta);
-    else if (avg <= 48) spmv_f64_kernel<16><<<blocks, 256, 0, st>>>(g->n, g->row_ptr, g->col_idx, g->values, x, y, beta);
-    else spmv_f64_kernel<32><<<blocks, 256, 0, st>>>(g->n, g->row_ptr, g->col_idx, g->values, x, y, beta);
+    const int64_t blocks = std::min<int64_t>((g->n + 255) / 256, (int64_t)num_sms() * 16);
+    spmv_f64_kernel<<<(unsigned)blocks, 256, 0, st>>>(g->n, g->row_ptr, g->col_idx, g->values, x, y, beta);
     MCF_CUDA_TRY(cudaGetLastError());
     return MCF_OK;
 }
@@ -466,6 +454,8 @@ mcf_status mcf_destroy_graph(mcf_graph_t g) {
     cudaFree(g->row_sq);
     cudaFree(g->diag);
     cudaFree(g->went);
+    cudaFree(g->node_od);
+    cudaFree(g->edge_od);
     delete g;
     return MCF_OK;
 }

@@ -60,12 +60,56 @@ struct mcf_graph {
     double* row_sq = nullptr;     // n: sum_j a_ij^2 (unscaled; weighted only)
     double* diag = nullptr;       // n: a_ii
     mcf::WEntry* went = nullptr;  // nnz (weighted only)
+    // Binary graphs with nnz < 2^32, built on the first solve that walks with
+    // them: node_od[i] = {row offset, degree} of node i and, per CSR entry,
+    // edge_od[p] = node_od[col_idx[p]], the record of the neighbour an entry
+    // leads to -- so a walk step reads one random 8-byte word instead of a
+    // column index and then a node record.
+    uint2* node_od = nullptr;     // n
+    uint2* edge_od = nullptr;     // nnz
     double lambda_max = 0.0;      // cached by mcf_spectral_radius (0 = unknown)
     double gershgorin = 0.0;
     int device = 0;
 };
 
 namespace mcf {
+
+// ---------------------------------------------------------------- row sums
+// sum_j a_ij x[j] for the 32 rows base .. base+31 of a warp: lane t owns row
+// base + t and sums it alone when it has at most SHORT entries; longer rows
+// are then summed by the whole warp, one at a time.  FP64 instructions on
+// this part issue at a small fraction of the FP32 rate, so every lane keeps
+// its own row instead of reducing across lanes for every row.  Must be called
+// by all 32 lanes with the same base.  Returns the sum of row base + lane.
+template <int SHORT>
+__device__ __forceinline__ double warp_row_sums(int64_t base, int64_t n, const int64_t* __restrict__ rp,
+                                                const int32_t* __restrict__ col, const float* __restrict__ val,
+                                                const double* __restrict__ x) {
+    const int lane = threadIdx.x & 31;
+    const int64_t row = base + lane;
+    int64_t b = 0, e = 0;
+    if (row < n) {
+        b = rp[row];
+        e = rp[row + 1];
+    }
+    double s = 0.0;
+    const bool is_short = e - b <= SHORT;
+    if (is_short)
+        for (int64_t p = b; p < e; ++p) s += (val ? (double)val[p] : 1.0) * x[col[p]];
+    unsigned longs = __ballot_sync(0xffffffffu, !is_short);
+    while (longs) {
+        const int t = __ffs(longs) - 1;
+        longs &= longs - 1;
+        const int64_t lb = __shfl_sync(0xffffffffu, b, t);
+        const int64_t le = __shfl_sync(0xffffffffu, e, t);
+        double part = 0.0;
+        for (int64_t p = lb + lane; p < le; p += 32) part += (val ? (double)val[p] : 1.0) * x[col[p]];
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) part += __shfl_xor_sync(0xffffffffu, part, d);
+        if (lane == t) s = part;
+    }
+    return s;
+}
 
 // ---------------------------------------------------------------- helpers (host)
 bool is_device_ptr(const void* p);

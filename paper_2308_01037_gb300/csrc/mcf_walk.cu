@@ -5,74 +5,16 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <stdlib.h>
+
 #include <algorithm>
 #include <string>
 #include <type_traits>
 
+#include "mcf_device.cuh"
 #include "mcf_internal.cuh"
 
 namespace mcf {
-
-// ====================================================================== RNG
-// Philox4x32-10 (Salmon, Moraes, Dror and Shaw, SC'11): ten rounds of two
-// 32x32 -> 64-bit products by 0xD2511F53 and 0xCD9E8D57; between rounds the
-// key is advanced by the Weyl constants 0x9E3779B9 and 0xBB67AE85.
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        if (r) {
-            k.x += 0x9E3779B9u;
-            k.y += 0xBB67AE85u;
-        }
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
-        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
-    }
-    return c;
-}
-
-// ====================================================================== node records
-// What one walk step reads about the state l it leaves: CSR offset, degree,
-// r_l (the contracted row <R_l, v>, Section 3.4) and the weight multiplier
-// sum_j |a'_lj| (Eq. weights: a/t = sign(a) * row sum).  One 16-byte (float)
-// or 32-byte (double) load per step.
-template <bool F64>
-struct Rec;
-template <>
-struct __align__(16) Rec<false> {
-    uint32_t off;
-    uint32_t deg;
-    float r;
-    float mult;
-};
-template <>
-struct __align__(16) Rec<true> {
-    int64_t off;
-    uint32_t deg;
-    uint32_t pad;
-    double r;
-    double mult;
-};
-
-constexpr int RED_BLOCKS = 256;
-constexpr int RED_THREADS = 256;
-constexpr int WARP_CHUNK = 32;      // walks per chunk (one per lane)
-constexpr int CHUNKS_PER_GRAB = 4;  // chunks a warp takes per atomic
-
-enum Counter { C_NEXT = 0, C_STEPS = 1, C_WALKS = 2, C_FLAGS = 3, C_TOTAL = 4, C_STARTS = 5, N_COUNTERS = 8 };
-
-__device__ double block_sum_d(double v) {
-    __shared__ double part[32];
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
-    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
-    __syncthreads();
-    double s = 0.0;
-    if (threadIdx.x == 0)
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += part[w];
-    __syncthreads();
-    return s;
-}
 
 // r = A' v evaluated as gamma * sum_j (a_ij v_j), the sum in CSR order with
 // every product and sum rounded on its own (thread per row); v == nullptr
@@ -193,15 +135,15 @@ __global__ void build_records(int64_t n, const int64_t* __restrict__ rp, const d
 // within the row from the Philox block u; returns the next state and the
 // signed multiplier sign(a_{l l'}) * sum_j |a'_lj|.
 template <bool F64, bool WEIGHTED>
-__device__ __forceinline__ uint32_t next_state(const Rec<F64>& x, uint4 u, const int32_t* __restrict__ col,
-                                               const WEntry* __restrict__ went,
+__device__ __forceinline__ uint32_t next_state(const Rec<F64>& x, uint32_t w0, uint32_t w1,
+                                               const int32_t* __restrict__ col, const WEntry* __restrict__ went,
                                                typename std::conditional<F64, double, float>::type& mult) {
-    const uint32_t b = __umulhi(u.x, x.deg);
+    const uint32_t b = __umulhi(w0, x.deg);
     mult = x.mult;
     if constexpr (!WEIGHTED) {
         return (uint32_t)__ldg(col + (int64_t)x.off + b);
     } else {
-        const float xr = __fmul_rn(__uint2float_rn(u.y >> 8), 5.9604644775390625e-08f);
+        const float xr = __fmul_rn(__uint2float_rn(w1 >> 8), 5.9604644775390625e-08f);
         WEntry e = went[(int64_t)x.off + b];
         if (!(xr < e.prob)) e = went[(int64_t)x.off + e.alias];
         if (e.val < 0.0f) mult = -mult;
@@ -210,89 +152,295 @@ __device__ __forceinline__ uint32_t next_state(const Rec<F64>& x, uint4 u, const
 }
 
 // ====================================================================== RandFunmAction walks
-// Persistent kernel.  A warp takes CHUNKS_PER_GRAB chunks of 32 consecutive
-// walk ids at a time; lane t runs walk 32c + t.  Walks of one start node are
-// contiguous, so lanes sharing a start combine their sums with a segmented
-// warp reduction and issue one float64 atomic per (chunk, start).
-template <bool F64, bool WEIGHTED>
-__global__ void __launch_bounds__(256) walk_action_kernel(
+// Persistent kernel with per-lane refill.  A warp takes CHUNKS_PER_GRAB
+// chunks of 32 consecutive walk ids per atomic; whenever lanes are idle they
+// are handed the next walk ids of the chunk in lane order, so no lane waits
+// for the longest walk of its warp.  The start node of a chunk's walks comes
+// from a 5-step shuffle binary search over the chunk's 32 start boundaries.
+// One loop iteration advances every active lane by one visit of
+// Algorithm 3's while loop.  A lane keeps a running sum while its
+// consecutive walks share a start node and adds it to acc[start] with one
+// float64 atomic when the start changes.
+template <bool F64, bool WEIGHTED, int MINB>
+__global__ void __launch_bounds__(256, MINB) walk_action_kernel(
     const Rec<F64>* __restrict__ rec, const int32_t* __restrict__ col, const WEntry* __restrict__ went,
     const int32_t* __restrict__ starts, const int64_t* __restrict__ soff, const uint32_t* __restrict__ chunk_s0,
-    const double* __restrict__ zeta_g, int K, double wc, uint2 key, uint32_t req, double* __restrict__ acc,
-    unsigned long long* __restrict__ counters) {
+    const double* __restrict__ zeta_g, int K, double wc, float wc32, uint2 key, uint32_t req, int grab,
+    double* __restrict__ acc, unsigned long long* __restrict__ counters) {
     using real = typename std::conditional<F64, double, float>::type;
+    using rtype = typename std::conditional<F64, double, float2>::type;
     __shared__ real zeta[MCF_MAX_COEFFS];
+    __shared__ WalkResults<rtype> rbuf[256 / 32];
     for (int k = threadIdx.x; k <= K; k += blockDim.x) zeta[k] = (real)zeta_g[k];
     __syncthreads();
+    const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const int64_t n_total = (int64_t)counters[C_TOTAL];
-    const int64_t S = (int64_t)counters[C_STARTS];
-    const int64_t n_chunks = (n_total + WARP_CHUNK - 1) / WARP_CHUNK;
-    unsigned long long my_steps = 0, my_walks = 0;
-    uint32_t flags = 0;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    WalkResults<rtype>& rb = rbuf[threadIdx.x >> 5];
+    int rb_n = 0;
+    const int32_t n_chunks = (int32_t)(((int64_t)counters[C_TOTAL] + WARP_CHUNK - 1) / WARP_CHUNK);
+
+    // warp-uniform pool of walk ids (chunk indices fit 32 bits: the host
+    // bounds the walk count below 2^36)
+    int32_t c = -1, c_end = -1;
+    int p = 0, valid = 0;
+    int32_t cs = 0;          // start index of walk 32c + lane
+    bool exhausted = false;
+    // lane state
+    bool active = false;
+    int64_t g = 0;
+    uint32_t l = 0, node0 = 0;
+    int k = 0;
+    real W = (real)1;
+    uint4 u = make_uint4(0u, 0u, 0u, 0u);
+    F2Acc a32;
+    double a64 = 0.0;
+    uint32_t my_steps = 0, my_walks = 0, flags = 0;
+
     for (;;) {
-        int64_t c0 = 0;
-        if (lane == 0) c0 = (int64_t)atomicAdd(&counters[C_NEXT], (unsigned long long)CHUNKS_PER_GRAB) ;
-        c0 = __shfl_sync(0xffffffffu, c0, 0);
-        if (c0 >= n_chunks) break;
-        const int64_t c1 = min(c0 + CHUNKS_PER_GRAB, n_chunks);
-        for (int64_t c = c0; c < c1; ++c) {
-            const int64_t g = c * WARP_CHUNK + lane;
-            const bool active = g < n_total;
-            // which start holds walk g: count the start boundaries <= g in the
-            // window of 32 starts beginning at the chunk's first start
-            const int64_t s0 = chunk_s0[c];
-            const int64_t bnd = (s0 + 1 + lane <= S) ? soff[s0 + 1 + lane] : INT64_MAX;
-            int cnt = 0;
+        unsigned idle = __ballot_sync(FULL, !active);
+        while (idle && !exhausted) {
+            if (p >= valid) {
+                ++c;
+                if (c >= c_end) {
+                    int32_t base = 0;
+                    if (lane == 0) base = (int32_t)atomicAdd((unsigned int*)&counters[C_NEXT], (unsigned)grab);
+                    base = __shfl_sync(FULL, base, 0);
+                    c = base;
+                    c_end = min(base + grab, n_chunks);
+                }
+                if (c >= n_chunks) {
+                    exhausted = true;
+                    break;
+                }
+                const int64_t S = (int64_t)counters[C_STARTS];
+                const int64_t s0 = chunk_s0[c];
+                const int64_t bnd = (s0 + 1 + lane <= S) ? soff[s0 + 1 + lane] : INT64_MAX;
+                const int64_t gl = (int64_t)c * WARP_CHUNK + lane;
+                int cnt = 0;
 #pragma unroll
-            for (int step = 16; step > 0; step >>= 1) {
-                const int64_t bv = __shfl_sync(0xffffffffu, bnd, cnt + step - 1);
-                if (bv <= g) cnt += step;
+                for (int step = 16; step > 0; step >>= 1) {
+                    const int64_t bv = __shfl_sync(FULL, bnd, cnt + step - 1);
+                    if (bv <= gl) cnt += step;
+                }
+                cs = (int32_t)(s0 + cnt);
+                valid = (int)min((int64_t)WARP_CHUNK, (int64_t)counters[C_TOTAL] - (int64_t)c * WARP_CHUNK);
+                p = 0;
             }
-            const int64_t sidx = active ? s0 + cnt : -1;
-            double sum = 0.0;
-            if (active) {
-                uint32_t l = (uint32_t)starts[sidx];
-                real W = (real)1;
-                const uint32_t glo = (uint32_t)g, ghi = (uint32_t)((uint64_t)g >> 32);
-                for (int k = 0; k <= K; ++k) {
-                    if (!((double)fabs(W) > wc)) break;  // Eq. weight_cutoff, W^(0) = 1
-                    const uint4 u = philox4x32_10(make_uint4((uint32_t)k, glo, ghi, req), key);
-                    const Rec<F64> x = rec[l];
-                    if constexpr (F64) sum += __dmul_rn(__dmul_rn(zeta[k + 2], W), x.r);
-                    else sum += (double)__fmul_rn(__fmul_rn(zeta[k + 2], W), x.r);
-                    if (k + 2 >= K || x.deg == 0) break;
-                    real mult;
-                    const uint32_t nl = next_state<F64, WEIGHTED>(x, u, col, went, mult);
+            const int avail = valid - p;
+            const int rank = __popc(idle & lt_mask);
+            const int src = min(p + rank, WARP_CHUNK - 1);
+            const int32_t s_new = __shfl_sync(FULL, cs, src);
+            if (((idle >> lane) & 1u) && rank < avail) {
+                g = (int64_t)c * WARP_CHUNK + p + rank;
+                node0 = (uint32_t)starts[s_new];
+                l = node0;
+                k = 0;
+                W = (real)1;
+                a32 = F2Acc();
+                a64 = 0.0;
+                active = true;
+            }
+            p += min(avail, __popc(idle));
+            idle = __ballot_sync(FULL, !active);
+        }
+        if (!__any_sync(FULL, active)) break;
+        bool done = false;
+        if (active) {
+            if constexpr (F64) done = !(fabs(W) > wc);
+            else done = !(fabsf(W) > wc32);  // same decision as (double)|W| > W_c
+            if (!done) {
+                uint32_t w0, w1;
+                walk_words<WEIGHTED>(u, k, (uint32_t)g, (uint32_t)((uint64_t)g >> 32), req, key, w0, w1);
+                const Rec<F64> x = load_rec(rec + l, policy_evict_last());
+                if constexpr (F64) a64 += __dmul_rn(__dmul_rn(zeta[k + 2], W), x.r);
+                else a32.add(__fmul_rn(__fmul_rn(zeta[k + 2], W), x.r));
+                if (k + 2 >= K || x.deg == 0) {
+                    done = true;
+                } else {
+                    const uint32_t b = __umulhi(w0, x.deg);
+                    real mult = x.mult;
+                    uint32_t nl;
+                    if constexpr (!WEIGHTED) {
+                        nl = (uint32_t)load_col(col + (int64_t)x.off + b, policy_evict_first());
+                    } else {
+                        const float xr = __fmul_rn(__uint2float_rn(w1 >> 8), 5.9604644775390625e-08f);
+                        WEntry e = went[(int64_t)x.off + b];
+                        if (!(xr < e.prob)) e = went[(int64_t)x.off + e.alias];
+                        if (e.val < 0.0f) mult = -mult;
+                        nl = (uint32_t)e.col;
+                    }
                     if constexpr (F64) W = __dmul_rn(W, mult);
                     else W = __fmul_rn(W, mult);
                     l = nl;
+                    ++k;
                     ++my_steps;
                 }
-                if constexpr (!F64) if (!isfinite(W) || !isfinite(sum)) flags |= 1u;
+            }
+            if (done) {
+                if constexpr (!F64) if (!isfinite(W) || !isfinite(a32.hi)) flags |= 1u;
                 ++my_walks;
+                active = false;
             }
-            // segmented suffix sums over lanes with equal sidx (contiguous runs)
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const double o = __shfl_down_sync(0xffffffffu, sum, d);
-                const int64_t os = __shfl_down_sync(0xffffffffu, sidx, d);
-                if (lane + d < 32 && os == sidx) sum += o;
-            }
-            const int64_t prev = __shfl_up_sync(0xffffffffu, sidx, 1);
-            if (active && (lane == 0 || prev != sidx)) atomicAdd(&acc[starts[sidx]], sum);
         }
+        if constexpr (F64) rb_n = rb.push(done, node0, a64, rb_n, lane, lt_mask, acc);
+        else rb_n = rb.push(done, node0, make_float2(a32.hi, a32.lo), rb_n, lane, lt_mask, acc);
     }
-    // per-warp totals
+    rb.flush(rb_n, lane, acc);
+    unsigned long long ws = my_steps, ww = my_walks;
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
-        my_steps += __shfl_down_sync(0xffffffffu, my_steps, d);
-        my_walks += __shfl_down_sync(0xffffffffu, my_walks, d);
-        flags |= __shfl_down_sync(0xffffffffu, flags, d);
+        ws += __shfl_down_sync(FULL, ws, d);
+        ww += __shfl_down_sync(FULL, ww, d);
+        flags |= __shfl_down_sync(FULL, flags, d);
     }
     if (lane == 0) {
-        atomicAdd(&counters[C_STEPS], my_steps);
-        atomicAdd(&counters[C_WALKS], my_walks);
+        atomicAdd(&counters[C_STEPS], ws);
+        atomicAdd(&counters[C_WALKS], ww);
+        if (flags) atomicOr(&counters[C_FLAGS], (unsigned long long)flags);
+    }
+}
+
+// ---------------------------------------------------------------- binary v = 1 path
+// For total communicability and Katz on a binary matrix, r_l and the weight
+// multiplier of a state are both gamma * deg_l, so a step needs only the
+// {row offset, degree} of the state it moves to.  These come from edge_od
+// (one random 8-byte read per step); rm[d] = float(gamma * d) is a per-solve
+// table indexed by degree (small, cache-resident).
+__global__ void build_node_od(int64_t n, const int64_t* __restrict__ rp, uint2* __restrict__ nod) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        nod[i] = make_uint2((uint32_t)rp[i], (uint32_t)(rp[i + 1] - rp[i]));
+}
+
+__global__ void build_edge_od(int64_t nnz, const int32_t* __restrict__ col, const uint2* __restrict__ nod,
+                              uint2* __restrict__ eod) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x)
+        eod[p] = nod[col[p]];
+}
+
+__global__ void degree_table(int64_t max_deg, double gamma, float* __restrict__ rm) {
+    for (int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; d <= max_deg; d += (int64_t)gridDim.x * blockDim.x)
+        rm[d] = __double2float_rn(__dmul_rn(gamma, (double)d));
+}
+
+// Same walk schedule, Philox streams, float32 arithmetic and accumulation as
+// walk_action_kernel<false, false, MINB> (so the same result up to float64
+// summation order), with the per-step state reduced to {offset, degree}.
+template <int MINB>
+__global__ void __launch_bounds__(256, MINB) walk_tc_kernel(
+    const uint2* __restrict__ nod, const uint2* __restrict__ eod, const float* __restrict__ rm,
+    const int32_t* __restrict__ starts, const int64_t* __restrict__ soff, const uint32_t* __restrict__ chunk_s0,
+    const double* __restrict__ zeta_g, int K, float wc32, uint2 key, uint32_t req, int grab,
+    double* __restrict__ acc, unsigned long long* __restrict__ counters) {
+    __shared__ float zeta[MCF_MAX_COEFFS];
+    __shared__ WalkResults<float2> rbuf[256 / 32];
+    for (int k = threadIdx.x; k <= K; k += blockDim.x) zeta[k] = (float)zeta_g[k];
+    __syncthreads();
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    WalkResults<float2>& rb = rbuf[threadIdx.x >> 5];
+    const int32_t n_chunks = (int32_t)(((int64_t)counters[C_TOTAL] + WARP_CHUNK - 1) / WARP_CHUNK);
+    int32_t c = -1, c_end = -1;
+    int p = 0, valid = 0, rb_n = 0;
+    int32_t cs = 0;
+    bool exhausted = false;
+    bool active = false;
+    int64_t g = 0;
+    uint32_t node0 = 0, off = 0, deg = 0;
+    int k = 0;
+    float W = 1.f;
+    uint4 u = make_uint4(0u, 0u, 0u, 0u);
+    F2Acc a32;
+    uint32_t my_steps = 0, my_walks = 0, flags = 0;
+    for (;;) {
+        unsigned idle = __ballot_sync(FULL, !active);
+        while (idle && !exhausted) {
+            if (p >= valid) {
+                ++c;
+                if (c >= c_end) {
+                    int32_t base = 0;
+                    if (lane == 0) base = (int32_t)atomicAdd((unsigned int*)&counters[C_NEXT], (unsigned)grab);
+                    base = __shfl_sync(FULL, base, 0);
+                    c = base;
+                    c_end = min(base + grab, n_chunks);
+                }
+                if (c >= n_chunks) {
+                    exhausted = true;
+                    break;
+                }
+                const int64_t S = (int64_t)counters[C_STARTS];
+                const int64_t s0 = chunk_s0[c];
+                const int64_t bnd = (s0 + 1 + lane <= S) ? soff[s0 + 1 + lane] : INT64_MAX;
+                const int64_t gl = (int64_t)c * WARP_CHUNK + lane;
+                int cnt = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1) {
+                    const int64_t bv = __shfl_sync(FULL, bnd, cnt + step - 1);
+                    if (bv <= gl) cnt += step;
+                }
+                cs = (int32_t)(s0 + cnt);
+                valid = (int)min((int64_t)WARP_CHUNK, (int64_t)counters[C_TOTAL] - (int64_t)c * WARP_CHUNK);
+                p = 0;
+            }
+            const int avail = valid - p;
+            const int rank = __popc(idle & lt_mask);
+            const int src = min(p + rank, WARP_CHUNK - 1);
+            const int32_t s_new = __shfl_sync(FULL, cs, src);
+            if (((idle >> lane) & 1u) && rank < avail) {
+                g = (int64_t)c * WARP_CHUNK + p + rank;
+                node0 = (uint32_t)starts[s_new];
+                const uint2 od = nod[node0];
+                off = od.x;
+                deg = od.y;
+                k = 0;
+                W = 1.f;
+                a32 = F2Acc();
+                active = true;
+            }
+            p += min(avail, __popc(idle));
+            idle = __ballot_sync(FULL, !active);
+        }
+        if (!__any_sync(FULL, active)) break;
+        bool done = false;
+        if (active) {
+            done = !(fabsf(W) > wc32);
+            if (!done) {
+                uint32_t w0, w1;
+                walk_words<false>(u, k, (uint32_t)g, (uint32_t)((uint64_t)g >> 32), req, key, w0, w1);
+                const float t = __ldg(rm + deg);
+                a32.add(__fmul_rn(__fmul_rn(zeta[k + 2], W), t));
+                if (k + 2 >= K || deg == 0) {
+                    done = true;
+                } else {
+                    const uint32_t b = __umulhi(w0, deg);
+                    const uint2 nx = load_od(eod + (int64_t)off + b, policy_evict_first());
+                    W = __fmul_rn(W, t);
+                    off = nx.x;
+                    deg = nx.y;
+                    ++k;
+                    ++my_steps;
+                }
+            }
+            if (done) {
+                if (!isfinite(W) || !isfinite(a32.hi)) flags |= 1u;
+                ++my_walks;
+                active = false;
+            }
+        }
+        rb_n = rb.push(done, node0, make_float2(a32.hi, a32.lo), rb_n, lane, lt_mask, acc);
+    }
+    rb.flush(rb_n, lane, acc);
+    unsigned long long ws = my_steps, ww = my_walks;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        ws += __shfl_down_sync(FULL, ws, d);
+        ww += __shfl_down_sync(FULL, ww, d);
+        flags |= __shfl_down_sync(FULL, flags, d);
+    }
+    if (lane == 0) {
+        atomicAdd(&counters[C_STEPS], ws);
+        atomicAdd(&counters[C_WALKS], ww);
         if (flags) atomicOr(&counters[C_FLAGS], (unsigned long long)flags);
     }
 }
@@ -303,25 +451,19 @@ __global__ void finalize_q(int64_t n, double* __restrict__ acc, const int64_t* _
         acc[i] = nw[i] > 0 ? acc[i] / (double)nw[i] : 0.0;
 }
 
-// y = zeta_0 v + zeta_1 r + A' q (Algorithm 3, last step); VEC lanes per row,
-// the row loop uniform across the warp so every lane reaches the shuffles.
-template <int VEC>
+// y = zeta_0 v + zeta_1 r + A' q (Algorithm 3, last step); a warp covers 32
+// consecutive rows (warp_row_sums).
 __global__ void action_epilogue(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                                 const float* __restrict__ val, double gamma, double z0, double z1,
                                 const double* __restrict__ v, const double* __restrict__ r,
                                 const double* __restrict__ q, double* __restrict__ y) {
-    constexpr int GROUPS = 32 / VEC;
-    const int lane = threadIdx.x & 31, sub = lane % VEC;
+    const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t base = warp * GROUPS; base < n; base += nwarps * GROUPS) {
-        const int64_t row = base + lane / VEC;
-        double s = 0.0;
-        if (row < n)
-            for (int64_t p = rp[row] + sub; p < rp[row + 1]; p += VEC) s += (val ? (double)val[p] : 1.0) * q[col[p]];
-#pragma unroll
-        for (int d = VEC / 2; d > 0; d >>= 1) s += __shfl_down_sync(0xffffffffu, s, d, VEC);
-        if (sub == 0 && row < n) y[row] = z0 * (v ? v[row] : 1.0) + z1 * r[row] + gamma * s;
+    for (int64_t base = warp * 32; base < n; base += nwarps * 32) {
+        const double s = warp_row_sums<32>(base, n, rp, col, val, q);
+        const int64_t row = base + lane;
+        if (row < n) y[row] = z0 * (v ? v[row] : 1.0) + z1 * r[row] + gamma * s;
     }
 }
 
@@ -396,14 +538,20 @@ template <bool F64, bool WEIGHTED, bool DENSE>
 __device__ int diag_walk(const DiagTable& t, uint32_t k0, int64_t g, int from, const Rec<F64>* __restrict__ rec,
                          const int32_t* __restrict__ col, const WEntry* __restrict__ went,
                          const typename std::conditional<F64, double, float>::type* zeta, int K, double wc,
-                         uint2 key, uint32_t req, unsigned long long& steps, uint32_t& flags) {
+                         float wc32, uint2 key, uint32_t req, unsigned long long& steps, uint32_t& flags) {
     using real = typename std::conditional<F64, double, float>::type;
     uint32_t l = k0;
     real W = (real)1;
+    uint4 u = make_uint4(0u, 0u, 0u, 0u);
     const uint32_t glo = (uint32_t)g, ghi = (uint32_t)((uint64_t)g >> 32);
     for (int k = 0; k <= K; ++k) {
-        if (!((double)fabs(W) > wc)) break;
-        const uint4 u = philox4x32_10(make_uint4((uint32_t)k, glo, ghi, req), key);
+        if constexpr (F64) {
+            if (!(fabs(W) > wc)) break;
+        } else {
+            if (!(fabsf(W) > wc32)) break;   // same decision as (double)|W| > W_c
+        }
+        uint32_t w0, w1;
+        walk_words<WEIGHTED>(u, k, glo, ghi, req, key, w0, w1);
         const Rec<F64> x = rec[l];
         if (k >= from) {
             double term;
@@ -413,7 +561,7 @@ __device__ int diag_walk(const DiagTable& t, uint32_t k0, int64_t g, int from, c
         }
         if (k + 2 >= K || x.deg == 0) break;
         real mult;
-        const uint32_t nl = next_state<F64, WEIGHTED>(x, u, col, went, mult);
+        const uint32_t nl = next_state<F64, WEIGHTED>(x, w0, w1, col, went, mult);
         if constexpr (F64) W = __dmul_rn(W, mult);
         else W = __fmul_rn(W, mult);
         l = nl;
@@ -428,7 +576,7 @@ __global__ void __launch_bounds__(256) walk_diag_kernel(
     const Rec<F64>* __restrict__ rec, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
     const float* __restrict__ val, const WEntry* __restrict__ went, const int32_t* __restrict__ starts,
     const int64_t* __restrict__ woff, const int64_t* __restrict__ nw, const uint8_t* __restrict__ want, double gamma,
-    const double* __restrict__ zeta_g, int K, double wc, uint2 key, uint32_t req, int64_t n, int cap_log2,
+    const double* __restrict__ zeta_g, int K, double wc, float wc32, uint2 key, uint32_t req, int64_t n, int cap_log2,
     double* __restrict__ dacc, unsigned long long* __restrict__ counters) {
     using real = typename std::conditional<F64, double, float>::type;
     extern __shared__ double smem_d[];
@@ -469,7 +617,7 @@ __global__ void __launch_bounds__(256) walk_diag_kernel(
             for (;;) {
                 if (pending) {
                     const int f = diag_walk<F64, WEIGHTED, DENSE>(t, k0, g0 + w, from, rec, col, went, zeta, K, wc,
-                                                                  key, req, steps, flags);
+                                                                  wc32, key, req, steps, flags);
                     if (f < 0) pending = false;
                     else from = f;
                 }
@@ -669,6 +817,14 @@ static void keep_pool_memory() {
     done[dev] = true;
 }
 
+// The largest float f <= W_c: for every float x, x > f exactly when
+// (double)x > W_c, so the walks take the cutoff decision in float32.
+static float cutoff_f32(double wc) {
+    float f = (float)wc;
+    if ((double)f > wc) f = nextafterf(f, -INFINITY);
+    return f;
+}
+
 static uint2 philox_key(uint64_t seed) { return make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)); }
 
 static mcf_status finish_stats(mcf_stats* stats, const unsigned long long* counters, cudaEvent_t e0, cudaEvent_t e1,
@@ -686,13 +842,94 @@ static mcf_status finish_stats(mcf_stats* stats, const unsigned long long* count
     return MCF_OK;
 }
 
+// Every walk step reads one random 4- to 16-byte word; by default the L2
+// fetches a whole line from DRAM on such a miss, moving about four times the
+// bytes the step uses.  The walk kernels are launched with the context's L2
+// fetch granularity lowered to 32 bytes (a per-context launch limit), and the
+// previous value is put back right after the launch.
+struct ScopedL2Fetch {
+    size_t old = 0;
+    bool set = false;
+    explicit ScopedL2Fetch(int bytes) {
+        if (bytes <= 0) return;
+        if (cudaDeviceGetLimit(&old, cudaLimitMaxL2FetchGranularity) == cudaSuccess &&
+            cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, (size_t)bytes) == cudaSuccess)
+            set = true;
+        cudaGetLastError();
+    }
+    ~ScopedL2Fetch() {
+        if (set) cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, old);
+        cudaGetLastError();
+    }
+};
+
+// Launch-shape knobs of the walk kernels, read once from the environment:
+// MCF_WALK_MINB (resident 256-thread blocks per SM the register budget is
+// sized for: 5, 6 or 8), MCF_WALK_GRAB (32-walk chunks a warp takes per atomic)
+// and MCF_WALK_TC_PATH (0 disables the per-entry record layout).
+struct WalkTuning {
+    int minb = 5;
+    int grab = 4;
+    bool tc_path = true;   // MCF_WALK_TC_PATH=0 selects the general node-record kernel for v = 1
+    int l2_fetch = 32;     // MCF_L2_FETCH_BYTES: L2 fetch granularity for walk kernels (0 = leave as is)
+};
+static const WalkTuning& walk_tuning() {
+    static WalkTuning t = [] {
+        WalkTuning w;
+        if (const char* e = getenv("MCF_L2_FETCH_BYTES")) w.l2_fetch = std::max(0, std::min(128, atoi(e)));
+        if (const char* e = getenv("MCF_WALK_TC_PATH")) w.tc_path = atoi(e) != 0;
+        if (const char* e = getenv("MCF_WALK_MINB")) w.minb = atoi(e) >= 8 ? 8 : (atoi(e) <= 5 ? 5 : 6);
+        if (const char* e = getenv("MCF_WALK_GRAB")) w.grab = std::max(1, std::min(64, atoi(e)));
+        return w;
+    }();
+    return t;
+}
+
+template <bool F64, bool WEIGHTED, int MINB>
+static void launch_action_walks_t(const mcf_graph* g, const Prep& P, uint32_t* chunk_s0, int K, double wc, uint2 key,
+                                  uint32_t req, double* acc, cudaStream_t st) {
+    auto kern = walk_action_kernel<F64, WEIGHTED, MINB>;
+    const int grid = persistent_grid(kern, 256, 0);
+    ScopedL2Fetch fetch(walk_tuning().l2_fetch);
+    kern<<<grid, 256, 0, st>>>((const Rec<F64>*)P.rec, g->col_idx, g->went, P.starts, P.soff, chunk_s0, P.zeta, K,
+                               wc, cutoff_f32(wc), key, req, walk_tuning().grab, acc, P.counters);
+}
+
+// Builds the graph's node_od / edge_od arrays on first use (binary, nnz < 2^32).
+static mcf_status ensure_edge_od(mcf_graph* g, cudaStream_t st) {
+    if (g->edge_od) return MCF_OK;
+    uint2 *nod = nullptr, *eod = nullptr;
+    if (cudaMalloc(&nod, (size_t)std::max<int64_t>(g->n, 1) * sizeof(uint2)) != cudaSuccess ||
+        cudaMalloc(&eod, (size_t)std::max<int64_t>(g->nnz, 1) * sizeof(uint2)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(nod);
+        cudaFree(eod);
+        return fail(MCF_ERR_OOM, "device allocation of the per-entry walk records failed");
+    }
+    build_node_od<<<grid_for(g->n, 256), 256, 0, st>>>(g->n, g->row_ptr, nod);
+    build_edge_od<<<grid_for(g->nnz, 256), 256, 0, st>>>(g->nnz, g->col_idx, nod, eod);
+    MCF_CUDA_TRY(cudaGetLastError());
+    g->node_od = nod;
+    g->edge_od = eod;
+    return MCF_OK;
+}
+
+template <int MINB>
+static void launch_tc_walks_t(const mcf_graph* g, const Prep& P, const float* rm, uint32_t* chunk_s0, int K,
+                              double wc, uint2 key, uint32_t req, double* acc, cudaStream_t st) {
+    auto kern = walk_tc_kernel<MINB>;
+    const int grid = persistent_grid(kern, 256, 0);
+    ScopedL2Fetch fetch(walk_tuning().l2_fetch);
+    kern<<<grid, 256, 0, st>>>(g->node_od, g->edge_od, rm, P.starts, P.soff, chunk_s0, P.zeta, K, cutoff_f32(wc), key,
+                               req, walk_tuning().grab, acc, P.counters);
+}
+
 template <bool F64, bool WEIGHTED>
 static void launch_action_walks(const mcf_graph* g, const Prep& P, uint32_t* chunk_s0, int K, double wc, uint2 key,
                                 uint32_t req, double* acc, cudaStream_t st) {
-    auto kern = walk_action_kernel<F64, WEIGHTED>;
-    const int grid = persistent_grid(kern, 256, 0);
-    kern<<<grid, 256, 0, st>>>((const Rec<F64>*)P.rec, g->col_idx, g->went, P.starts, P.soff, chunk_s0, P.zeta, K,
-                               wc, key, req, acc, P.counters);
+    if (walk_tuning().minb == 8) launch_action_walks_t<F64, WEIGHTED, 8>(g, P, chunk_s0, K, wc, key, req, acc, st);
+    else if (walk_tuning().minb == 5) launch_action_walks_t<F64, WEIGHTED, 5>(g, P, chunk_s0, K, wc, key, req, acc, st);
+    else launch_action_walks_t<F64, WEIGHTED, 6>(g, P, chunk_s0, K, wc, key, req, acc, st);
 }
 
 static mcf_status solve_action(mcf_graph* g, const mcf_params* p, const double* v, double* y, mcf_stats* stats,
@@ -731,6 +968,7 @@ static mcf_status solve_action(mcf_graph* g, const mcf_params* p, const double* 
         if (K >= 2) {
             // walk ids are bounded by N_s + n (rounding) or walks_per_node * n
             const int64_t max_walks = p->walks_per_node > 0 ? p->walks_per_node * n : p->n_walks + n;
+            if (max_walks >= ((int64_t)1 << 36)) return fail(MCF_ERR_INVALID_ARG, "more than 2^36 walks per solve");
             const int64_t max_chunks = max_walks / WARP_CHUNK + 2;
             uint32_t* chunk_s0;
             MCF_TRY(sc.get(&chunk_s0, max_chunks));
@@ -741,22 +979,25 @@ static mcf_status solve_action(mcf_graph* g, const mcf_params* p, const double* 
                 cudaEventRecord(e0, st);
             }
             const uint2 key = philox_key(p->seed);
-            if (f64 && g->weighted) launch_action_walks<true, true>(g, P, chunk_s0, K, p->w_cutoff, key, p->request_id, acc, st);
+            const bool tc_path = ones && !f64 && !g->weighted && g->nnz < ((int64_t)1 << 32) && walk_tuning().tc_path;
+            if (tc_path) {
+                MCF_TRY(ensure_edge_od(g, st));
+                float* rm;
+                MCF_TRY(sc.get(&rm, g->max_degree + 1));
+                degree_table<<<grid_for(g->max_degree + 1, 256), 256, 0, st>>>(g->max_degree, gamma, rm);
+                if (walk_tuning().minb == 8) launch_tc_walks_t<8>(g, P, rm, chunk_s0, K, p->w_cutoff, key, p->request_id, acc, st);
+                else if (walk_tuning().minb == 5) launch_tc_walks_t<5>(g, P, rm, chunk_s0, K, p->w_cutoff, key, p->request_id, acc, st);
+                else launch_tc_walks_t<6>(g, P, rm, chunk_s0, K, p->w_cutoff, key, p->request_id, acc, st);
+            } else if (f64 && g->weighted) launch_action_walks<true, true>(g, P, chunk_s0, K, p->w_cutoff, key, p->request_id, acc, st);
             else if (f64) launch_action_walks<true, false>(g, P, chunk_s0, K, p->w_cutoff, key, p->request_id, acc, st);
             else if (g->weighted) launch_action_walks<false, true>(g, P, chunk_s0, K, p->w_cutoff, key, p->request_id, acc, st);
             else launch_action_walks<false, false>(g, P, chunk_s0, K, p->w_cutoff, key, p->request_id, acc, st);
             if (stats) cudaEventRecord(e1, st);
         }
         finalize_q<<<grid_for(n, 256), 256, 0, st>>>(n, acc, P.nw);
-        const double avg = (double)g->nnz / (double)n;
         const double z0 = p->coeffs[0], z1 = K >= 1 ? p->coeffs[1] : 0.0;
-        const int blocks = num_sms() * 8;
-        if (avg <= 6)
-            action_epilogue<4><<<blocks, 256, 0, st>>>(n, g->row_ptr, g->col_idx, g->values, gamma, z0, z1, v_dev, P.r, acc, y_dev);
-        else if (avg <= 24)
-            action_epilogue<8><<<blocks, 256, 0, st>>>(n, g->row_ptr, g->col_idx, g->values, gamma, z0, z1, v_dev, P.r, acc, y_dev);
-        else
-            action_epilogue<32><<<blocks, 256, 0, st>>>(n, g->row_ptr, g->col_idx, g->values, gamma, z0, z1, v_dev, P.r, acc, y_dev);
+        action_epilogue<<<grid_for(n, 256), 256, 0, st>>>(n, g->row_ptr, g->col_idx, g->values, gamma, z0, z1, v_dev,
+                                                          P.r, acc, y_dev);
         MCF_CUDA_TRY(cudaGetLastError());
     }
     if (!y_on_dev && n > 0) MCF_CUDA_TRY(cudaMemcpyAsync(y, y_dev, n * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -780,9 +1021,10 @@ static mcf_status launch_diag(const mcf_graph* g, const Prep& P, const uint8_t* 
     const size_t smem = (size_t)cap * (DENSE ? sizeof(double) : sizeof(double) + sizeof(int32_t));
     MCF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = persistent_grid(kern, DIAG_THREADS, smem);
+    ScopedL2Fetch fetch(walk_tuning().l2_fetch);
     kern<<<grid, DIAG_THREADS, smem, st>>>((const Rec<F64>*)P.rec, g->row_ptr, g->col_idx, g->values, g->went,
-                                           P.starts, P.woff, P.nw, want, gamma, P.zeta, K, wc, key, req, g->n,
-                                           DIAG_HASH_LOG2, dacc, P.counters);
+                                           P.starts, P.woff, P.nw, want, gamma, P.zeta, K, wc, cutoff_f32(wc), key, req,
+                                           g->n, DIAG_HASH_LOG2, dacc, P.counters);
     MCF_CUDA_TRY(cudaGetLastError());
     return MCF_OK;
 }
@@ -1039,15 +1281,8 @@ static mcf_status solve_tc_noalloc(int64_t n, int64_t nnz, const int64_t* row_pt
         else launch_action_walks<false, false>(&view, P, chunk_s0, K, p->w_cutoff, key, p->request_id, acc, st);
     }
     finalize_q<<<grid_for(n, 256), 256, 0, st>>>(n, acc, P.nw);
-    const double avg = (double)nnz / (double)n;
     const double z0 = p->coeffs[0], z1 = K >= 1 ? p->coeffs[1] : 0.0;
-    const int blocks = num_sms() * 8;
-    if (avg <= 6)
-        action_epilogue<4><<<blocks, 256, 0, st>>>(n, row_ptr, col_idx, nullptr, gamma, z0, z1, nullptr, P.r, acc, y);
-    else if (avg <= 24)
-        action_epilogue<8><<<blocks, 256, 0, st>>>(n, row_ptr, col_idx, nullptr, gamma, z0, z1, nullptr, P.r, acc, y);
-    else
-        action_epilogue<32><<<blocks, 256, 0, st>>>(n, row_ptr, col_idx, nullptr, gamma, z0, z1, nullptr, P.r, acc, y);
+    action_epilogue<<<grid_for(n, 256), 256, 0, st>>>(n, row_ptr, col_idx, nullptr, gamma, z0, z1, nullptr, P.r, acc, y);
     MCF_CUDA_TRY(cudaGetLastError());
     return MCF_OK;
 }
