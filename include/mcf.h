@@ -158,6 +158,106 @@ mcf_status mcf_subgraph_centrality(mcf_graph_t g, const mcf_params* params, cons
  * Errors: MCF_ERR_INVALID_ARG (gamma <= 0, rho >= 1, K too large), as mcf_action. */
 mcf_status mcf_katz(mcf_graph_t g, double gamma, int32_t K, const mcf_params* params, double* y, mcf_stats* stats);
 
+/* ------------------------------------------------------------------ batches */
+
+typedef enum {
+    MCF_QUERY_TOTAL_COMMUNICABILITY = 0, /* f(A')1 (Eq. total_comm)                          */
+    MCF_QUERY_KATZ = 1,                  /* (I - gamma A)^{-1} 1 as a Neumann series (Sec. 4.5) */
+    MCF_QUERY_SUBGRAPH_CENTRALITY = 2,   /* diag f(A'), all nodes or a subset (Sec. 3.3)    */
+    MCF_QUERY_ACTION = 3                 /* f(A')v (Algorithm 3)                            */
+} mcf_query_kind;
+
+/* One request of a batch.  Every field means what it means for the single
+ * call of the same kind (mcf_total_communicability, mcf_katz,
+ * mcf_subgraph_centrality, mcf_action); params.stream is ignored. */
+typedef struct {
+    mcf_graph_t graph;
+    int32_t kind;            /* mcf_query_kind                                      */
+    int32_t katz_terms;      /* MCF_QUERY_KATZ: K (0 = from the tail bound)          */
+    double katz_gamma;       /* MCF_QUERY_KATZ: gamma                                */
+    mcf_params params;       /* coefficients, scale, walks, cutoff, seed, request id */
+    const double* v;         /* MCF_QUERY_ACTION: float64[n], host or device         */
+    const int64_t* nodes;    /* MCF_QUERY_SUBGRAPH_CENTRALITY: subset, or NULL       */
+    int64_t n_nodes;
+    double* out;             /* float64[n] (or [n_nodes]), host or device            */
+} mcf_query;
+
+typedef struct mcf_batch* mcf_batch_t;
+
+#define MCF_BATCH_CUDA_GRAPH 1u  /* capture the fused launch sequence in a CUDA graph */
+#define MCF_BATCH_AUTOTUNE 2u    /* time candidate launch shapes once per batch shape and keep the fastest */
+
+/* Plans a batch of queries on any mix of resident graphs.  Total
+ * communicability and Katz queries on binary graphs in MCF_F32W_F64ACC run
+ * together in ONE persistent walk launch; subgraph-centrality queries on
+ * binary graphs in MCF_F32W_F64ACC run together in one diag launch; their
+ * preparation and epilogues are segmented kernels over all of them.  Other
+ * queries (general v, weighted graphs, MCF_F64) run one after another with
+ * the single-query path.  Every query keeps its own walk ids and Philox
+ * streams, so each result equals the single call's result up to float64
+ * summation order.  The plan owns its device scratch; query pointers must
+ * stay valid until mcf_batch_destroy.  `stream` orders the planning work.
+ * Errors: as the single calls; MCF_ERR_INVALID_ARG for an empty batch. */
+mcf_status mcf_batch_create(const mcf_query* queries, int32_t n_queries, uint32_t flags, void* stream,
+                            mcf_batch_t* out);
+
+/* Runs the batch on `stream` (replaying the CUDA graph when captured) and
+ * waits for it.  stats (may be NULL) receives the totals over the batch. */
+mcf_status mcf_batch_run(mcf_batch_t batch, void* stream, mcf_stats* stats);
+
+/* Releases the plan (after synchronising the device). NULL is a no-op. */
+mcf_status mcf_batch_destroy(mcf_batch_t batch);
+
+/* ------------------------------------------------------------------ serving */
+
+typedef struct mcf_server* mcf_server_t;
+
+typedef struct {
+    size_t hbm_budget_bytes;   /* device memory the in-flight requests may use (scratch estimate) */
+    int32_t max_inflight;      /* batches executing concurrently, one stream each (>= 1)         */
+    int32_t max_batch;         /* requests per batch (>= 1)                                      */
+    double batch_window_ms;    /* how long the scheduler waits for more arrivals before it forms
+                                  a batch when a worker is free (0 = form at once)                */
+} mcf_server_config;
+
+typedef struct {
+    int64_t submitted, completed, rejected, batches;
+    int64_t walk_steps;        /* over completed requests                          */
+    double p50_ms, p99_ms, max_ms, mean_ms;  /* latency submit -> result ready      */
+    double busy_s;             /* wall time from the first submit to the last completion */
+} mcf_server_stats;
+
+/* Starts a request server on the current device: a scheduler thread that
+ * admits queued requests while their estimated device footprint fits the
+ * budget, groups them into batches (mcf_batch_*), and hands each batch to a
+ * free worker stream.  Requests that arrive while batches are running are
+ * admitted as workers and memory free up, and their batches run on the
+ * device concurrently with the running ones (continuous batching).  Graphs
+ * stay resident; each request keeps its own walk ids and Philox streams, so
+ * its result equals the single call's result.
+ * Errors: MCF_ERR_INVALID_ARG (zero budget, max_inflight < 1), MCF_ERR_CUDA. */
+mcf_status mcf_server_create(const mcf_server_config* config, mcf_server_t* out);
+
+/* Queues a copy of *query (its arrays must stay valid until the request
+ * completes) and returns a ticket.  A request whose footprint alone exceeds
+ * the budget completes immediately with MCF_ERR_ADMISSION. */
+mcf_status mcf_server_submit(mcf_server_t s, const mcf_query* query, uint64_t* ticket);
+
+/* *done = 1 once the ticket's result is in query->out; *result is its status. */
+mcf_status mcf_server_poll(mcf_server_t s, uint64_t ticket, int32_t* done, mcf_status* result);
+
+/* Waits (at most timeout_s seconds; < 0 = no limit) for a ticket.  Returns
+ * MCF_ERR_TIMEOUT if it is still running; *result is the request's status and
+ * *latency_ms its submit-to-completion time (either may be NULL). */
+mcf_status mcf_server_wait(mcf_server_t s, uint64_t ticket, double timeout_s, mcf_status* result,
+                           double* latency_ms);
+
+/* Counters and latency percentiles over the completed requests. */
+mcf_status mcf_server_get_stats(mcf_server_t s, mcf_server_stats* out);
+
+/* Waits for every queued request, then stops the server. NULL is a no-op. */
+mcf_status mcf_server_destroy(mcf_server_t s);
+
 /* ---------------------------------------------------------- allocation-free */
 
 /* Size limits of mcf_total_communicability_noalloc (its fixed scratch array). */

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "mcf_internal.cuh"
 
 namespace mcf {
@@ -76,7 +78,7 @@ constexpr int CHUNKS_PER_GRAB = 4;  // chunks a warp takes per atomic
 
 enum Counter { C_NEXT = 0, C_STEPS = 1, C_WALKS = 2, C_FLAGS = 3, C_TOTAL = 4, C_STARTS = 5, N_COUNTERS = 8 };
 
-__device__ double block_sum_d(double v) {
+__device__ __forceinline__ double block_sum_d(double v) {
     __shared__ double part[32];
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
@@ -222,5 +224,166 @@ struct WalkResults {
         return n;
     }
 };
+
+// ---------------------------------------------------------------- state transition
+// SelectNextState (Section 3.1) for the state whose record is x: position
+// within the row from the Philox block u; returns the next state and the
+// signed multiplier sign(a_{l l'}) * sum_j |a'_lj|.
+template <bool F64, bool WEIGHTED>
+__device__ __forceinline__ uint32_t next_state(const Rec<F64>& x, uint32_t w0, uint32_t w1,
+                                               const int32_t* __restrict__ col, const WEntry* __restrict__ went,
+                                               typename std::conditional<F64, double, float>::type& mult) {
+    const uint32_t b = __umulhi(w0, x.deg);
+    mult = x.mult;
+    if constexpr (!WEIGHTED) {
+        return (uint32_t)__ldg(col + (int64_t)x.off + b);
+    } else {
+        const float xr = __fmul_rn(__uint2float_rn(w1 >> 8), 5.9604644775390625e-08f);
+        WEntry e = went[(int64_t)x.off + b];
+        if (!(xr < e.prob)) e = went[(int64_t)x.off + e.alias];
+        if (e.val < 0.0f) mult = -mult;
+        return (uint32_t)e.col;
+    }
+}
+
+// ---------------------------------------------------------------- RandFunmDiag row Q_k
+struct DiagTable {
+    double* val;       // global, per CTA: n (dense) or cap (hash) entries
+    int32_t* key;      // shared (hash): node of each slot, -1 when free
+    int32_t* used;     // shared (hash): slots in use, in insertion order
+    int32_t cap_log2;
+    int32_t limit;
+    int* count;        // shared (hash): number of slots in use
+};
+
+__device__ __forceinline__ uint32_t hash_slot(uint32_t x, int cap_log2) {
+    return (x * 0x9E3779B1u) >> (32 - cap_log2);
+}
+
+// Slot of node l (inserting it if absent); -1 when the table is full.
+template <bool DENSE>
+__device__ __forceinline__ int q_slot(const DiagTable& t, uint32_t l) {
+    if constexpr (DENSE) {
+        return (int)l;
+    } else {
+        const uint32_t mask = (1u << t.cap_log2) - 1u;
+        uint32_t h = hash_slot(l, t.cap_log2);
+        for (uint32_t probe = 0; probe <= mask; ++probe, h = (h + 1) & mask) {
+            const int32_t k = t.key[h];
+            if (k == (int32_t)l) return (int)h;
+            if (k == -1) {
+                if (*(volatile int*)t.count >= t.limit) return -1;
+                const int32_t prev = atomicCAS(&t.key[h], -1, (int32_t)l);
+                if (prev == -1) {
+                    const int pos = atomicAdd(t.count, 1);
+                    t.used[pos] = (int32_t)h;
+                    return (int)h;
+                }
+                if (prev == (int32_t)l) return (int)h;
+            }
+        }
+        return -1;
+    }
+}
+
+template <bool DENSE>
+__device__ __forceinline__ double q_get(const DiagTable& t, uint32_t l) {
+    // row values are updated by L2 reductions: read them from L2, not L1
+    if constexpr (DENSE) {
+        return __ldcg(t.val + l);
+    } else {
+        const uint32_t mask = (1u << t.cap_log2) - 1u;
+        uint32_t h = hash_slot(l, t.cap_log2);
+        for (uint32_t probe = 0; probe <= mask; ++probe, h = (h + 1) & mask) {
+            const int32_t k = t.key[h];
+            if (k == (int32_t)l) return __ldcg(t.val + h);
+            if (k == -1) return 0.0;
+        }
+        return 0.0;
+    }
+}
+
+// Runs walk g from column k0, recording the visits of steps >= from (from >= 1:
+// the step-0 visit is added in bulk) and counting the transitions of steps
+// >= count_from.  Returns -1 when the walk is complete, else the step whose
+// visit could not be stored.
+template <bool F64, bool WEIGHTED, bool DENSE>
+__device__ int diag_walk(const DiagTable& t, uint32_t k0, int64_t g, int from, int count_from,
+                         const Rec<F64>* __restrict__ rec,
+                         const int32_t* __restrict__ col, const WEntry* __restrict__ went,
+                         const typename std::conditional<F64, double, float>::type* zeta, int K, double wc,
+                         float wc32, uint2 key, uint32_t req, uint32_t& steps, uint32_t& flags) {
+    using real = typename std::conditional<F64, double, float>::type;
+    uint32_t l = k0;
+    real W = (real)1;
+    uint4 u = make_uint4(0u, 0u, 0u, 0u);
+    const uint32_t glo = (uint32_t)g, ghi = (uint32_t)((uint64_t)g >> 32);
+    for (int k = 0; k <= K; ++k) {
+        if constexpr (F64) {
+            if (!(fabs(W) > wc)) break;
+        } else {
+            if (!(fabsf(W) > wc32)) break;   // same decision as (double)|W| > W_c
+        }
+        uint32_t w0, w1;
+        walk_words<WEIGHTED>(u, k, glo, ghi, req, key, w0, w1);
+        const Rec<F64> x = rec[l];
+        if (k >= from) {
+            const int h = q_slot<DENSE>(t, l);
+            if (h < 0) return k;
+            double term;
+            if constexpr (F64) term = __dmul_rn(zeta[k + 2], W);
+            else term = (double)__fmul_rn(zeta[k + 2], W);
+            atomicAdd(&t.val[h], term);
+        }
+        if (k + 2 >= K || x.deg == 0) break;
+        real mult;
+        const uint32_t nl = next_state<F64, WEIGHTED>(x, w0, w1, col, went, mult);
+        if constexpr (F64) W = __dmul_rn(W, mult);
+        else W = __fmul_rn(W, mult);
+        l = nl;
+        if (k >= count_from) ++steps;
+    }
+    if constexpr (!F64) if (!isfinite(W)) flags |= 1u;
+    return -1;
+}
+
+// d_i += a'_ik <Q_k, C'_i> / N_k for the neighbours i of k (warp per neighbour).
+template <bool DENSE>
+__device__ __forceinline__ void diag_apply(const DiagTable& t, uint32_t k0, int64_t Nk, const int64_t* __restrict__ rp,
+                                           const int32_t* __restrict__ col, const float* __restrict__ val,
+                                           const uint8_t* __restrict__ want, double gamma, double* __restrict__ dacc) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (int64_t p = rp[k0] + wid; p < rp[k0 + 1]; p += nwarp) {
+        const int32_t i = col[p];
+        if (want && !want[i]) continue;
+        double dot = 0.0;
+        if (val) {
+            for (int64_t q = rp[i] + lane; q < rp[i + 1]; q += 32)
+                dot += (double)val[q] * q_get<DENSE>(t, (uint32_t)col[q]);
+        } else {
+            for (int64_t q = rp[i] + lane; q < rp[i + 1]; q += 32) dot += q_get<DENSE>(t, (uint32_t)col[q]);
+        }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) dot += __shfl_down_sync(0xffffffffu, dot, d);
+        if (lane == 0) {
+            const double aik = gamma * (val ? (double)val[p] : 1.0);
+            atomicAdd(&dacc[i], (aik * (gamma * dot)) / (double)Nk);
+        }
+    }
+}
+
+template <bool DENSE>
+__device__ __forceinline__ void diag_clear(const DiagTable& t, int64_t n) {
+    if constexpr (DENSE) {
+        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) __stcg(t.val + i, 0.0);
+    } else {
+        const int c = *t.count;
+        for (int e = threadIdx.x; e < c; e += blockDim.x) {
+            const int h = t.used[e];
+            t.key[h] = -1;
+            __stcg(t.val + h, 0.0);
+        }
+    }
+}
 
 }  // namespace mcf

@@ -10,6 +10,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -478,6 +479,8 @@ mcf_status mcf_gershgorin(mcf_graph_t g, double* bound) {
 mcf_status mcf_spectral_radius(mcf_graph_t g, double tol, int32_t max_iter, double* lambda_max) {
     set_error("");
     if (!g || !lambda_max) return fail(MCF_ERR_INVALID_ARG, "NULL argument");
+    static std::mutex mu;   // one power iteration at a time (it caches its result on the graph)
+    std::lock_guard<std::mutex> lk(mu);
     if (!(tol > 0.0) || max_iter < 1) return fail(MCF_ERR_INVALID_ARG, "tol must be > 0 and max_iter >= 1");
     if (g->n == 0 || g->nnz == 0) {
         *lambda_max = 0.0;

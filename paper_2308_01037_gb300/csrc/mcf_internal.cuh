@@ -4,6 +4,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <stdlib.h>
+
+#include <algorithm>
 #include <string>
 
 #include "../../include/mcf.h"
@@ -149,5 +152,77 @@ struct Scratch {
         return MCF_OK;
     }
 };
+
+// ---------------------------------------------------------------- launch helpers (host)
+inline int grid_for(int64_t work, int threads) {
+    int64_t b = (work + threads - 1) / threads;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)num_sms() * 32));
+}
+
+template <class KernelT>
+inline int persistent_grid(KernelT kernel, int threads, size_t smem) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+    if (per_sm < 1) per_sm = 1;
+    return per_sm * num_sms();
+}
+
+// The largest float f <= W_c: for every float x, x > f exactly when
+// (double)x > W_c, so the walks take the cutoff decision in float32.
+inline float cutoff_f32(double wc) {
+    float f = (float)wc;
+    if ((double)f > wc) f = nextafterf(f, -INFINITY);
+    return f;
+}
+
+inline uint2 philox_key(uint64_t seed) { return make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)); }
+
+// Every walk step reads one random 4- to 16-byte word; by default the L2
+// fetches a whole line from DRAM on such a miss, moving about four times the
+// bytes the step uses.  The walk kernels are launched with the context's L2
+// fetch granularity lowered to 32 bytes (a per-context launch limit), and the
+// previous value is put back right after the launch.
+struct ScopedL2Fetch {
+    size_t old = 0;
+    bool set = false;
+    explicit ScopedL2Fetch(int bytes) {
+        if (bytes <= 0) return;
+        if (cudaDeviceGetLimit(&old, cudaLimitMaxL2FetchGranularity) == cudaSuccess &&
+            cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, (size_t)bytes) == cudaSuccess)
+            set = true;
+        cudaGetLastError();
+    }
+    ~ScopedL2Fetch() {
+        if (set) cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, old);
+        cudaGetLastError();
+    }
+};
+
+// Launch-shape knobs of the walk kernels, read once from the environment:
+// MCF_WALK_MINB (resident 256-thread blocks per SM the register budget is
+// sized for: 5, 6 or 8), MCF_WALK_GRAB (32-walk chunks a warp takes per atomic)
+// and MCF_WALK_TC_PATH (0 disables the per-entry record layout).
+struct WalkTuning {
+    int minb = 5;
+    int grab = 4;
+    bool tc_path = true;   // MCF_WALK_TC_PATH=0 selects the general node-record kernel for v = 1
+    int l2_fetch = 32;     // MCF_L2_FETCH_BYTES: L2 fetch granularity for walk kernels (0 = leave as is)
+};
+inline const WalkTuning& walk_tuning() {
+    static WalkTuning t = [] {
+        WalkTuning w;
+        if (const char* e = getenv("MCF_L2_FETCH_BYTES")) w.l2_fetch = std::max(0, std::min(128, atoi(e)));
+        if (const char* e = getenv("MCF_WALK_TC_PATH")) w.tc_path = atoi(e) != 0;
+        if (const char* e = getenv("MCF_WALK_MINB")) w.minb = atoi(e) >= 8 ? 8 : (atoi(e) <= 5 ? 5 : 6);
+        if (const char* e = getenv("MCF_WALK_GRAB")) w.grab = std::max(1, std::min(64, atoi(e)));
+        return w;
+    }();
+    return t;
+}
+
+// Builds the graph's node_od / edge_od arrays on first use (binary, nnz < 2^32).
+mcf_status ensure_edge_od(mcf_graph* g, cudaStream_t st);
+// Keeps freed stream-ordered scratch in the device's default pool.
+void keep_pool_memory();
 
 }  // namespace mcf

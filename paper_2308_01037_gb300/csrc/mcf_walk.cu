@@ -8,6 +8,7 @@
 #include <stdlib.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
 #include <type_traits>
 
@@ -128,26 +129,6 @@ __global__ void build_records(int64_t n, const int64_t* __restrict__ rp, const d
             x.mult = __double2float_rn(mult);
         }
         rec[i] = x;
-    }
-}
-
-// SelectNextState (Section 3.1) for the state whose record is x: position
-// within the row from the Philox block u; returns the next state and the
-// signed multiplier sign(a_{l l'}) * sum_j |a'_lj|.
-template <bool F64, bool WEIGHTED>
-__device__ __forceinline__ uint32_t next_state(const Rec<F64>& x, uint32_t w0, uint32_t w1,
-                                               const int32_t* __restrict__ col, const WEntry* __restrict__ went,
-                                               typename std::conditional<F64, double, float>::type& mult) {
-    const uint32_t b = __umulhi(w0, x.deg);
-    mult = x.mult;
-    if constexpr (!WEIGHTED) {
-        return (uint32_t)__ldg(col + (int64_t)x.off + b);
-    } else {
-        const float xr = __fmul_rn(__uint2float_rn(w1 >> 8), 5.9604644775390625e-08f);
-        WEntry e = went[(int64_t)x.off + b];
-        if (!(xr < e.prob)) e = went[(int64_t)x.off + e.alias];
-        if (e.val < 0.0f) mult = -mult;
-        return (uint32_t)e.col;
     }
 }
 
@@ -469,137 +450,52 @@ __global__ void action_epilogue(int64_t n, const int64_t* __restrict__ rp, const
 
 // ====================================================================== RandFunmDiag walks
 // One CTA per start column k at a time (taken from an atomic counter).  Its
-// threads run the N_k walks and add zeta_{m+2} W^(m) into row Q_k held in
-// shared memory (a dense array when n is small, else an open-addressing hash
-// keyed by node id).  Then d_i += a'_ik <Q_k, C'_i> / N_k for every neighbour
-// i of k (warp per neighbour, float64 atomics).  A hash that reaches its fill
-// limit stops the inserting walk; the CTA applies and clears Q_k, and the walk
-// is replayed from its first unrecorded visit (walks are deterministic in
-// their Philox counters, and Q_k enters d linearly).
-struct DiagTable {
-    double* val;
-    int32_t* key;
-    int32_t cap_log2;
-    int32_t limit;
-    int* count;
-};
-
-__device__ __forceinline__ uint32_t hash_slot(uint32_t x, int cap_log2) {
-    return (x * 0x9E3779B1u) >> (32 - cap_log2);
-}
-
-template <bool DENSE>
-__device__ __forceinline__ bool q_add(const DiagTable& t, uint32_t l, double v) {
-    if constexpr (DENSE) {
-        atomicAdd(&t.val[l], v);
-        return true;
-    } else {
-        const uint32_t mask = (1u << t.cap_log2) - 1u;
-        uint32_t h = hash_slot(l, t.cap_log2);
-        for (uint32_t probe = 0; probe <= mask; ++probe, h = (h + 1) & mask) {
-            int32_t k = t.key[h];
-            if (k == (int32_t)l) {
-                atomicAdd(&t.val[h], v);
-                return true;
-            }
-            if (k == -1) {
-                if (*(volatile int*)t.count >= t.limit) return false;
-                const int32_t prev = atomicCAS(&t.key[h], -1, (int32_t)l);
-                if (prev == -1) atomicAdd(t.count, 1);
-                if (prev == -1 || prev == (int32_t)l) {
-                    atomicAdd(&t.val[h], v);
-                    return true;
-                }
-            }
-        }
-        return false;
-    }
-}
-
-template <bool DENSE>
-__device__ __forceinline__ double q_get(const DiagTable& t, uint32_t l) {
-    if constexpr (DENSE) {
-        return t.val[l];
-    } else {
-        const uint32_t mask = (1u << t.cap_log2) - 1u;
-        uint32_t h = hash_slot(l, t.cap_log2);
-        for (uint32_t probe = 0; probe <= mask; ++probe, h = (h + 1) & mask) {
-            const int32_t k = t.key[h];
-            if (k == (int32_t)l) return t.val[h];
-            if (k == -1) return 0.0;
-        }
-        return 0.0;
-    }
-}
-
-// Runs walk g from column k, recording the visits of steps >= from.  Returns
-// -1 when the walk is complete, else the step whose visit could not be stored.
-template <bool F64, bool WEIGHTED, bool DENSE>
-__device__ int diag_walk(const DiagTable& t, uint32_t k0, int64_t g, int from, const Rec<F64>* __restrict__ rec,
-                         const int32_t* __restrict__ col, const WEntry* __restrict__ went,
-                         const typename std::conditional<F64, double, float>::type* zeta, int K, double wc,
-                         float wc32, uint2 key, uint32_t req, unsigned long long& steps, uint32_t& flags) {
-    using real = typename std::conditional<F64, double, float>::type;
-    uint32_t l = k0;
-    real W = (real)1;
-    uint4 u = make_uint4(0u, 0u, 0u, 0u);
-    const uint32_t glo = (uint32_t)g, ghi = (uint32_t)((uint64_t)g >> 32);
-    for (int k = 0; k <= K; ++k) {
-        if constexpr (F64) {
-            if (!(fabs(W) > wc)) break;
-        } else {
-            if (!(fabsf(W) > wc32)) break;   // same decision as (double)|W| > W_c
-        }
-        uint32_t w0, w1;
-        walk_words<WEIGHTED>(u, k, glo, ghi, req, key, w0, w1);
-        const Rec<F64> x = rec[l];
-        if (k >= from) {
-            double term;
-            if constexpr (F64) term = __dmul_rn(zeta[k + 2], W);
-            else term = (double)__fmul_rn(zeta[k + 2], W);
-            if (!q_add<DENSE>(t, l, term)) return k;
-        }
-        if (k + 2 >= K || x.deg == 0) break;
-        real mult;
-        const uint32_t nl = next_state<F64, WEIGHTED>(x, w0, w1, col, went, mult);
-        if constexpr (F64) W = __dmul_rn(W, mult);
-        else W = __fmul_rn(W, mult);
-        l = nl;
-        if (k >= from) ++steps;
-    }
-    if constexpr (!F64) if (!isfinite(W)) flags |= 1u;
-    return -1;
-}
-
+// threads run the N_k walks (thread t runs walks t, t + blockDim, ...) and
+// add zeta_{m+2} W^(m) into row Q_k.  Q_k's float64 values live in a
+// per-CTA region of global memory and are updated with float64 reductions,
+// which the L2 executes (GB300's SM float64 pipe is narrow, and shared-memory
+// float64 atomics loop on it).  Small graphs index the region densely by
+// node; larger ones use an open-addressing hash whose keys, and the list of
+// slots in use, live in shared memory.  Every walk visits k at step 0 with
+// weight 1, so those N_k visits are added once as N_k * zeta_2.  After the
+// walks, d_i += a'_ik <Q_k, C'_i> / N_k for every neighbour i of k (warp per
+// neighbour).  A hash that reaches its fill limit stops the inserting walk;
+// once every thread has stopped or finished, the CTA applies and clears the
+// partial row and the stopped walks resume from their first unrecorded visit
+// (walks are deterministic in their Philox counters and Q_k enters d
+// linearly).
 template <bool F64, bool WEIGHTED, bool DENSE>
 __global__ void __launch_bounds__(256) walk_diag_kernel(
     const Rec<F64>* __restrict__ rec, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
     const float* __restrict__ val, const WEntry* __restrict__ went, const int32_t* __restrict__ starts,
     const int64_t* __restrict__ woff, const int64_t* __restrict__ nw, const uint8_t* __restrict__ want, double gamma,
     const double* __restrict__ zeta_g, int K, double wc, float wc32, uint2 key, uint32_t req, int64_t n, int cap_log2,
-    double* __restrict__ dacc, unsigned long long* __restrict__ counters) {
+    double* __restrict__ qval, double* __restrict__ dacc, unsigned long long* __restrict__ counters) {
     using real = typename std::conditional<F64, double, float>::type;
-    extern __shared__ double smem_d[];
+    extern __shared__ int32_t smem_i[];
     __shared__ real zeta[MCF_MAX_COEFFS];
     __shared__ int64_t cur;
     __shared__ int count;
     for (int k = threadIdx.x; k <= K; k += blockDim.x) zeta[k] = (real)zeta_g[k];
     DiagTable t;
-    const int cap = DENSE ? (int)n : (1 << cap_log2);
-    t.val = smem_d;
-    t.key = reinterpret_cast<int32_t*>(smem_d + cap);
+    const int64_t cap = DENSE ? n : ((int64_t)1 << cap_log2);
+    t.val = qval + (int64_t)blockIdx.x * cap;
+    t.key = smem_i;
+    t.used = smem_i + (DENSE ? 0 : cap);
     t.cap_log2 = cap_log2;
-    t.limit = DENSE ? cap : (cap - cap / 4 - (int)blockDim.x);
+    t.limit = DENSE ? 0 : (int)(cap - cap / 4 - (int64_t)blockDim.x);
     t.count = &count;
-    for (int i = threadIdx.x; i < cap; i += blockDim.x) {
-        t.val[i] = 0.0;
+    for (int64_t i = threadIdx.x; i < cap; i += blockDim.x) {
+        __stcg(t.val + i, 0.0);
         if (!DENSE) t.key[i] = -1;
     }
     if (threadIdx.x == 0) count = 0;
     const int64_t S = (int64_t)counters[C_STARTS];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    unsigned long long steps = 0, walks = 0;
-    uint32_t flags = 0;
+    uint32_t steps = 0, walks = 0, flags = 0;
+    // the step-0 visit (weight 1 at k): taken when 1 > W_c, as in the walks
+    bool visit0;
+    if constexpr (F64) visit0 = 1.0 > wc;
+    else visit0 = 1.0f > wc32;
     __syncthreads();
     for (;;) {
         if (threadIdx.x == 0) cur = (int64_t)atomicAdd(&counters[C_NEXT], 1ull);
@@ -609,74 +505,60 @@ __global__ void __launch_bounds__(256) walk_diag_kernel(
         const uint32_t k0 = (uint32_t)starts[s];
         const int64_t Nk = nw[k0];
         const int64_t g0 = woff[k0];
-        for (int64_t w0 = 0; w0 < Nk; w0 += blockDim.x) {
-            const int64_t w = w0 + threadIdx.x;
-            bool pending = w < Nk;
-            int from = 0;
-            if (pending) ++walks;
-            for (;;) {
-                if (pending) {
-                    const int f = diag_walk<F64, WEIGHTED, DENSE>(t, k0, g0 + w, from, rec, col, went, zeta, K, wc,
-                                                                  wc32, key, req, steps, flags);
-                    if (f < 0) pending = false;
-                    else from = f;
-                }
-                if (!__syncthreads_or(pending)) break;
-                // table full: apply the partial row Q_k, clear it, resume
-                for (int64_t p = rp[k0] + wid; p < rp[k0 + 1]; p += nwarp) {
-                    const int32_t i = col[p];
-                    if (want && !want[i]) continue;
-                    double dot = 0.0;
-                    for (int64_t q = rp[i] + lane; q < rp[i + 1]; q += 32)
-                        dot += __dmul_rn(gamma * (val ? (double)val[q] : 1.0), q_get<DENSE>(t, (uint32_t)col[q]));
-#pragma unroll
-                    for (int d = 16; d > 0; d >>= 1) dot += __shfl_down_sync(0xffffffffu, dot, d);
-                    if (lane == 0) atomicAdd(&dacc[i], (gamma * (val ? (double)val[p] : 1.0) * dot) / (double)Nk);
-                }
-                __syncthreads();
-                for (int i = threadIdx.x; i < cap; i += blockDim.x) {
-                    t.val[i] = 0.0;
-                    if (!DENSE) t.key[i] = -1;
-                }
-                if (threadIdx.x == 0) count = 0;
-                __syncthreads();
-            }
+        if (threadIdx.x == 0 && visit0 && K >= 2) {
+            double z2;
+            if constexpr (F64) z2 = zeta[2];
+            else z2 = (double)zeta[2];
+            const int h = q_slot<DENSE>(t, k0);     // empty table: always succeeds
+            atomicAdd(&t.val[h], (double)Nk * z2);
         }
         __syncthreads();
-        // d_i += a'_ik <Q_k, C'_i> / N_k for the neighbours i of k
-        for (int64_t p = rp[k0] + wid; p < rp[k0 + 1]; p += nwarp) {
-            const int32_t i = col[p];
-            if (want && !want[i]) continue;
-            double dot = 0.0;
-            for (int64_t q = rp[i] + lane; q < rp[i + 1]; q += 32)
-                dot += __dmul_rn(gamma * (val ? (double)val[q] : 1.0), q_get<DENSE>(t, (uint32_t)col[q]));
-#pragma unroll
-            for (int d = 16; d > 0; d >>= 1) dot += __shfl_down_sync(0xffffffffu, dot, d);
-            if (lane == 0) atomicAdd(&dacc[i], (gamma * (val ? (double)val[p] : 1.0) * dot) / (double)Nk);
-        }
-        __syncthreads();
-        if (DENSE) {
-            // clear only what this start touched: the visited nodes are the
-            // rows read above plus k itself; a full clear is cheap for small n
-            for (int i = threadIdx.x; i < cap; i += blockDim.x) t.val[i] = 0.0;
-        } else {
-            for (int i = threadIdx.x; i < cap; i += blockDim.x) {
-                t.val[i] = 0.0;
-                t.key[i] = -1;
+        int64_t w = threadIdx.x;
+        int from = 1, cfrom = 0;
+        walks += (uint32_t)(Nk > (int64_t)threadIdx.x ? (Nk - 1 - threadIdx.x) / blockDim.x + 1 : 0);
+        for (;;) {
+            bool stopped = false;
+            while (w < Nk) {
+                const int f = diag_walk<F64, WEIGHTED, DENSE>(t, k0, g0 + w, from, cfrom, rec, col, went, zeta, K, wc,
+                                                              wc32, key, req, steps, flags);
+                if (f >= 0) {
+                    from = f;
+                    cfrom = f;
+                    stopped = true;
+                    break;
+                }
+                w += blockDim.x;
+                from = 1;
+                cfrom = 0;
             }
+            if (!__syncthreads_or(stopped)) break;
+            // the table filled up: apply the partial row, clear it, resume
+            __threadfence_block();
+            diag_apply<DENSE>(t, k0, Nk, rp, col, val, want, gamma, dacc);
+            __syncthreads();
+            diag_clear<DENSE>(t, n);
+            __syncthreads();
+            if (threadIdx.x == 0) count = 0;
+            __syncthreads();
         }
+        __threadfence_block();
+        diag_apply<DENSE>(t, k0, Nk, rp, col, val, want, gamma, dacc);
+        __syncthreads();
+        diag_clear<DENSE>(t, n);
+        __syncthreads();
         if (threadIdx.x == 0) count = 0;
-        __syncthreads();
     }
+    const int lane = threadIdx.x & 31;
+    unsigned long long ws = steps, ww = walks;
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
-        steps += __shfl_down_sync(0xffffffffu, steps, d);
-        walks += __shfl_down_sync(0xffffffffu, walks, d);
+        ws += __shfl_down_sync(0xffffffffu, ws, d);
+        ww += __shfl_down_sync(0xffffffffu, ww, d);
         flags |= __shfl_down_sync(0xffffffffu, flags, d);
     }
     if (lane == 0) {
-        atomicAdd(&counters[C_STEPS], steps);
-        atomicAdd(&counters[C_WALKS], walks);
+        atomicAdd(&counters[C_STEPS], ws);
+        atomicAdd(&counters[C_WALKS], ww);
         if (flags) atomicOr(&counters[C_FLAGS], (unsigned long long)flags);
     }
 }
@@ -728,19 +610,6 @@ static mcf_status check_params(const mcf_graph* g, const mcf_params* p) {
     if (p->precision == MCF_F32W_F64ACC && g->nnz >= ((int64_t)1 << 32))
         return fail(MCF_ERR_UNSUPPORTED, "float32 walk records need nnz < 2^32");
     return MCF_OK;
-}
-
-static int grid_for(int64_t work, int threads) {
-    int64_t b = (work + threads - 1) / threads;
-    return (int)std::max<int64_t>(1, std::min<int64_t>(b, (int64_t)num_sms() * 32));
-}
-
-template <class KernelT>
-static int persistent_grid(KernelT kernel, int threads, size_t smem) {
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
-    if (per_sm < 1) per_sm = 1;
-    return per_sm * num_sms();
 }
 
 // Everything a solve prepares before its walks: r, the chain's allocation,
@@ -803,7 +672,7 @@ static mcf_status prepare(const mcf_graph* g, const mcf_params* p, double gamma,
 
 // Keeps freed stream-ordered scratch in the device's default pool instead of
 // returning it to the driver at every synchronisation.
-static void keep_pool_memory() {
+void keep_pool_memory() {
     static bool done[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
@@ -816,16 +685,6 @@ static void keep_pool_memory() {
     cudaGetLastError();
     done[dev] = true;
 }
-
-// The largest float f <= W_c: for every float x, x > f exactly when
-// (double)x > W_c, so the walks take the cutoff decision in float32.
-static float cutoff_f32(double wc) {
-    float f = (float)wc;
-    if ((double)f > wc) f = nextafterf(f, -INFINITY);
-    return f;
-}
-
-static uint2 philox_key(uint64_t seed) { return make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)); }
 
 static mcf_status finish_stats(mcf_stats* stats, const unsigned long long* counters, cudaEvent_t e0, cudaEvent_t e1,
                                cudaStream_t st) {
@@ -842,49 +701,6 @@ static mcf_status finish_stats(mcf_stats* stats, const unsigned long long* count
     return MCF_OK;
 }
 
-// Every walk step reads one random 4- to 16-byte word; by default the L2
-// fetches a whole line from DRAM on such a miss, moving about four times the
-// bytes the step uses.  The walk kernels are launched with the context's L2
-// fetch granularity lowered to 32 bytes (a per-context launch limit), and the
-// previous value is put back right after the launch.
-struct ScopedL2Fetch {
-    size_t old = 0;
-    bool set = false;
-    explicit ScopedL2Fetch(int bytes) {
-        if (bytes <= 0) return;
-        if (cudaDeviceGetLimit(&old, cudaLimitMaxL2FetchGranularity) == cudaSuccess &&
-            cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, (size_t)bytes) == cudaSuccess)
-            set = true;
-        cudaGetLastError();
-    }
-    ~ScopedL2Fetch() {
-        if (set) cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, old);
-        cudaGetLastError();
-    }
-};
-
-// Launch-shape knobs of the walk kernels, read once from the environment:
-// MCF_WALK_MINB (resident 256-thread blocks per SM the register budget is
-// sized for: 5, 6 or 8), MCF_WALK_GRAB (32-walk chunks a warp takes per atomic)
-// and MCF_WALK_TC_PATH (0 disables the per-entry record layout).
-struct WalkTuning {
-    int minb = 5;
-    int grab = 4;
-    bool tc_path = true;   // MCF_WALK_TC_PATH=0 selects the general node-record kernel for v = 1
-    int l2_fetch = 32;     // MCF_L2_FETCH_BYTES: L2 fetch granularity for walk kernels (0 = leave as is)
-};
-static const WalkTuning& walk_tuning() {
-    static WalkTuning t = [] {
-        WalkTuning w;
-        if (const char* e = getenv("MCF_L2_FETCH_BYTES")) w.l2_fetch = std::max(0, std::min(128, atoi(e)));
-        if (const char* e = getenv("MCF_WALK_TC_PATH")) w.tc_path = atoi(e) != 0;
-        if (const char* e = getenv("MCF_WALK_MINB")) w.minb = atoi(e) >= 8 ? 8 : (atoi(e) <= 5 ? 5 : 6);
-        if (const char* e = getenv("MCF_WALK_GRAB")) w.grab = std::max(1, std::min(64, atoi(e)));
-        return w;
-    }();
-    return t;
-}
-
 template <bool F64, bool WEIGHTED, int MINB>
 static void launch_action_walks_t(const mcf_graph* g, const Prep& P, uint32_t* chunk_s0, int K, double wc, uint2 key,
                                   uint32_t req, double* acc, cudaStream_t st) {
@@ -896,7 +712,11 @@ static void launch_action_walks_t(const mcf_graph* g, const Prep& P, uint32_t* c
 }
 
 // Builds the graph's node_od / edge_od arrays on first use (binary, nnz < 2^32).
-static mcf_status ensure_edge_od(mcf_graph* g, cudaStream_t st) {
+mcf_status ensure_edge_od(mcf_graph* g, cudaStream_t st) {
+    // built once per graph; concurrent callers on other streams must not see
+    // the pointers before the arrays are complete
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
     if (g->edge_od) return MCF_OK;
     uint2 *nod = nullptr, *eod = nullptr;
     if (cudaMalloc(&nod, (size_t)std::max<int64_t>(g->n, 1) * sizeof(uint2)) != cudaSuccess ||
@@ -909,6 +729,7 @@ static mcf_status ensure_edge_od(mcf_graph* g, cudaStream_t st) {
     build_node_od<<<grid_for(g->n, 256), 256, 0, st>>>(g->n, g->row_ptr, nod);
     build_edge_od<<<grid_for(g->nnz, 256), 256, 0, st>>>(g->nnz, g->col_idx, nod, eod);
     MCF_CUDA_TRY(cudaGetLastError());
+    MCF_CUDA_TRY(cudaStreamSynchronize(st));
     g->node_od = nod;
     g->edge_od = eod;
     return MCF_OK;
@@ -1009,22 +830,36 @@ static mcf_status solve_action(mcf_graph* g, const mcf_params* p, const double* 
     return MCF_OK;
 }
 
-constexpr int DIAG_THREADS = 256;
-constexpr int DIAG_HASH_LOG2 = 13;                       // 8192 slots = 96 KB of shared memory
-constexpr int64_t DIAG_DENSE_MAX = 12288;                // dense row Q_k up to 96 KB
+constexpr int64_t DIAG_DENSE_MAX = 16384;   // dense row Q_k (global memory) up to this many nodes
 
+// Launch shape of the diag kernel: threads per CTA follow the walks per start
+// (64 .. 256) and the hash holds about four visits per walk of a start (at
+// most 2^14 slots); a start with more distinct visits flushes its partial row.
 template <bool F64, bool WEIGHTED, bool DENSE>
 static mcf_status launch_diag(const mcf_graph* g, const Prep& P, const uint8_t* want, double gamma, int K, double wc,
-                              uint2 key, uint32_t req, double* dacc, cudaStream_t st) {
+                              uint2 key, uint32_t req, int64_t nk_hint, double* dacc, Scratch& sc, cudaStream_t st) {
     auto kern = walk_diag_kernel<F64, WEIGHTED, DENSE>;
-    const int cap = DENSE ? (int)g->n : (1 << DIAG_HASH_LOG2);
-    const size_t smem = (size_t)cap * (DENSE ? sizeof(double) : sizeof(double) + sizeof(int32_t));
-    MCF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int grid = persistent_grid(kern, DIAG_THREADS, smem);
+    int threads = 256;
+    if (nk_hint > 0 && nk_hint <= 64) threads = 64;
+    else if (nk_hint > 0 && nk_hint <= 128) threads = 128;
+    int cap_log2 = 0;
+    size_t smem = 0;
+    int64_t cap = g->n;
+    if (!DENSE) {
+        const int64_t want_slots = std::max<int64_t>(4 * std::max<int64_t>(nk_hint, 1) * 4, 4 * threads);
+        cap_log2 = 10;
+        while (cap_log2 < 14 && ((int64_t)1 << cap_log2) < want_slots) ++cap_log2;
+        cap = (int64_t)1 << cap_log2;
+        smem = (size_t)cap * 2 * sizeof(int32_t);
+    }
+    MCF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 0)));
+    const int grid = persistent_grid(kern, threads, smem);
+    double* qval;
+    MCF_TRY(sc.get(&qval, (size_t)grid * (size_t)std::max<int64_t>(cap, 1)));
     ScopedL2Fetch fetch(walk_tuning().l2_fetch);
-    kern<<<grid, DIAG_THREADS, smem, st>>>((const Rec<F64>*)P.rec, g->row_ptr, g->col_idx, g->values, g->went,
-                                           P.starts, P.woff, P.nw, want, gamma, P.zeta, K, wc, cutoff_f32(wc), key, req,
-                                           g->n, DIAG_HASH_LOG2, dacc, P.counters);
+    kern<<<grid, threads, smem, st>>>((const Rec<F64>*)P.rec, g->row_ptr, g->col_idx, g->values, g->went, P.starts,
+                                      P.woff, P.nw, want, gamma, P.zeta, K, wc, cutoff_f32(wc), key, req, g->n,
+                                      cap_log2, qval, dacc, P.counters);
     MCF_CUDA_TRY(cudaGetLastError());
     return MCF_OK;
 }
@@ -1092,7 +927,8 @@ static mcf_status solve_diag(mcf_graph* g, const mcf_params* p, const int64_t* n
             const uint2 key = philox_key(p->seed);
             const bool dense = n <= DIAG_DENSE_MAX;
             mcf_status rc;
-#define MCF_DIAG(F, W, D) rc = launch_diag<F, W, D>(g, P, want, gamma, K, p->w_cutoff, key, p->request_id, dacc, st)
+            const int64_t nk_hint = p->walks_per_node > 0 ? p->walks_per_node : std::max<int64_t>(1, p->n_walks / std::max<int64_t>(n, 1));
+#define MCF_DIAG(F, W, D) rc = launch_diag<F, W, D>(g, P, want, gamma, K, p->w_cutoff, key, p->request_id, nk_hint, dacc, sc, st)
             if (f64) {
                 if (g->weighted) { if (dense) MCF_DIAG(true, true, true); else MCF_DIAG(true, true, false); }
                 else { if (dense) MCF_DIAG(true, false, true); else MCF_DIAG(true, false, false); }

@@ -43,6 +43,35 @@ class mcf_params(ctypes.Structure):
                 ("deterministic", ctypes.c_int32), ("stream", ctypes.c_void_p)]
 
 
+class mcf_query(ctypes.Structure):
+    _fields_ = [("graph", ctypes.c_void_p), ("kind", ctypes.c_int32), ("katz_terms", ctypes.c_int32),
+                ("katz_gamma", ctypes.c_double), ("params", mcf_params), ("v", ctypes.c_void_p),
+                ("nodes", ctypes.c_void_p), ("n_nodes", ctypes.c_int64), ("out", ctypes.c_void_p)]
+
+
+MCF_QUERY_TOTAL_COMMUNICABILITY = 0
+MCF_QUERY_KATZ = 1
+MCF_QUERY_SUBGRAPH_CENTRALITY = 2
+MCF_QUERY_ACTION = 3
+MCF_BATCH_CUDA_GRAPH = 1
+MCF_BATCH_AUTOTUNE = 2
+
+
+class mcf_server_config(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("batch_window_ms", ctypes.c_double)]
+
+
+class mcf_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("rejected", ctypes.c_int64),
+                ("batches", ctypes.c_int64), ("walk_steps", ctypes.c_int64), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("busy_s", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class mcf_stats(ctypes.Structure):
     _fields_ = [("walks", ctypes.c_int64), ("walk_steps", ctypes.c_int64), ("kernel_ms", ctypes.c_double),
                 ("flags", ctypes.c_uint32)]
@@ -63,6 +92,15 @@ SIGNATURES = {
     "mcf_total_communicability": ([_P, _P, _P, _P], ctypes.c_int),
     "mcf_subgraph_centrality": ([_P, _P, _P, _I64, _P, _P], ctypes.c_int),
     "mcf_katz": ([_P, _D, _I32, _P, _P, _P], ctypes.c_int),
+    "mcf_batch_create": ([_P, _I32, _U32, _P, _P], ctypes.c_int),
+    "mcf_batch_run": ([_P, _P, _P], ctypes.c_int),
+    "mcf_batch_destroy": ([_P], ctypes.c_int),
+    "mcf_server_create": ([_P, _P], ctypes.c_int),
+    "mcf_server_submit": ([_P, _P, _P], ctypes.c_int),
+    "mcf_server_poll": ([_P, ctypes.c_uint64, _P, _P], ctypes.c_int),
+    "mcf_server_wait": ([_P, ctypes.c_uint64, _D, _P, _P], ctypes.c_int),
+    "mcf_server_get_stats": ([_P, _P], ctypes.c_int),
+    "mcf_server_destroy": ([_P], ctypes.c_int),
     "mcf_total_communicability_noalloc": ([_I64, _I64, _P, _P, _P, _P], ctypes.c_int),
     "mcf_last_error": ([], ctypes.c_char_p),
     "mcf_version": ([], ctypes.c_char_p),
@@ -246,6 +284,133 @@ def mcf_katz(g: GraphHandle, gamma, K=0, out=None, device_out=None, stats=False,
     _check(load().mcf_katz(g.handle, float(gamma), int(K), ctypes.byref(p), yp,
                            ctypes.byref(st) if stats else None))
     return (y, st.as_dict()) if stats else y
+
+
+def _query_struct(q):
+    """mcf_query for a dict (see mcf_batch_create) plus the objects it points into."""
+    g = q["graph"]
+    kind = q["kind"]
+    nodes = q.get("nodes")
+    m = len(nodes) if (kind == MCF_QUERY_SUBGRAPH_CENTRALITY and nodes is not None) else g.n
+    out = q.get("out")
+    if out is None:
+        out = _output(None, m, q.get("device_out"))
+    op, ko = _ptr(out, np.float64)
+    vp, kv = _ptr(q.get("v"), np.float64)
+    npt, kn = _ptr(nodes, np.int64)
+    pkw = {k: q[k] for k in ("scale", "n_walks", "walks_per_node", "w_cutoff", "seed", "request_id", "precision")
+           if k in q}
+    p, kc = _params(q.get("coeffs", [1.0]), **pkw)
+    st = mcf_query(g.handle, kind, int(q.get("katz_terms", 0)), float(q.get("katz_gamma", 0.0)), p, vp, npt,
+                   int(0 if nodes is None else len(nodes)), op)
+    return st, out, [ko, kv, kn, kc, g]
+
+
+class BatchHandle:
+    """Owns an mcf_batch_t and keeps the arrays its queries point to alive."""
+
+    def __init__(self, handle, keep, outputs):
+        self.handle = handle
+        self._keep = keep
+        self.outputs = outputs
+
+    def close(self):
+        if self.handle:
+            load().mcf_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mcf_batch_create(queries, flags=0, stream=None):
+    """Plans a batch.  ``queries``: list of dicts with keys graph (GraphHandle),
+    kind (MCF_QUERY_*), coeffs, out (array; allocated when absent), and the
+    mcf_params keywords (scale, n_walks, walks_per_node, w_cutoff, seed,
+    request_id, precision), plus katz_gamma/katz_terms, v, nodes."""
+    arr = (mcf_query * len(queries))()
+    keep, outputs = [], []
+    for i, q in enumerate(queries):
+        arr[i], out, k = _query_struct(q)
+        outputs.append(out)
+        keep += k
+    h = ctypes.c_void_p()
+    _check(load().mcf_batch_create(arr, len(queries), int(flags), stream, ctypes.byref(h)))
+    return BatchHandle(h.value, keep + [arr], outputs)
+
+
+def mcf_batch_run(b: BatchHandle, stream=None, stats=False):
+    st = mcf_stats()
+    _check(load().mcf_batch_run(b.handle, stream, ctypes.byref(st) if stats else None))
+    return (b.outputs, st.as_dict()) if stats else b.outputs
+
+
+def mcf_batch_destroy(b: BatchHandle):
+    b.close()
+
+
+class ServerHandle:
+    """Owns an mcf_server_t and the arrays of its pending requests."""
+
+    def __init__(self, handle):
+        self.handle = handle
+        self.pending = {}
+
+    def close(self):
+        if self.handle:
+            load().mcf_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mcf_server_create(hbm_budget_bytes, max_inflight=2, max_batch=16, batch_window_ms=0.0) -> ServerHandle:
+    cfg = mcf_server_config(int(hbm_budget_bytes), int(max_inflight), int(max_batch), float(batch_window_ms))
+    h = ctypes.c_void_p()
+    _check(load().mcf_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return ServerHandle(h.value)
+
+
+def mcf_server_submit(s: ServerHandle, query: dict) -> int:
+    """Queues a request (dict as for mcf_batch_create); returns its ticket."""
+    st, out, keep = _query_struct(query)
+    t = ctypes.c_uint64()
+    _check(load().mcf_server_submit(s.handle, ctypes.byref(st), ctypes.byref(t)))
+    s.pending[t.value] = (out, keep + [st])
+    return t.value
+
+
+def mcf_server_poll(s: ServerHandle, ticket: int):
+    done, res = ctypes.c_int32(), ctypes.c_int()
+    _check(load().mcf_server_poll(s.handle, ctypes.c_uint64(ticket), ctypes.byref(done), ctypes.byref(res)))
+    return bool(done.value), res.value
+
+
+def mcf_server_wait(s: ServerHandle, ticket: int, timeout_s: float = -1.0):
+    """Waits for a ticket; returns (output array, latency in ms); raises on a failed request."""
+    res, lat = ctypes.c_int(), ctypes.c_double()
+    _check(load().mcf_server_wait(s.handle, ctypes.c_uint64(ticket), float(timeout_s), ctypes.byref(res),
+                                  ctypes.byref(lat)))
+    _check(res.value)
+    out, _ = s.pending.pop(ticket)
+    return out, lat.value
+
+
+def mcf_server_get_stats(s: ServerHandle) -> dict:
+    st = mcf_server_stats()
+    _check(load().mcf_server_get_stats(s.handle, ctypes.byref(st)))
+    return st.as_dict()
+
+
+def mcf_server_destroy(s: ServerHandle):
+    s.close()
 
 
 def mcf_total_communicability_noalloc(n, row_ptr, col_idx, coeffs, out, **kw):

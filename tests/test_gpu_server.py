@@ -1,0 +1,118 @@
+"""The request server (mcf_server_*): continuous batching over resident graphs.
+
+Requests submitted concurrently are grouped into batches that run on several
+streams at once; each request keeps its own walk ids, so its result must equal
+the single call's (parity tolerance 1e-12 relative) whatever it was batched
+with.  Admission by device footprint and the latency counters are checked too.
+"""
+import threading
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import reference as R
+from paper_2308_01037_gb300 import inputs as I
+from paper_2308_01037_gb300 import mcf as M
+
+pytestmark = pytest.mark.gpu
+
+RTOL, ATOL = 1e-12, 1e-13
+
+
+@pytest.fixture(scope="module")
+def pool():
+    gs = [I.rmat(10, 16, seed=11), I.rmat(12, 16, seed=12), I.barabasi_albert(3000, 4, 13)]
+    out = []
+    for g in gs:
+        h = M.mcf_create_graph(g.n, g.row_ptr, g.col_idx)
+        out.append((g, h, 1.0 / R.lambda_max(g)))
+    return out
+
+
+def request(pool, i, rng):
+    g, h, gam = pool[i % len(pool)]
+    kind = [M.MCF_QUERY_TOTAL_COMMUNICABILITY, M.MCF_QUERY_KATZ, M.MCF_QUERY_SUBGRAPH_CENTRALITY,
+            M.MCF_QUERY_ACTION][i % 4]
+    base = dict(graph=h, kind=kind, seed=1000 + i, request_id=i, precision=M.MCF_F32W_F64ACC)
+    c = R.exp_coeffs(30)
+    if kind == M.MCF_QUERY_TOTAL_COMMUNICABILITY:
+        base.update(coeffs=c, scale=gam, n_walks=20 * g.n, w_cutoff=1e-6)
+    elif kind == M.MCF_QUERY_KATZ:
+        base.update(katz_gamma=0.85 * gam, katz_terms=0, walks_per_node=4)
+    elif kind == M.MCF_QUERY_SUBGRAPH_CENTRALITY:
+        base.update(coeffs=c, scale=gam, walks_per_node=40,
+                    nodes=rng.choice(g.n, size=min(64, g.n), replace=False).astype(np.int64))
+    else:
+        base.update(coeffs=c, scale=gam, n_walks=10 * g.n, v=rng.standard_normal(g.n))
+    return base
+
+
+def single(q):
+    keys = ("scale", "n_walks", "walks_per_node", "w_cutoff", "seed", "request_id", "precision")
+    kw = {k: q[k] for k in keys if k in q}
+    if q["kind"] == M.MCF_QUERY_TOTAL_COMMUNICABILITY:
+        return M.mcf_total_communicability(q["graph"], q["coeffs"], **kw)
+    if q["kind"] == M.MCF_QUERY_KATZ:
+        return M.mcf_katz(q["graph"], q["katz_gamma"], q["katz_terms"], **kw)
+    if q["kind"] == M.MCF_QUERY_SUBGRAPH_CENTRALITY:
+        return M.mcf_subgraph_centrality(q["graph"], q["coeffs"], nodes=q["nodes"], **kw)
+    return M.mcf_action(q["graph"], q["v"], q["coeffs"], **kw)
+
+
+def test_results_in_the_mix_equal_results_alone(pool):
+    rng = np.random.default_rng(0)
+    qs = [request(pool, i, rng) for i in range(48)]
+    srv = M.mcf_server_create(hbm_budget_bytes=8 << 30, max_inflight=3, max_batch=8, batch_window_ms=1.0)
+    tickets = [None] * len(qs)
+
+    def client(lo, hi):
+        for i in range(lo, hi):
+            tickets[i] = M.mcf_server_submit(srv, qs[i])
+
+    th = [threading.Thread(target=client, args=(k * 12, (k + 1) * 12)) for k in range(4)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    outs = [M.mcf_server_wait(srv, t, timeout_s=120.0) for t in tickets]
+    st = M.mcf_server_get_stats(srv)
+    srv.close()
+    assert st["completed"] == len(qs) and st["rejected"] == 0
+    assert st["batches"] >= 2 and 0 < st["p50_ms"] <= st["p99_ms"] <= st["max_ms"]
+    for q, (out, lat) in zip(qs, outs):
+        ref = single(q)
+        err = np.abs(np.asarray(out) - ref)
+        assert np.all(err <= RTOL * np.abs(ref) + ATOL)
+        assert lat > 0
+
+
+def test_admission_by_memory_budget(pool):
+    g, h, gam = pool[1]
+    srv = M.mcf_server_create(hbm_budget_bytes=1 << 20, max_inflight=1, max_batch=4)
+    t = M.mcf_server_submit(srv, dict(graph=h, kind=M.MCF_QUERY_TOTAL_COMMUNICABILITY, coeffs=R.exp_coeffs(10),
+                                      scale=gam, n_walks=1000))
+    done, res = M.mcf_server_poll(srv, t)
+    assert done and res == 5   # MCF_ERR_ADMISSION
+    with pytest.raises(M.McfError):
+        M.mcf_server_wait(srv, t)
+    assert M.mcf_server_get_stats(srv)["rejected"] == 1
+    srv.close()
+
+
+def test_requests_queue_until_memory_frees(pool):
+    """A budget that fits one request at a time still serves them all, one batch each."""
+    g, h, gam = pool[0]
+    c = R.exp_coeffs(20)
+    qs = [dict(graph=h, kind=M.MCF_QUERY_TOTAL_COMMUNICABILITY, coeffs=c, scale=gam, n_walks=10 * g.n, seed=i,
+               request_id=i) for i in range(6)]
+    srv = M.mcf_server_create(hbm_budget_bytes=(112 * g.n + g.n + (4 << 20)), max_inflight=2, max_batch=8)
+    tickets = [M.mcf_server_submit(srv, q) for q in qs]
+    outs = [M.mcf_server_wait(srv, t, timeout_s=60.0)[0] for t in tickets]
+    st = M.mcf_server_get_stats(srv)
+    srv.close()
+    assert st["batches"] == len(qs)
+    for q, out in zip(qs, outs):
+        ref = single(q)
+        assert np.all(np.abs(out - ref) <= RTOL * np.abs(ref) + ATOL)
