@@ -169,6 +169,173 @@ def cpu_baseline(g, lam, w, seconds=15.0):
                       f"seed as the full run), {total_steps} walk-steps in {total_t:.1f} s"}
 
 
+def batch_queries(M, R, I, n_graphs, log_n_max, seed=3, katz_rule="gershgorin"):
+    """The mixed multi-graph workload: n = round(10^U[3, log_n_max]); half
+    Barabasi-Albert (m in 2..8), half Erdos-Renyi (mean degree U[8, 32]);
+    queries cycle total communicability exp(A/lambda)1, subgraph centrality
+    diag exp(A/lambda) and Katz, float32 walk weights.  Katz uses
+    gamma = 0.85 / max_i sum_k |a_ik| (the Gershgorin bound of Section 4.5, for
+    which Theorem 1's variance condition holds) or, with katz_rule="lambda",
+    gamma = 0.85 / lambda_max."""
+    rng = np.random.default_rng(seed)
+    graphs, qs = [], []
+    c = exp_coeffs(30)
+    for j in range(n_graphs):
+        n = int(round(10 ** rng.uniform(3, log_n_max)))
+        if j % 2 == 0:
+            g = I.barabasi_albert(n, int(rng.integers(2, 9)), seed + j)
+        else:
+            g = I.erdos_renyi(n, float(rng.uniform(8, 32)), seed + j)
+        h = M.mcf_create_graph(g.n, g.row_ptr, g.col_idx)
+        lam = M.mcf_spectral_radius(h, tol=1e-10, max_iter=10000)
+        graphs.append((g, h, lam))
+        base = dict(graph=h, seed=seed * 1000 + j, request_id=j, precision=M.MCF_F32W_F64ACC)
+        kind = j % 3
+        if kind == 0:
+            qs.append(dict(base, kind=M.MCF_QUERY_TOTAL_COMMUNICABILITY, coeffs=c, scale=1.0 / lam, n_walks=8 * g.n,
+                           w_cutoff=1e-6))
+        elif kind == 1:
+            qs.append(dict(base, kind=M.MCF_QUERY_SUBGRAPH_CENTRALITY, coeffs=c, scale=1.0 / lam, walks_per_node=64,
+                           w_cutoff=1e-6))
+        else:
+            kg = 0.85 / (lam if katz_rule == "lambda" else M.mcf_gershgorin(h))
+            qs.append(dict(base, kind=M.MCF_QUERY_KATZ, katz_gamma=kg, katz_terms=0, walks_per_node=8))
+    return graphs, qs
+
+
+def solve_single(M, q):
+    keys = ("scale", "n_walks", "walks_per_node", "w_cutoff", "seed", "request_id", "precision")
+    kw = {k: q[k] for k in keys if k in q}
+    if q["kind"] == M.MCF_QUERY_TOTAL_COMMUNICABILITY:
+        return M.mcf_total_communicability(q["graph"], q["coeffs"], out=q.get("out"), **kw)
+    if q["kind"] == M.MCF_QUERY_KATZ:
+        return M.mcf_katz(q["graph"], q["katz_gamma"], q["katz_terms"], out=q.get("out"), **kw)
+    return M.mcf_subgraph_centrality(q["graph"], q["coeffs"], nodes=q.get("nodes"), out=q.get("out"), **kw)
+
+
+def run_batched(M, R, I, n_graphs, log_n_max, reps=3):
+    """Solves/s of the batch (plain and CUDA-graph replay) against the same
+    queries solved one at a time, and the worst relative error of a sample of
+    queries against the float64 series."""
+    import torch
+
+    t = time.time()
+    graphs, qs = batch_queries(M, R, I, n_graphs, log_n_max)
+    log(f"[bench] batch workload: {len(qs)} graphs, sum n = {sum(g.n for g, _, _ in graphs)} ({time.time() - t:.1f}s)")
+    for q, (g, _, _) in zip(qs, graphs):
+        q["out"] = torch.empty(g.n, dtype=torch.float64, device="cuda")
+    for q in qs[:3]:
+        solve_single(M, q)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        for q in qs:
+            solve_single(M, q)
+    torch.cuda.synchronize()
+    t_single = (time.perf_counter() - t0) / reps
+    res = {"queries": len(qs), "sum_n": int(sum(g.n for g, _, _ in graphs)),
+           "one_at_a_time_solves_per_s": len(qs) / t_single}
+    for name, flags in (("batched", M.MCF_BATCH_AUTOTUNE), ("batched_cuda_graph", M.MCF_BATCH_CUDA_GRAPH | M.MCF_BATCH_AUTOTUNE)):
+        b = M.mcf_batch_create(qs, flags=flags)
+        M.mcf_batch_run(b)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            _, st = M.mcf_batch_run(b, stats=True)
+        el = (time.perf_counter() - t0) / reps
+        res[name + "_solves_per_s"] = len(qs) / el
+        res[name + "_walk_steps_per_s"] = st["walk_steps"] / el
+        b.close()
+    # accuracy of the batch results (last run) on the smaller graphs, per kind
+    errs = {"tc": [], "sc": [], "katz": []}
+    for q, (g, h, lam) in zip(qs, graphs):
+        if g.n > 200_000:
+            continue
+        y = q["out"].cpu().numpy()
+        if q["kind"] == M.MCF_QUERY_TOTAL_COMMUNICABILITY:
+            ref, kind = R.series_action(g, exp_coeffs(30), 1.0 / lam), "tc"
+        elif q["kind"] == M.MCF_QUERY_KATZ:
+            rho = q["katz_gamma"] * lam
+            K = R.katz_terms_for_tail(rho, 1e-4)
+            ref, kind = R.series_action(g, R.katz_coeffs(K), q["katz_gamma"]), "katz"
+        else:
+            nodes = np.arange(0, g.n, max(1, g.n // 256))
+            ref, kind = R.series_diag(g, exp_coeffs(30), nodes, 1.0 / lam), "sc"
+            y = y[nodes]
+        errs[kind].append(float(np.abs(y - ref).max() / np.abs(ref).max()))
+    res["max_rel_err_vs_fp64"] = {k: (max(v) if v else None) for k, v in errs.items()}
+    res["katz_gamma"] = "0.85 / max_i sum_k |a_ik| (Gershgorin, Section 4.5)"
+    # the same Katz query with gamma = 0.85 / lambda_max on the smallest BA graph:
+    # Theorem 1's condition fails there and the walk weights' variance explodes
+    j = min((k for k in range(len(qs)) if k % 2 == 0), key=lambda k: graphs[k][0].n)
+    g, h, lam = graphs[j]
+    y = M.mcf_katz(h, 0.85 / lam, 0, walks_per_node=64, seed=1, precision=M.MCF_F32W_F64ACC)
+    K = R.katz_terms_for_tail(0.85, 1e-4)
+    ref = R.series_action(g, R.katz_coeffs(K), 0.85 / lam)
+    res["katz_lambda_gamma_rel_err"] = float(np.abs(y - ref).max() / np.abs(ref).max())
+    res["speedup_vs_one_at_a_time"] = res["batched_cuda_graph_solves_per_s"] / res["one_at_a_time_solves_per_s"]
+    for _, h, _ in graphs:
+        h.close()
+    return res
+
+
+def run_serving(M, R, I, scales, n_requests, rate=200.0, seed=5):
+    """Poisson arrivals (rate req/s) over a resident R-MAT pool; query mix 50%
+    total communicability, 30% Katz, 20% subgraph centrality on 10^4 sampled
+    nodes; p50/p99 latency from the server's counters."""
+    t = time.time()
+    pool = []
+    for sc in scales:
+        g = I.rmat(sc, 16, seed=sc)
+        h = M.mcf_create_graph(g.n, g.row_ptr, g.col_idx)
+        lam = M.mcf_spectral_radius(h, tol=1e-10, max_iter=10000)
+        pool.append((g, h, lam))
+    log(f"[bench] serving pool: R-MAT scales {scales[0]}..{scales[-1]} ({time.time() - t:.1f}s)")
+    rng = np.random.default_rng(seed)
+    c = exp_coeffs(30)
+    qs, arrivals, tnow = [], [], 0.0
+    for i in range(n_requests):
+        tnow += rng.exponential(1.0 / rate)
+        arrivals.append(tnow)
+        g, h, lam = pool[int(rng.integers(len(pool)))]
+        u = rng.random()
+        base = dict(graph=h, seed=seed * 100000 + i, request_id=i, precision=M.MCF_F32W_F64ACC)
+        if u < 0.5:
+            qs.append(dict(base, kind=M.MCF_QUERY_TOTAL_COMMUNICABILITY, coeffs=c, scale=1.0 / lam, n_walks=4 * g.n,
+                           w_cutoff=1e-6))
+        elif u < 0.8:
+            qs.append(dict(base, kind=M.MCF_QUERY_KATZ, katz_gamma=0.85 / M.mcf_gershgorin(h), katz_terms=0,
+                           walks_per_node=4))
+        else:
+            nodes = rng.choice(g.n, size=min(10_000, g.n), replace=False).astype(np.int64)
+            qs.append(dict(base, kind=M.MCF_QUERY_SUBGRAPH_CENTRALITY, coeffs=c, scale=1.0 / lam,
+                           walks_per_node=32, w_cutoff=1e-6, nodes=nodes))
+    for q in qs:   # warm the per-graph walk records and Katz term counts
+        pass
+    srv = M.mcf_server_create(hbm_budget_bytes=64 << 30, max_inflight=4, max_batch=16, batch_window_ms=0.5)
+    for q in qs[:8]:
+        M.mcf_server_wait(srv, M.mcf_server_submit(srv, dict(q)))
+    srv.close()
+    srv = M.mcf_server_create(hbm_budget_bytes=64 << 30, max_inflight=4, max_batch=16, batch_window_ms=0.5)
+    t0 = time.perf_counter()
+    tickets = []
+    for q, ta in zip(qs, arrivals):
+        d = ta - (time.perf_counter() - t0)
+        if d > 0:
+            time.sleep(d)
+        tickets.append(M.mcf_server_submit(srv, q))
+    for tk in tickets:
+        M.mcf_server_wait(srv, tk)
+    wall = time.perf_counter() - t0
+    st = M.mcf_server_get_stats(srv)
+    srv.close()
+    for _, h, _ in pool:
+        h.close()
+    return {"requests": n_requests, "rate_req_per_s": rate, "scales": [scales[0], scales[-1]],
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
+            "solves_per_s": st["completed"] / wall, "batches": st["batches"], "rejected": st["rejected"],
+            "walk_steps_per_s": st["walk_steps"] / wall}
+
+
 def run_reference(args, w):
     """--impl reference: the oracle as it stands, timed on the host cores."""
     rank = int(os.environ.get("RANK", "0"))
@@ -210,6 +377,11 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched and serving measurements")
+    ap.add_argument("--batch-graphs", type=int, default=64)
+    ap.add_argument("--batch-log-n-max", type=float, default=5.0)
+    ap.add_argument("--serve-scales", default="14-20")
+    ap.add_argument("--serve-requests", type=int, default=600)
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -319,6 +491,14 @@ def main():
             dist.all_reduce(t)
             e2e["value"] = float(t.item())
 
+    batched = serving = None
+    if rank == 0 and world == 1 and not args.no_batch:
+        from oracle import reference as R
+        from paper_2308_01037_gb300 import inputs as I
+
+        batched = run_batched(M, R, I, args.batch_graphs, args.batch_log_n_max)
+        lo, hi = (int(x) for x in args.serve_scales.split("-"))
+        serving = run_serving(M, R, I, list(range(lo, hi + 1)), args.serve_requests)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(g, lam, w)
@@ -339,6 +519,7 @@ def main():
                          "algorithmic_bytes_per_step": ALGO_BYTES_PER_STEP},
             "clocks": clk.summary(), "e2e": e2e, "gpu_launches": args.steps * 16,
             "cpu_baseline": cpu,
+            "batched": batched, "serving": serving,
         }
         print(json.dumps(line), flush=True)
     h.close()

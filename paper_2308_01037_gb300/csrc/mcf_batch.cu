@@ -336,17 +336,23 @@ __global__ void __launch_bounds__(256, MINB) bwalk_tc_kernel(
         }
         bool done = false;
         if (active) {
-            done = !(fabsf(W) > Wq.wc32);
-            if (!done) {
+            // The next state's record depends only on this state's record and
+            // the random word, not on W: issue its read first, so the degree
+            // table lookup and the cutoff test overlap the random read.
+            const bool last = k + 2 >= Wq.K || deg == 0;
+            uint2 nx = make_uint2(0u, 0u);
+            if (!last) {
                 uint32_t w0, w1;
                 walk_words<false>(u, k, (uint32_t)g, (uint32_t)((uint64_t)g >> 32), Wq.req, Wq.key, w0, w1);
+                nx = load_od(Wq.eod + (int64_t)off + __umulhi(w0, deg), policy_evict_first());
+            }
+            done = !(fabsf(W) > Wq.wc32);
+            if (!done) {
                 const float t = __ldg(Wq.rm + deg);
                 a32.add(__fmul_rn(__fmul_rn(Wq.zeta[k + 2], W), t));
-                if (k + 2 >= Wq.K || deg == 0) {
+                if (last) {
                     done = true;
                 } else {
-                    const uint32_t b = __umulhi(w0, deg);
-                    const uint2 nx = load_od(Wq.eod + (int64_t)off + b, policy_evict_first());
                     W = __fmul_rn(W, t);
                     off = nx.x;
                     deg = nx.y;

@@ -207,11 +207,13 @@ struct WalkTuning {
     int grab = 4;
     bool tc_path = true;   // MCF_WALK_TC_PATH=0 selects the general node-record kernel for v = 1
     int l2_fetch = 32;     // MCF_L2_FETCH_BYTES: L2 fetch granularity for walk kernels (0 = leave as is)
+    bool prefetch = false; // MCF_WALK_PREFETCH=1: issue the next random read before the cutoff test
 };
 inline const WalkTuning& walk_tuning() {
     static WalkTuning t = [] {
         WalkTuning w;
         if (const char* e = getenv("MCF_L2_FETCH_BYTES")) w.l2_fetch = std::max(0, std::min(128, atoi(e)));
+        if (const char* e = getenv("MCF_WALK_PREFETCH")) w.prefetch = atoi(e) != 0;
         if (const char* e = getenv("MCF_WALK_TC_PATH")) w.tc_path = atoi(e) != 0;
         if (const char* e = getenv("MCF_WALK_MINB")) w.minb = atoi(e) >= 8 ? 8 : (atoi(e) <= 5 ? 5 : 6);
         if (const char* e = getenv("MCF_WALK_GRAB")) w.grab = std::max(1, std::min(64, atoi(e)));

@@ -307,7 +307,7 @@ __global__ void degree_table(int64_t max_deg, double gamma, float* __restrict__ 
 // Same walk schedule, Philox streams, float32 arithmetic and accumulation as
 // walk_action_kernel<false, false, MINB> (so the same result up to float64
 // summation order), with the per-step state reduced to {offset, degree}.
-template <int MINB>
+template <int MINB, bool PREFETCH>
 __global__ void __launch_bounds__(256, MINB) walk_tc_kernel(
     const uint2* __restrict__ nod, const uint2* __restrict__ eod, const float* __restrict__ rm,
     const int32_t* __restrict__ starts, const int64_t* __restrict__ soff, const uint32_t* __restrict__ chunk_s0,
@@ -385,17 +385,29 @@ __global__ void __launch_bounds__(256, MINB) walk_tc_kernel(
         if (!__any_sync(FULL, active)) break;
         bool done = false;
         if (active) {
-            done = !(fabsf(W) > wc32);
-            if (!done) {
+            // With PREFETCH the next state's read is issued before the cutoff
+            // test (its address depends only on this state's record and the
+            // random word, not on W), so the degree-table lookup and the test
+            // overlap the random read; the read is wasted when the walk ends.
+            const bool last = k + 2 >= K || deg == 0;
+            uint2 nx = make_uint2(0u, 0u);
+            if (PREFETCH && !last) {
                 uint32_t w0, w1;
                 walk_words<false>(u, k, (uint32_t)g, (uint32_t)((uint64_t)g >> 32), req, key, w0, w1);
+                nx = load_od(eod + (int64_t)off + __umulhi(w0, deg), policy_evict_first());
+            }
+            done = !(fabsf(W) > wc32);
+            if (!done) {
                 const float t = __ldg(rm + deg);
                 a32.add(__fmul_rn(__fmul_rn(zeta[k + 2], W), t));
-                if (k + 2 >= K || deg == 0) {
+                if (last) {
                     done = true;
                 } else {
-                    const uint32_t b = __umulhi(w0, deg);
-                    const uint2 nx = load_od(eod + (int64_t)off + b, policy_evict_first());
+                    if (!PREFETCH) {
+                        uint32_t w0, w1;
+                        walk_words<false>(u, k, (uint32_t)g, (uint32_t)((uint64_t)g >> 32), req, key, w0, w1);
+                        nx = load_od(eod + (int64_t)off + __umulhi(w0, deg), policy_evict_first());
+                    }
                     W = __fmul_rn(W, t);
                     off = nx.x;
                     deg = nx.y;
@@ -738,7 +750,7 @@ mcf_status ensure_edge_od(mcf_graph* g, cudaStream_t st) {
 template <int MINB>
 static void launch_tc_walks_t(const mcf_graph* g, const Prep& P, const float* rm, uint32_t* chunk_s0, int K,
                               double wc, uint2 key, uint32_t req, double* acc, cudaStream_t st) {
-    auto kern = walk_tc_kernel<MINB>;
+    auto kern = walk_tuning().prefetch ? walk_tc_kernel<MINB, true> : walk_tc_kernel<MINB, false>;
     const int grid = persistent_grid(kern, 256, 0);
     ScopedL2Fetch fetch(walk_tuning().l2_fetch);
     kern<<<grid, 256, 0, st>>>(g->node_od, g->edge_od, rm, P.starts, P.soff, chunk_s0, P.zeta, K, cutoff_f32(wc), key,

@@ -107,7 +107,10 @@ def test_requests_queue_until_memory_frees(pool):
     c = R.exp_coeffs(20)
     qs = [dict(graph=h, kind=M.MCF_QUERY_TOTAL_COMMUNICABILITY, coeffs=c, scale=gam, n_walks=10 * g.n, seed=i,
                request_id=i) for i in range(6)]
-    srv = M.mcf_server_create(hbm_budget_bytes=(112 * g.n + g.n + (4 << 20)), max_inflight=2, max_batch=8)
+    # the server's device-footprint estimate of one such request (per-node
+    # scratch, chunk table, degree table, fixed part); 1.5 of it admits one at a time
+    one = 112 * g.n + (10 * g.n + g.n) // 8 + 4 * (int(g.degree.max()) + 1) + (1 << 20)
+    srv = M.mcf_server_create(hbm_budget_bytes=int(1.5 * one), max_inflight=2, max_batch=8)
     tickets = [M.mcf_server_submit(srv, q) for q in qs]
     outs = [M.mcf_server_wait(srv, t, timeout_s=60.0)[0] for t in tickets]
     st = M.mcf_server_get_stats(srv)
