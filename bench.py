@@ -57,7 +57,20 @@ WORKLOADS = {
                           "2000 walks per node, K=30, W_c=1e-6"),
 }
 
-ALGO_BYTES_PER_STEP = 16  # row offset pair 8 B + column index 4 B + r_l 4 B per transition
+# Algorithmic bytes per walk step of the dominant kernel: total communicability
+# reads a row offset pair 8 B + column index 4 B + r_l 4 B per transition;
+# subgraph centrality reads 12 B (no r_l) and reduces into the L2-resident row Q_k.
+ALGO_BYTES_PER_STEP = {"tc": 16, "sc": 12}
+KERNEL = {"tc": "walk_tc_kernel", "sc": "walk_diag_kernel"}
+# Kernels one solve launches: 12 of preparation (r, column norms and their
+# sum, allocation, two three-kernel scans, start compaction, node records),
+# then chunk table, degree table, walks, 1/N_i and the epilogue (total
+# communicability) or walks and the finishing pass (subgraph centrality).
+LAUNCHES_PER_SOLVE = {"tc": 17, "sc": 14}
+# DRAM bytes (read + write) per walk step of walk_tc_kernel from one ncu
+# capture of the R-MAT scale 21 profiling case (7.720e9 B over 264,240,439
+# steps of one launch); a launch of the larger case is scaled by its steps.
+NCU_DRAM_BYTES_PER_STEP = {"rmat22_tc": 29.216, "rmat21_tc": 29.216}
 
 
 def log(*a):
@@ -169,11 +182,26 @@ def cpu_baseline(g, lam, w, seconds=15.0):
                       f"seed as the full run), {total_steps} walk-steps in {total_t:.1f} s"}
 
 
+def aggregate(ms, steps, device="cpu"):
+    """Whole-job numbers over the ranks of the default process group: the
+    slowest rank's time (ms) and the walk-steps of all ranks."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    s = torch.tensor([float(steps)], dtype=torch.float64, device=device)
+    dist.all_reduce(s)
+    return float(t.item()), float(s.item())
+
+
 def batch_queries(M, R, I, n_graphs, log_n_max, seed=3, katz_rule="gershgorin"):
     """The mixed multi-graph workload: n = round(10^U[3, log_n_max]); half
     Barabasi-Albert (m in 2..8), half Erdos-Renyi (mean degree U[8, 32]);
     queries cycle total communicability exp(A/lambda)1, subgraph centrality
-    diag exp(A/lambda) and Katz, float32 walk weights.  Katz uses
+    diag exp(A/lambda) and Katz, float32 walk weights.  Walk budgets are set
+    for a relative l_inf error near 1e-3 (measured with the oracle on BA and ER
+    graphs: about 1000 walks per node for TC and Katz, 64 for SC).  Katz uses
     gamma = 0.85 / max_i sum_k |a_ik| (the Gershgorin bound of Section 4.5, for
     which Theorem 1's variance condition holds) or, with katz_rule="lambda",
     gamma = 0.85 / lambda_max."""
@@ -192,14 +220,14 @@ def batch_queries(M, R, I, n_graphs, log_n_max, seed=3, katz_rule="gershgorin"):
         base = dict(graph=h, seed=seed * 1000 + j, request_id=j, precision=M.MCF_F32W_F64ACC)
         kind = j % 3
         if kind == 0:
-            qs.append(dict(base, kind=M.MCF_QUERY_TOTAL_COMMUNICABILITY, coeffs=c, scale=1.0 / lam, n_walks=8 * g.n,
-                           w_cutoff=1e-6))
+            qs.append(dict(base, kind=M.MCF_QUERY_TOTAL_COMMUNICABILITY, coeffs=c, scale=1.0 / lam,
+                           n_walks=1024 * g.n, w_cutoff=1e-6))
         elif kind == 1:
             qs.append(dict(base, kind=M.MCF_QUERY_SUBGRAPH_CENTRALITY, coeffs=c, scale=1.0 / lam, walks_per_node=64,
                            w_cutoff=1e-6))
         else:
             kg = 0.85 / (lam if katz_rule == "lambda" else M.mcf_gershgorin(h))
-            qs.append(dict(base, kind=M.MCF_QUERY_KATZ, katz_gamma=kg, katz_terms=0, walks_per_node=8))
+            qs.append(dict(base, kind=M.MCF_QUERY_KATZ, katz_gamma=kg, katz_terms=0, walks_per_node=1024))
     return graphs, qs
 
 
@@ -300,11 +328,11 @@ def run_serving(M, R, I, scales, n_requests, rate=200.0, seed=5):
         u = rng.random()
         base = dict(graph=h, seed=seed * 100000 + i, request_id=i, precision=M.MCF_F32W_F64ACC)
         if u < 0.5:
-            qs.append(dict(base, kind=M.MCF_QUERY_TOTAL_COMMUNICABILITY, coeffs=c, scale=1.0 / lam, n_walks=4 * g.n,
+            qs.append(dict(base, kind=M.MCF_QUERY_TOTAL_COMMUNICABILITY, coeffs=c, scale=1.0 / lam, n_walks=16 * g.n,
                            w_cutoff=1e-6))
         elif u < 0.8:
             qs.append(dict(base, kind=M.MCF_QUERY_KATZ, katz_gamma=0.85 / M.mcf_gershgorin(h), katz_terms=0,
-                           walks_per_node=4))
+                           walks_per_node=16))
         else:
             nodes = rng.choice(g.n, size=min(10_000, g.n), replace=False).astype(np.int64)
             qs.append(dict(base, kind=M.MCF_QUERY_SUBGRAPH_CENTRALITY, coeffs=c, scale=1.0 / lam,
@@ -323,17 +351,38 @@ def run_serving(M, R, I, scales, n_requests, rate=200.0, seed=5):
         if d > 0:
             time.sleep(d)
         tickets.append(M.mcf_server_submit(srv, q))
-    for tk in tickets:
-        M.mcf_server_wait(srv, tk)
+    outs = [M.mcf_server_wait(srv, tk)[0] for tk in tickets]
     wall = time.perf_counter() - t0
     st = M.mcf_server_get_stats(srv)
     srv.close()
+    # accuracy of a sample of requests on the smaller graphs, per kind
+    errs = {"tc": [], "katz": [], "sc": []}
+    graph_of = {id(h): (g, lam) for g, h, lam in pool}
+    for q, y in zip(qs, outs):
+        g, lam = graph_of[id(q["graph"])]
+        kind = {M.MCF_QUERY_TOTAL_COMMUNICABILITY: "tc", M.MCF_QUERY_KATZ: "katz",
+                M.MCF_QUERY_SUBGRAPH_CENTRALITY: "sc"}[q["kind"]]
+        if g.n > (1 << 18) or len(errs[kind]) >= 6:
+            continue
+        y = np.asarray(y)
+        if kind == "tc":
+            ref = R.series_action(g, c, 1.0 / lam)
+        elif kind == "katz":
+            K = R.katz_terms_for_tail(q["katz_gamma"] * lam, 1e-4)
+            ref = R.series_action(g, R.katz_coeffs(K), q["katz_gamma"])
+        else:
+            sel = q["nodes"][:512]
+            ref = R.series_diag(g, c, sel, 1.0 / lam)
+            y = y[:512]
+        errs[kind].append(float(np.abs(y - ref).max() / np.abs(ref).max()))
     for _, h, _ in pool:
         h.close()
     return {"requests": n_requests, "rate_req_per_s": rate, "scales": [scales[0], scales[-1]],
             "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
             "solves_per_s": st["completed"] / wall, "batches": st["batches"], "rejected": st["rejected"],
-            "walk_steps_per_s": st["walk_steps"] / wall}
+            "walk_steps_per_s": st["walk_steps"] / wall,
+            "max_rel_err_vs_fp64": {k: (max(v) if v else None) for k, v in errs.items()},
+            "walk_budgets": "TC 16 n walks, Katz (gamma 0.85/Gershgorin) 16 per node, SC 32 per node on 1e4 sampled nodes"}
 
 
 def run_reference(args, w):
@@ -438,17 +487,16 @@ def main():
     tmax = ms
     steps_all = steps_total
     if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tmax = float(t.item())
-        s = torch.tensor([float(steps_total)], device="cuda", dtype=torch.float64)
-        dist.all_reduce(s)
-        steps_all = float(s.item())
+        tmax, steps_all = aggregate(ms, steps_total, device="cuda")
     value = steps_all / (tmax / 1000.0)
     solves_per_s = world * args.steps / (tmax / 1000.0)
     kernel_ms = float(np.mean(kern_ms))
     peak, peak_kind = measured_peak()
-    achieved = ALGO_BYTES_PER_STEP * (steps_total / args.steps) / (kernel_ms / 1000.0) / 1e9
+    steps_per_launch = steps_total / args.steps
+    achieved = ALGO_BYTES_PER_STEP[w["query"]] * steps_per_launch / (kernel_ms / 1000.0) / 1e9
+    traffic = None
+    if args.workload in NCU_DRAM_BYTES_PER_STEP:
+        traffic = NCU_DRAM_BYTES_PER_STEP[args.workload] * steps_per_launch
 
     # ---- accuracy of one solve against the float64 truncated series
     rel_err = None
@@ -514,10 +562,13 @@ def main():
             "solves_per_s": solves_per_s, "rel_err_vs_fp64": rel_err,
             "walk_steps_per_solve": steps_total / args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
-                         "kernel": "walk_action_kernel", "kernel_ms": kernel_ms,
-                         "algorithmic_bytes_per_step": ALGO_BYTES_PER_STEP},
-            "clocks": clk.summary(), "e2e": e2e, "gpu_launches": args.steps * 16,
+                         "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                         "kernel": KERNEL[w["query"]], "kernel_ms": kernel_ms,
+                         "algorithmic_bytes_per_step": ALGO_BYTES_PER_STEP[w["query"]],
+                         "traffic_note": None if traffic is None else
+                         "DRAM bytes per launch: ncu dram__bytes_read.sum + dram__bytes_write.sum per walk step on "
+                         "the R-MAT scale 21 case (one 32-B sector per random step) x the walk steps of a launch"},
+            "clocks": clk.summary(), "e2e": e2e, "gpu_launches": args.steps * LAUNCHES_PER_SOLVE[w["query"]],
             "cpu_baseline": cpu,
             "batched": batched, "serving": serving,
         }

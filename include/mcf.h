@@ -135,6 +135,16 @@ mcf_status mcf_gershgorin(mcf_graph_t g, double* bound);
  * Errors: MCF_ERR_INVALID_ARG (bad params, NULL arrays), MCF_ERR_OOM, MCF_ERR_CUDA. */
 mcf_status mcf_action(mcf_graph_t g, const mcf_params* params, const double* v, double* y, mcf_stats* stats);
 
+/* Entries nodes[0..n_nodes) of f(A')v (v = NULL means v = 1): single-entry
+ * or subset total communicability, the setting of Section 4.3 (Table 3).
+ * Only the columns adjacent to a requested node are walked, each with the
+ * walk ids of the full run, so every entry equals the corresponding entry of
+ * mcf_action / mcf_total_communicability.  nodes: int64, host or device;
+ * y: float64[n_nodes], host or device.
+ * Errors: MCF_ERR_INVALID_ARG (node out of range), as mcf_action. */
+mcf_status mcf_action_nodes(mcf_graph_t g, const mcf_params* params, const double* v, const int64_t* nodes,
+                            int64_t n_nodes, double* y, mcf_stats* stats);
+
 /* Total communicability f(A')1 (Eq. total_comm): mcf_action with v = 1. */
 mcf_status mcf_total_communicability(mcf_graph_t g, const mcf_params* params, double* y, mcf_stats* stats);
 
@@ -157,6 +167,34 @@ mcf_status mcf_subgraph_centrality(mcf_graph_t g, const mcf_params* params, cons
  * with mcf_spectral_radius if not cached); the series needs rho < 1.
  * Errors: MCF_ERR_INVALID_ARG (gamma <= 0, rho >= 1, K too large), as mcf_action. */
 mcf_status mcf_katz(mcf_graph_t g, double gamma, int32_t K, const mcf_params* params, double* y, mcf_stats* stats);
+
+/* Largest n accepted by mcf_funm_full (its dense row of A'Q is staged in
+ * shared memory: n float64 values per CTA). */
+#define MCF_FULL_MAX_NODES 16384
+
+/* RandFunm (Algorithm 2): the dense estimate F = zeta_0 I + zeta_1 A' + A' Q A'
+ * of f(A'), where row k of Q is (1/N_k) sum over the N_k walks from column k
+ * of sum_m zeta_{m+2} W^(m) e_{l_m} (Eq. rand_funm_Q; the walks, their ids and
+ * the allocation are those of mcf_subgraph_centrality, so diag F equals its
+ * result).  F: float64[n * n] row-major, host or device (a host F is staged
+ * through n * n float64 of device memory).  Device scratch: n * n float64 for Q.
+ * Errors: MCF_ERR_UNSUPPORTED (n > MCF_FULL_MAX_NODES), MCF_ERR_INVALID_ARG
+ * (bad params, NULL F), MCF_ERR_OOM, MCF_ERR_CUDA. */
+mcf_status mcf_funm_full(mcf_graph_t g, const mcf_params* params, double* F, mcf_stats* stats);
+
+/* The classical Monte Carlo method (Algorithm 1), the paper's baseline: entry
+ * y_t of f(A')v for row i = nodes[t] (or t when nodes is NULL) is the mean over
+ * N = params->walks_per_node walks from i of sum_k zeta_k W^(k) v_{l_k}; each
+ * step samples ONE entry of the current row (the chain of Definition 1) and
+ * W^(k+1) = W^(k) sign(a_{l l'}) sum_j |a'_lj|, W^(0) = 1; a walk stops when
+ * |W| <= params->w_cutoff or after K = n_coeffs - 1 steps.  Walk s of row i
+ * has id i * N + s.  v: float64[n] (host or device) or NULL for v = 1;
+ * y: float64[n_nodes] (or [n]), host or device.  Float64 only
+ * (params->precision = MCF_F64); params->n_walks is ignored.
+ * Errors: MCF_ERR_UNSUPPORTED (precision), MCF_ERR_INVALID_ARG (walks_per_node
+ * < 1, node out of range), MCF_ERR_OOM, MCF_ERR_CUDA. */
+mcf_status mcf_mc_classic(mcf_graph_t g, const mcf_params* params, const double* v, const int64_t* nodes,
+                          int64_t n_nodes, double* y, mcf_stats* stats);
 
 /* ------------------------------------------------------------------ batches */
 

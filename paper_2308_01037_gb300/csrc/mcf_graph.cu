@@ -150,34 +150,36 @@ enum : uint32_t {
     BAD_SYMMETRY = 16u,
 };
 
-__device__ __forceinline__ int64_t find_in_row(const int32_t* __restrict__ col, int64_t b, int64_t e, int32_t key) {
-    while (b < e) {
-        int64_t m = b + ((e - b) >> 1);
-        int32_t c = col[m];
-        if (c < key) b = m + 1;
-        else e = m;
-    }
-    return b;
+__device__ __forceinline__ unsigned long long pair_hash(uint32_t lo, uint32_t hi, uint32_t vbits) {
+    unsigned long long z = ((unsigned long long)lo << 32 | hi) ^ ((unsigned long long)vbits * 0xD1B54A32D192ED03ull);
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
 }
 
-// Warp per row: checks order, range, finiteness and the symmetric partner of
-// every entry; records loops, the diagonal (zeroed beforehand) and the
-// maximum degree.
+// Warp per row: checks order, range and finiteness; records loops, the
+// diagonal (zeroed beforehand) and the maximum degree.  Symmetry: every
+// off-diagonal entry (i, j) adds a 64-bit mix of the unordered pair and its
+// value to sums[0] when i < j and to sums[1] when i > j; the matrix is
+// symmetric exactly when the two multisets agree, which the equality of the
+// wrap-around sums confirms up to a 2^-64 chance of a missed difference.
 __global__ void validate_rows(int64_t n, int64_t nnz, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                               const float* __restrict__ val, uint32_t* __restrict__ bad,
                               unsigned long long* __restrict__ maxdeg, unsigned long long* __restrict__ loops,
-                              double* __restrict__ diag) {
+                              double* __restrict__ diag, unsigned long long* __restrict__ sums) {
     const int lane = threadIdx.x & 31;
     int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long s_lo = 0, s_hi = 0;
+    uint32_t flags = 0;
     for (int64_t i = warp; i < n; i += nwarps) {
         int64_t b = rp[i], e = rp[i + 1];
         if (b > e || b < 0 || e > nnz) {
-            if (lane == 0) atomicOr(bad, BAD_ROWPTR);
+            flags |= BAD_ROWPTR;
             continue;
         }
         if (lane == 0) atomicMax(maxdeg, (unsigned long long)(e - b));
-        uint32_t flags = 0;
         for (int64_t p = b + lane; p < e; p += 32) {
             int32_t j = col[p];
             if (j < 0 || j >= n) { flags |= BAD_COLUMN; continue; }
@@ -189,12 +191,20 @@ __global__ void validate_rows(int64_t n, int64_t nnz, const int64_t* __restrict_
                 diag[i] = (double)a;
                 continue;
             }
-            int64_t jb = rp[j], je = rp[j + 1];
-            if (jb > je || jb < 0 || je > nnz) { flags |= BAD_ROWPTR; continue; }
-            int64_t q = find_in_row(col, jb, je, (int32_t)i);
-            if (q >= je || col[q] != (int32_t)i) flags |= BAD_SYMMETRY;
-            else if (val && val[q] != a) flags |= BAD_SYMMETRY;
+            const uint32_t vb = val ? __float_as_uint(a) : 0u;
+            if ((int64_t)j > i) s_lo += pair_hash((uint32_t)i, (uint32_t)j, vb);
+            else s_hi += pair_hash((uint32_t)j, (uint32_t)i, vb);
         }
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        s_lo += __shfl_down_sync(0xffffffffu, s_lo, d);
+        s_hi += __shfl_down_sync(0xffffffffu, s_hi, d);
+        flags |= __shfl_down_sync(0xffffffffu, flags, d);
+    }
+    if (lane == 0) {
+        if (s_lo) atomicAdd(&sums[0], s_lo);
+        if (s_hi) atomicAdd(&sums[1], s_hi);
         if (flags) atomicOr(bad, flags);
     }
 }
@@ -387,7 +397,7 @@ mcf_status mcf_create_graph(int64_t n, const int64_t* row_ptr, const int32_t* co
             return cleanup(fail(MCF_ERR_CUDA, "values copy failed"));
     }
     // validation
-    struct Flags { uint32_t bad; uint32_t pad; unsigned long long maxdeg; unsigned long long loops; };
+    struct Flags { uint32_t bad; uint32_t pad; unsigned long long maxdeg; unsigned long long loops; unsigned long long sums[2]; };
     Flags* dflags = nullptr;
     if (cudaMalloc(&dflags, sizeof(Flags)) != cudaSuccess) { cudaGetLastError(); return cleanup(fail(MCF_ERR_OOM, "alloc")); }
     cudaMemset(dflags, 0, sizeof(Flags));
@@ -395,12 +405,13 @@ mcf_status mcf_create_graph(int64_t n, const int64_t* row_ptr, const int32_t* co
     if (n > 0) {
         int blocks = (int)std::min<int64_t>((n + 7) / 8, (int64_t)num_sms() * 16);
         validate_rows<<<blocks, 256>>>(n, nnz, g->row_ptr, g->col_idx, g->values, &dflags->bad, &dflags->maxdeg,
-                                       &dflags->loops, g->diag);
+                                       &dflags->loops, g->diag, dflags->sums);
     }
     Flags hf;
     cudaError_t e = cudaMemcpy(&hf, dflags, sizeof(Flags), cudaMemcpyDeviceToHost);
     cudaFree(dflags);
     if (e != cudaSuccess) return cleanup(fail(MCF_ERR_CUDA, std::string("validation: ") + cudaGetErrorString(e)));
+    if (!(hf.bad & (BAD_ROWPTR | BAD_COLUMN)) && hf.sums[0] != hf.sums[1]) hf.bad |= BAD_SYMMETRY;
     if (hf.bad) {
         std::string why;
         if (hf.bad & BAD_ROWPTR) why += " row_ptr not non-decreasing within [0, nnz];";

@@ -114,6 +114,38 @@ __device__ __forceinline__ double warp_row_sums(int64_t base, int64_t n, const i
     return s;
 }
 
+// Row sums for 32 listed rows: lane t owns row rows[base + t] (t < m).
+template <int SHORT>
+__device__ __forceinline__ double warp_listed_row_sums(int64_t base, int64_t m, const int64_t* __restrict__ rows,
+                                                       const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                                       const float* __restrict__ val, const double* __restrict__ x) {
+    const int lane = threadIdx.x & 31;
+    const int64_t t = base + lane;
+    int64_t b = 0, e = 0;
+    if (t < m) {
+        const int64_t row = rows[t];
+        b = rp[row];
+        e = rp[row + 1];
+    }
+    double s = 0.0;
+    const bool is_short = e - b <= SHORT;
+    if (is_short)
+        for (int64_t p = b; p < e; ++p) s += (val ? (double)val[p] : 1.0) * x[col[p]];
+    unsigned longs = __ballot_sync(0xffffffffu, !is_short);
+    while (longs) {
+        const int tl = __ffs(longs) - 1;
+        longs &= longs - 1;
+        const int64_t lb = __shfl_sync(0xffffffffu, b, tl);
+        const int64_t le = __shfl_sync(0xffffffffu, e, tl);
+        double part = 0.0;
+        for (int64_t p = lb + lane; p < le; p += 32) part += (val ? (double)val[p] : 1.0) * x[col[p]];
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) part += __shfl_xor_sync(0xffffffffu, part, d);
+        if (lane == tl) s = part;
+    }
+    return s;
+}
+
 // ---------------------------------------------------------------- helpers (host)
 bool is_device_ptr(const void* p);
 int num_sms();
@@ -208,12 +240,14 @@ struct WalkTuning {
     bool tc_path = true;   // MCF_WALK_TC_PATH=0 selects the general node-record kernel for v = 1
     int l2_fetch = 32;     // MCF_L2_FETCH_BYTES: L2 fetch granularity for walk kernels (0 = leave as is)
     bool prefetch = false; // MCF_WALK_PREFETCH=1: issue the next random read before the cutoff test
+    int walks_per_thread = 1;  // MCF_WALK_PER_THREAD=2: two walks per thread in the TC kernel
 };
 inline const WalkTuning& walk_tuning() {
     static WalkTuning t = [] {
         WalkTuning w;
         if (const char* e = getenv("MCF_L2_FETCH_BYTES")) w.l2_fetch = std::max(0, std::min(128, atoi(e)));
         if (const char* e = getenv("MCF_WALK_PREFETCH")) w.prefetch = atoi(e) != 0;
+        if (const char* e = getenv("MCF_WALK_PER_THREAD")) w.walks_per_thread = atoi(e) == 2 ? 2 : 1;
         if (const char* e = getenv("MCF_WALK_TC_PATH")) w.tc_path = atoi(e) != 0;
         if (const char* e = getenv("MCF_WALK_MINB")) w.minb = atoi(e) >= 8 ? 8 : (atoi(e) <= 5 ? 5 : 6);
         if (const char* e = getenv("MCF_WALK_GRAB")) w.grab = std::max(1, std::min(64, atoi(e)));

@@ -120,12 +120,12 @@ __global__ void build_records(int64_t n, const int64_t* __restrict__ rp, const d
             x.off = b;
             x.deg = (uint32_t)d;
             x.pad = 0;
-            x.r = r[i];
+            x.r = r ? r[i] : 0.0;
             x.mult = mult;
         } else {
             x.off = (uint32_t)b;
             x.deg = (uint32_t)d;
-            x.r = __double2float_rn(r[i]);
+            x.r = r ? __double2float_rn(r[i]) : 0.0f;
             x.mult = __double2float_rn(mult);
         }
         rec[i] = x;
@@ -145,7 +145,8 @@ __global__ void build_records(int64_t n, const int64_t* __restrict__ rp, const d
 template <bool F64, bool WEIGHTED, int MINB>
 __global__ void __launch_bounds__(256, MINB) walk_action_kernel(
     const Rec<F64>* __restrict__ rec, const int32_t* __restrict__ col, const WEntry* __restrict__ went,
-    const int32_t* __restrict__ starts, const int64_t* __restrict__ soff, const uint32_t* __restrict__ chunk_s0,
+    const int32_t* __restrict__ starts, const int64_t* __restrict__ soff, const int64_t* __restrict__ goff,
+    const uint32_t* __restrict__ chunk_s0,
     const double* __restrict__ zeta_g, int K, double wc, float wc32, uint2 key, uint32_t req, int grab,
     double* __restrict__ acc, unsigned long long* __restrict__ counters) {
     using real = typename std::conditional<F64, double, float>::type;
@@ -214,6 +215,7 @@ __global__ void __launch_bounds__(256, MINB) walk_action_kernel(
             const int32_t s_new = __shfl_sync(FULL, cs, src);
             if (((idle >> lane) & 1u) && rank < avail) {
                 g = (int64_t)c * WARP_CHUNK + p + rank;
+                if (goff != soff) g = goff[s_new] + (g - soff[s_new]);   // node subset: full-run walk id
                 node0 = (uint32_t)starts[s_new];
                 l = node0;
                 k = 0;
@@ -310,7 +312,8 @@ __global__ void degree_table(int64_t max_deg, double gamma, float* __restrict__ 
 template <int MINB, bool PREFETCH>
 __global__ void __launch_bounds__(256, MINB) walk_tc_kernel(
     const uint2* __restrict__ nod, const uint2* __restrict__ eod, const float* __restrict__ rm,
-    const int32_t* __restrict__ starts, const int64_t* __restrict__ soff, const uint32_t* __restrict__ chunk_s0,
+    const int32_t* __restrict__ starts, const int64_t* __restrict__ soff, const int64_t* __restrict__ goff,
+    const uint32_t* __restrict__ chunk_s0,
     const double* __restrict__ zeta_g, int K, float wc32, uint2 key, uint32_t req, int grab,
     double* __restrict__ acc, unsigned long long* __restrict__ counters) {
     __shared__ float zeta[MCF_MAX_COEFFS];
@@ -370,6 +373,7 @@ __global__ void __launch_bounds__(256, MINB) walk_tc_kernel(
             const int32_t s_new = __shfl_sync(FULL, cs, src);
             if (((idle >> lane) & 1u) && rank < avail) {
                 g = (int64_t)c * WARP_CHUNK + p + rank;
+                if (goff != soff) g = goff[s_new] + (g - soff[s_new]);   // node subset: full-run walk id
                 node0 = (uint32_t)starts[s_new];
                 const uint2 od = nod[node0];
                 off = od.x;
@@ -438,6 +442,164 @@ __global__ void __launch_bounds__(256, MINB) walk_tc_kernel(
     }
 }
 
+// Two (NW) walks per thread: the same schedule as walk_tc_kernel, but each
+// warp runs NW independent pools of 32-walk chunks and every thread advances
+// one walk of each pool per iteration, issuing both random reads before it
+// consumes either, so a thread keeps NW dependent-read chains in flight.
+struct TcPool {
+    int32_t c = -1, c_end = -1;
+    int p = 0, valid = 0;
+    int32_t cs = 0;
+    bool exhausted = false;
+};
+struct TcLane {
+    bool active = false;
+    int64_t g = 0;
+    uint32_t node0 = 0, off = 0, deg = 0;
+    int k = 0;
+    float W = 1.f;
+    uint4 u = make_uint4(0u, 0u, 0u, 0u);
+    F2Acc a;
+};
+
+__device__ __forceinline__ void tc_refill(TcPool& P, TcLane& L, const uint2* __restrict__ nod,
+                                          const int32_t* __restrict__ starts, const int64_t* __restrict__ soff,
+                                          const int64_t* __restrict__ goff,
+                                          const uint32_t* __restrict__ chunk_s0, int32_t n_chunks, int grab,
+                                          unsigned long long* __restrict__ counters, int lane, unsigned lt_mask) {
+    const unsigned FULL = 0xffffffffu;
+    unsigned idle = __ballot_sync(FULL, !L.active);
+    while (idle && !P.exhausted) {
+        if (P.p >= P.valid) {
+            ++P.c;
+            if (P.c >= P.c_end) {
+                int32_t base = 0;
+                if (lane == 0) base = (int32_t)atomicAdd((unsigned int*)&counters[C_NEXT], (unsigned)grab);
+                base = __shfl_sync(FULL, base, 0);
+                P.c = base;
+                P.c_end = min(base + grab, n_chunks);
+            }
+            if (P.c >= n_chunks) {
+                P.exhausted = true;
+                break;
+            }
+            const int64_t S = (int64_t)counters[C_STARTS];
+            const int64_t s0 = chunk_s0[P.c];
+            const int64_t bnd = (s0 + 1 + lane <= S) ? soff[s0 + 1 + lane] : INT64_MAX;
+            const int64_t gl = (int64_t)P.c * WARP_CHUNK + lane;
+            int cnt = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int64_t bv = __shfl_sync(FULL, bnd, cnt + step - 1);
+                if (bv <= gl) cnt += step;
+            }
+            P.cs = (int32_t)(s0 + cnt);
+            P.valid = (int)min((int64_t)WARP_CHUNK, (int64_t)counters[C_TOTAL] - (int64_t)P.c * WARP_CHUNK);
+            P.p = 0;
+        }
+        const int avail = P.valid - P.p;
+        const int rank = __popc(idle & lt_mask);
+        const int src = min(P.p + rank, WARP_CHUNK - 1);
+        const int32_t s_new = __shfl_sync(FULL, P.cs, src);
+        if (((idle >> lane) & 1u) && rank < avail) {
+            L.g = (int64_t)P.c * WARP_CHUNK + P.p + rank;
+            if (goff != soff) L.g = goff[s_new] + (L.g - soff[s_new]);
+            L.node0 = (uint32_t)starts[s_new];
+            const uint2 od = nod[L.node0];
+            L.off = od.x;
+            L.deg = od.y;
+            L.k = 0;
+            L.W = 1.f;
+            L.a = F2Acc();
+            L.active = true;
+        }
+        P.p += min(avail, __popc(idle));
+        idle = __ballot_sync(FULL, !L.active);
+    }
+}
+
+template <int MINB, int NW>
+__global__ void __launch_bounds__(256, MINB) walk_tc_multi_kernel(
+    const uint2* __restrict__ nod, const uint2* __restrict__ eod, const float* __restrict__ rm,
+    const int32_t* __restrict__ starts, const int64_t* __restrict__ soff, const int64_t* __restrict__ goff,
+    const uint32_t* __restrict__ chunk_s0,
+    const double* __restrict__ zeta_g, int K, float wc32, uint2 key, uint32_t req, int grab,
+    double* __restrict__ acc, unsigned long long* __restrict__ counters) {
+    __shared__ float zeta[MCF_MAX_COEFFS];
+    __shared__ WalkResults<float2> rbuf[256 / 32];
+    for (int k = threadIdx.x; k <= K; k += blockDim.x) zeta[k] = (float)zeta_g[k];
+    __syncthreads();
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    WalkResults<float2>& rb = rbuf[threadIdx.x >> 5];
+    const int32_t n_chunks = (int32_t)(((int64_t)counters[C_TOTAL] + WARP_CHUNK - 1) / WARP_CHUNK);
+    TcPool P[NW];
+    TcLane L[NW];
+    int rb_n = 0;
+    uint32_t my_steps = 0, my_walks = 0, flags = 0;
+    for (;;) {
+        bool any = false;
+#pragma unroll
+        for (int s = 0; s < NW; ++s) {
+            tc_refill(P[s], L[s], nod, starts, soff, goff, chunk_s0, n_chunks, grab, counters, lane, lt_mask);
+            any |= L[s].active;
+        }
+        if (!__any_sync(FULL, any)) break;
+        uint2 nx[NW];
+        bool last[NW];
+#pragma unroll
+        for (int s = 0; s < NW; ++s) {
+            last[s] = L[s].k + 2 >= K || L[s].deg == 0;
+            nx[s] = make_uint2(0u, 0u);
+            if (L[s].active && !last[s]) {
+                uint32_t w0, w1;
+                walk_words<false>(L[s].u, L[s].k, (uint32_t)L[s].g, (uint32_t)((uint64_t)L[s].g >> 32), req, key, w0, w1);
+                nx[s] = load_od(eod + (int64_t)L[s].off + __umulhi(w0, L[s].deg), policy_evict_first());
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < NW; ++s) {
+            bool done = false;
+            if (L[s].active) {
+                done = !(fabsf(L[s].W) > wc32);
+                if (!done) {
+                    const float t = __ldg(rm + L[s].deg);
+                    L[s].a.add(__fmul_rn(__fmul_rn(zeta[L[s].k + 2], L[s].W), t));
+                    if (last[s]) {
+                        done = true;
+                    } else {
+                        L[s].W = __fmul_rn(L[s].W, t);
+                        L[s].off = nx[s].x;
+                        L[s].deg = nx[s].y;
+                        ++L[s].k;
+                        ++my_steps;
+                    }
+                }
+                if (done) {
+                    if (!isfinite(L[s].W) || !isfinite(L[s].a.hi)) flags |= 1u;
+                    ++my_walks;
+                    L[s].active = false;
+                }
+            }
+            rb_n = rb.push(done, L[s].node0, make_float2(L[s].a.hi, L[s].a.lo), rb_n, lane, lt_mask, acc);
+        }
+    }
+    rb.flush(rb_n, lane, acc);
+    unsigned long long ws = my_steps, ww = my_walks;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        ws += __shfl_down_sync(FULL, ws, d);
+        ww += __shfl_down_sync(FULL, ww, d);
+        flags |= __shfl_down_sync(FULL, flags, d);
+    }
+    if (lane == 0) {
+        atomicAdd(&counters[C_STEPS], ws);
+        atomicAdd(&counters[C_WALKS], ww);
+        if (flags) atomicOr(&counters[C_FLAGS], (unsigned long long)flags);
+    }
+}
+
 // q_i = acc_i / N_i (Eq. rand_funm_action_formula, the 1/N_i factor of W^(0)).
 __global__ void finalize_q(int64_t n, double* __restrict__ acc, const int64_t* __restrict__ nw) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -457,6 +619,40 @@ __global__ void action_epilogue(int64_t n, const int64_t* __restrict__ rp, const
         const double s = warp_row_sums<32>(base, n, rp, col, val, q);
         const int64_t row = base + lane;
         if (row < n) y[row] = z0 * (v ? v[row] : 1.0) + z1 * r[row] + gamma * s;
+    }
+}
+
+// Node subsets: the walked space holds only the needed starts' walks;
+// cof[s] is where start s's walks begin in it (soff[s] keeps the full-run id).
+__global__ void subset_walks(int64_t n, const int64_t* __restrict__ flag, const int64_t* __restrict__ nw,
+                             int64_t* __restrict__ wmask) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        wmask[i] = flag[i] ? nw[i] : 0;
+}
+
+__global__ void subset_offsets(int64_t n, const int64_t* __restrict__ flag, const int64_t* __restrict__ spos,
+                               const int64_t* __restrict__ cw, int64_t* __restrict__ cof,
+                               const unsigned long long* __restrict__ counters) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (flag[i]) cof[spos[i]] = cw[i];
+    if (blockIdx.x == 0 && threadIdx.x == 0) cof[counters[C_STARTS]] = (int64_t)counters[C_TOTAL];
+}
+
+// y_t = zeta_0 v_i + zeta_1 r_i + (A' q)_i for i = nodes[t].
+__global__ void action_epilogue_nodes(int64_t m, const int64_t* __restrict__ nodes, const int64_t* __restrict__ rp,
+                                      const int32_t* __restrict__ col, const float* __restrict__ val, double gamma,
+                                      double z0, double z1, const double* __restrict__ v, const double* __restrict__ r,
+                                      const double* __restrict__ q, double* __restrict__ y) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = warp * 32; base < m; base += nwarps * 32) {
+        const double s = warp_listed_row_sums<32>(base, m, nodes, rp, col, val, q);
+        const int64_t t = base + lane;
+        if (t < m) {
+            const int64_t i = nodes[t];
+            y[t] = z0 * (v ? v[i] : 1.0) + z1 * r[i] + gamma * s;
+        }
     }
 }
 
@@ -635,7 +831,8 @@ struct Prep {
     int64_t* woff = nullptr;
     int64_t* spos = nullptr;
     int32_t* starts = nullptr;
-    int64_t* soff = nullptr;
+    int64_t* soff = nullptr;   // first full-run walk id of each start (+ the total)
+    int64_t* cof = nullptr;    // first walk of each start in the walked space (== soff unless a node subset)
     unsigned long long* counters = nullptr;
     void* rec = nullptr;
     double* zeta = nullptr;
@@ -656,6 +853,7 @@ static mcf_status prepare(const mcf_graph* g, const mcf_params* p, double gamma,
     MCF_TRY(sc.get(&P.spos, n));
     MCF_TRY(sc.get(&P.starts, n));
     MCF_TRY(sc.get(&P.soff, n + 1));
+    P.cof = P.soff;
     MCF_TRY(sc.get(&P.counters, N_COUNTERS));
     MCF_TRY(sc.get(&P.zeta, MCF_MAX_COEFFS));
     P.scan_bytes = scan_tmp_bytes(n);
@@ -719,8 +917,8 @@ static void launch_action_walks_t(const mcf_graph* g, const Prep& P, uint32_t* c
     auto kern = walk_action_kernel<F64, WEIGHTED, MINB>;
     const int grid = persistent_grid(kern, 256, 0);
     ScopedL2Fetch fetch(walk_tuning().l2_fetch);
-    kern<<<grid, 256, 0, st>>>((const Rec<F64>*)P.rec, g->col_idx, g->went, P.starts, P.soff, chunk_s0, P.zeta, K,
-                               wc, cutoff_f32(wc), key, req, walk_tuning().grab, acc, P.counters);
+    kern<<<grid, 256, 0, st>>>((const Rec<F64>*)P.rec, g->col_idx, g->went, P.starts, P.cof, P.soff, chunk_s0, P.zeta,
+                               K, wc, cutoff_f32(wc), key, req, walk_tuning().grab, acc, P.counters);
 }
 
 // Builds the graph's node_od / edge_od arrays on first use (binary, nnz < 2^32).
@@ -750,11 +948,19 @@ mcf_status ensure_edge_od(mcf_graph* g, cudaStream_t st) {
 template <int MINB>
 static void launch_tc_walks_t(const mcf_graph* g, const Prep& P, const float* rm, uint32_t* chunk_s0, int K,
                               double wc, uint2 key, uint32_t req, double* acc, cudaStream_t st) {
+    if (walk_tuning().walks_per_thread == 2) {
+        auto kern = walk_tc_multi_kernel<(MINB > 4 ? 4 : MINB), 2>;
+        const int grid = persistent_grid(kern, 256, 0);
+        ScopedL2Fetch fetch(walk_tuning().l2_fetch);
+        kern<<<grid, 256, 0, st>>>(g->node_od, g->edge_od, rm, P.starts, P.cof, P.soff, chunk_s0, P.zeta, K,
+                                   cutoff_f32(wc), key, req, walk_tuning().grab, acc, P.counters);
+        return;
+    }
     auto kern = walk_tuning().prefetch ? walk_tc_kernel<MINB, true> : walk_tc_kernel<MINB, false>;
     const int grid = persistent_grid(kern, 256, 0);
     ScopedL2Fetch fetch(walk_tuning().l2_fetch);
-    kern<<<grid, 256, 0, st>>>(g->node_od, g->edge_od, rm, P.starts, P.soff, chunk_s0, P.zeta, K, cutoff_f32(wc), key,
-                               req, walk_tuning().grab, acc, P.counters);
+    kern<<<grid, 256, 0, st>>>(g->node_od, g->edge_od, rm, P.starts, P.cof, P.soff, chunk_s0, P.zeta, K,
+                               cutoff_f32(wc), key, req, walk_tuning().grab, acc, P.counters);
 }
 
 template <bool F64, bool WEIGHTED>
@@ -766,11 +972,12 @@ static void launch_action_walks(const mcf_graph* g, const Prep& P, uint32_t* chu
 }
 
 static mcf_status solve_action(mcf_graph* g, const mcf_params* p, const double* v, double* y, mcf_stats* stats,
-                               bool ones) {
+                               bool ones, const int64_t* nodes = nullptr, int64_t n_nodes = -1) {
     set_error("");
     MCF_TRY(check_params(g, p));
     if (!y) return fail(MCF_ERR_INVALID_ARG, "y is NULL");
     if (!ones && !v) return fail(MCF_ERR_INVALID_ARG, "v is NULL");
+    if (nodes && n_nodes < 0) return fail(MCF_ERR_INVALID_ARG, "n_nodes must be >= 0");
     cudaStream_t st = (cudaStream_t)p->stream;
     const int64_t n = g->n;
     const double gamma = p->scale == 0.0 ? 1.0 : p->scale;
@@ -788,11 +995,52 @@ static mcf_status solve_action(mcf_graph* g, const mcf_params* p, const double* 
             v_dev = vd;
         }
     }
+    const int64_t m = nodes ? n_nodes : n;
     const bool y_on_dev = is_device_ptr(y);
     double* y_dev = y;
-    if (!y_on_dev) MCF_TRY(sc.get(&y_dev, n));
+    if (!y_on_dev) MCF_TRY(sc.get(&y_dev, m));
+    // a node subset walks only the columns adjacent to the requested nodes
+    const int64_t* nodes_dev = nullptr;
+    uint8_t *need = nullptr, *want = nullptr;
+    if (nodes) {
+        if (m == 0) return MCF_OK;
+        if (is_device_ptr(nodes)) {
+            unsigned long long* chk;
+            MCF_TRY(sc.get(&chk, N_COUNTERS));
+            MCF_CUDA_TRY(cudaMemsetAsync(chk, 0, N_COUNTERS * sizeof(unsigned long long), st));
+            check_nodes<<<grid_for(m, 256), 256, 0, st>>>(m, nodes, n, chk);
+            unsigned long long h = 0;
+            MCF_CUDA_TRY(cudaMemcpyAsync(&h, &chk[C_FLAGS], sizeof(h), cudaMemcpyDeviceToHost, st));
+            MCF_CUDA_TRY(cudaStreamSynchronize(st));
+            if (h & 2ull) return fail(MCF_ERR_INVALID_ARG, "node index out of range");
+            nodes_dev = nodes;
+        } else {
+            for (int64_t t = 0; t < m; ++t)
+                if (nodes[t] < 0 || nodes[t] >= n) return fail(MCF_ERR_INVALID_ARG, "node index out of range");
+            int64_t* nd;
+            MCF_TRY(sc.get(&nd, m));
+            MCF_CUDA_TRY(cudaMemcpyAsync(nd, nodes, m * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+            nodes_dev = nd;
+        }
+        MCF_TRY(sc.get(&need, n));
+        MCF_TRY(sc.get(&want, n));
+        MCF_CUDA_TRY(cudaMemsetAsync(need, 0, n, st));
+        MCF_CUDA_TRY(cudaMemsetAsync(want, 0, n, st));
+        mark_nodes<<<grid_for(m, 256), 256, 0, st>>>(m, nodes_dev, g->row_ptr, g->col_idx, need, want);
+    }
     Prep P;
-    MCF_TRY(prepare(g, p, gamma, v_dev, nullptr, sc, P, st));
+    MCF_TRY(prepare(g, p, gamma, v_dev, need, sc, P, st));
+    P.cof = P.soff;
+    if (nodes && n > 0) {
+        int64_t *wmask, *cw, *cof;
+        MCF_TRY(sc.get(&wmask, n));
+        MCF_TRY(sc.get(&cw, n));
+        MCF_TRY(sc.get(&cof, n + 1));
+        subset_walks<<<grid_for(n, 256), 256, 0, st>>>(n, P.flag, P.nw, wmask);
+        MCF_TRY(scan_i64(wmask, cw, n, (int64_t*)&P.counters[C_TOTAL], P.scan_tmp, P.scan_bytes, st));
+        subset_offsets<<<grid_for(n, 256), 256, 0, st>>>(n, P.flag, P.spos, cw, cof, P.counters);
+        P.cof = cof;
+    }
     double* acc;
     MCF_TRY(sc.get(&acc, n));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -805,7 +1053,7 @@ static mcf_status solve_action(mcf_graph* g, const mcf_params* p, const double* 
             const int64_t max_chunks = max_walks / WARP_CHUNK + 2;
             uint32_t* chunk_s0;
             MCF_TRY(sc.get(&chunk_s0, max_chunks));
-            chunk_table<<<grid_for(n, 256), 256, 0, st>>>(P.soff, P.counters, chunk_s0);
+            chunk_table<<<grid_for(n, 256), 256, 0, st>>>(P.cof, P.counters, chunk_s0);
             if (stats) {
                 cudaEventCreate(&e0);
                 cudaEventCreate(&e1);
@@ -829,11 +1077,15 @@ static mcf_status solve_action(mcf_graph* g, const mcf_params* p, const double* 
         }
         finalize_q<<<grid_for(n, 256), 256, 0, st>>>(n, acc, P.nw);
         const double z0 = p->coeffs[0], z1 = K >= 1 ? p->coeffs[1] : 0.0;
-        action_epilogue<<<grid_for(n, 256), 256, 0, st>>>(n, g->row_ptr, g->col_idx, g->values, gamma, z0, z1, v_dev,
-                                                          P.r, acc, y_dev);
+        if (nodes_dev)
+            action_epilogue_nodes<<<grid_for(m, 256), 256, 0, st>>>(m, nodes_dev, g->row_ptr, g->col_idx, g->values,
+                                                                    gamma, z0, z1, v_dev, P.r, acc, y_dev);
+        else
+            action_epilogue<<<grid_for(n, 256), 256, 0, st>>>(n, g->row_ptr, g->col_idx, g->values, gamma, z0, z1,
+                                                              v_dev, P.r, acc, y_dev);
         MCF_CUDA_TRY(cudaGetLastError());
     }
-    if (!y_on_dev && n > 0) MCF_CUDA_TRY(cudaMemcpyAsync(y, y_dev, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (!y_on_dev && m > 0) MCF_CUDA_TRY(cudaMemcpyAsync(y, y_dev, m * sizeof(double), cudaMemcpyDeviceToHost, st));
     mcf_status rc = finish_stats(stats, P.counters, e0, e1, st);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
@@ -965,6 +1217,340 @@ static mcf_status solve_diag(mcf_graph* g, const mcf_params* p, const int64_t* n
     return MCF_OK;
 }
 
+// ====================================================================== RandFunm (Algorithm 2), dense F
+// Row k0 of N_k0 * Q (Eq. rand_funm_Q before its 1/N_k0 factor) for every
+// start column k0.  One CTA per start at a time (atomic counter); its threads
+// run the N_k0 walks and add zeta_{m+2} W^(m) into the dense row with float64
+// reductions executed by the L2.  The N_k0 step-0 visits are added once.
+template <bool F64, bool WEIGHTED>
+__global__ void __launch_bounds__(128) walk_full_kernel(
+    const Rec<F64>* __restrict__ rec, const int32_t* __restrict__ col, const WEntry* __restrict__ went,
+    const int32_t* __restrict__ starts, const int64_t* __restrict__ woff, const int64_t* __restrict__ nw,
+    const double* __restrict__ zeta_g, int K, double wc, float wc32, uint2 key, uint32_t req, int64_t n,
+    double* __restrict__ Q, unsigned long long* __restrict__ counters) {
+    using real = typename std::conditional<F64, double, float>::type;
+    __shared__ real zeta[MCF_MAX_COEFFS];
+    __shared__ int64_t cur;
+    for (int k = threadIdx.x; k <= K; k += blockDim.x) zeta[k] = (real)zeta_g[k];
+    DiagTable t;
+    t.key = nullptr;
+    t.used = nullptr;
+    t.cap_log2 = 0;
+    t.limit = 0;
+    t.count = nullptr;
+    const int64_t S = (int64_t)counters[C_STARTS];
+    uint32_t steps = 0, walks = 0, flags = 0;
+    bool visit0;
+    if constexpr (F64) visit0 = 1.0 > wc;
+    else visit0 = 1.0f > wc32;
+    __syncthreads();
+    for (;;) {
+        if (threadIdx.x == 0) cur = (int64_t)atomicAdd(&counters[C_NEXT], 1ull);
+        __syncthreads();
+        const int64_t s = cur;
+        __syncthreads();   // every thread has read cur before it is reused
+        if (s >= S) break;
+        const uint32_t k0 = (uint32_t)starts[s];
+        const int64_t Nk = nw[k0];
+        const int64_t g0 = woff[k0];
+        t.val = Q + (int64_t)k0 * n;
+        if (threadIdx.x == 0 && visit0) {
+            double z2;
+            if constexpr (F64) z2 = zeta[2];
+            else z2 = (double)zeta[2];
+            atomicAdd(&t.val[k0], (double)Nk * z2);
+        }
+        walks += (uint32_t)(Nk > (int64_t)threadIdx.x ? (Nk - 1 - threadIdx.x) / blockDim.x + 1 : 0);
+        for (int64_t w = threadIdx.x; w < Nk; w += blockDim.x)
+            diag_walk<F64, WEIGHTED, true>(t, k0, g0 + w, 1, 0, rec, col, went, zeta, K, wc, wc32, key, req, steps,
+                                           flags);
+    }
+    const int lane = threadIdx.x & 31;
+    unsigned long long ws = steps, ww = walks;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        ws += __shfl_down_sync(0xffffffffu, ws, d);
+        ww += __shfl_down_sync(0xffffffffu, ww, d);
+        flags |= __shfl_down_sync(0xffffffffu, flags, d);
+    }
+    if (lane == 0) {
+        atomicAdd(&counters[C_STEPS], ws);
+        atomicAdd(&counters[C_WALKS], ww);
+        if (flags) atomicOr(&counters[C_FLAGS], (unsigned long long)flags);
+    }
+}
+
+// F = zeta_0 I + zeta_1 A' + A' Q A' (Algorithm 2, last step) one row i at a
+// time: row i of A'Q is formed in shared memory from the rows of N Q of i's
+// neighbours, each divided by its N_m (Eq. rand_funm_Q); then
+// F_ij = zeta_0 [i == j] + sum_{m in N(j)} a'_jm (A'Q)_im (a'_jm = a'_mj for a
+// symmetric A, so row j of A' serves as column j), and finally
+// zeta_1 a'_ij is added for the entries of row i.
+__global__ void __launch_bounds__(512) full_epilogue(int64_t n, const int64_t* __restrict__ rp,
+                                                     const int32_t* __restrict__ col, const float* __restrict__ val,
+                                                     const double* __restrict__ Q, const int64_t* __restrict__ nw,
+                                                     double gamma, double z0, double z1, int K,
+                                                     double* __restrict__ F) {
+    extern __shared__ double aq[];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+        const int64_t b = rp[i], e = rp[i + 1];
+        for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+            double a = 0.0;
+            if (K >= 2)
+                for (int64_t p = b; p < e; ++p) {
+                    const int32_t m = col[p];
+                    const int64_t Nm = nw[m];
+                    if (Nm == 0) continue;   // no walks from column m: its row of Q is zero
+                    const double q = __ddiv_rn(__ldcs(Q + (int64_t)m * n + j), (double)Nm);
+                    a = __dadd_rn(a, __dmul_rn(__dmul_rn(gamma, val ? (double)val[p] : 1.0), q));
+                }
+            aq[j] = a;
+        }
+        __syncthreads();
+        double* Fi = F + i * n;
+        for (int64_t base = (int64_t)wid * 32; base < n; base += (int64_t)nwarp * 32) {
+            const double s = warp_row_sums<32>(base, n, rp, col, val, aq);
+            const int64_t j = base + lane;
+            if (j < n) Fi[j] = (j == i ? z0 : 0.0) + gamma * s;
+        }
+        __syncthreads();
+        if (K >= 1)
+            for (int64_t p = b + threadIdx.x; p < e; p += blockDim.x)
+                atomicAdd(&Fi[col[p]], z1 * (gamma * (val ? (double)val[p] : 1.0)));
+        __syncthreads();
+    }
+}
+
+constexpr int64_t FULL_MAX_NODES = MCF_FULL_MAX_NODES;
+
+static mcf_status solve_full(mcf_graph* g, const mcf_params* p, double* F, mcf_stats* stats) {
+    set_error("");
+    MCF_TRY(check_params(g, p));
+    if (!F) return fail(MCF_ERR_INVALID_ARG, "F is NULL");
+    const int64_t n = g->n;
+    if (n > FULL_MAX_NODES)
+        return fail(MCF_ERR_UNSUPPORTED, "the dense estimate needs n <= " + std::to_string(FULL_MAX_NODES));
+    cudaStream_t st = (cudaStream_t)p->stream;
+    const double gamma = p->scale == 0.0 ? 1.0 : p->scale;
+    const int K = p->n_coeffs - 1;
+    const bool f64 = p->precision == MCF_F64;
+    keep_pool_memory();
+    Scratch sc(st);
+    const bool f_on_dev = is_device_ptr(F);
+    double* F_dev = F;
+    if (!f_on_dev) MCF_TRY(sc.get(&F_dev, (size_t)std::max<int64_t>(n * n, 1)));
+    Prep P;
+    MCF_TRY(prepare(g, p, gamma, nullptr, nullptr, sc, P, st));
+    double* Q;
+    MCF_TRY(sc.get(&Q, (size_t)std::max<int64_t>(n * n, 1)));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (n > 0) {
+        if (K >= 2) {
+            MCF_CUDA_TRY(cudaMemsetAsync(Q, 0, (size_t)(n * n) * sizeof(double), st));
+            if (stats) {
+                cudaEventCreate(&e0);
+                cudaEventCreate(&e1);
+                cudaEventRecord(e0, st);
+            }
+            const uint2 key = philox_key(p->seed);
+            const float wc32 = cutoff_f32(p->w_cutoff);
+#define MCF_FULL(F64_, W_)                                                                                           \
+    do {                                                                                                             \
+        auto kern = walk_full_kernel<F64_, W_>;                                                                      \
+        const int grid = persistent_grid(kern, 128, 0);                                                              \
+        kern<<<grid, 128, 0, st>>>((const Rec<F64_>*)P.rec, g->col_idx, g->went, P.starts, P.woff, P.nw, P.zeta, K, \
+                                   p->w_cutoff, wc32, key, p->request_id, n, Q, P.counters);                         \
+    } while (0)
+            if (f64) {
+                if (g->weighted) MCF_FULL(true, true);
+                else MCF_FULL(true, false);
+            } else {
+                if (g->weighted) MCF_FULL(false, true);
+                else MCF_FULL(false, false);
+            }
+#undef MCF_FULL
+            MCF_CUDA_TRY(cudaGetLastError());
+            if (stats) cudaEventRecord(e1, st);
+        }
+        const size_t smem = (size_t)n * sizeof(double);
+        MCF_CUDA_TRY(cudaFuncSetAttribute(full_epilogue, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const int grid = (int)std::min<int64_t>(n, persistent_grid(full_epilogue, 512, smem));
+        const double z0 = p->coeffs[0], z1 = K >= 1 ? p->coeffs[1] : 0.0;
+        full_epilogue<<<grid, 512, smem, st>>>(n, g->row_ptr, g->col_idx, g->values, Q, P.nw, gamma, z0, z1, K,
+                                               F_dev);
+        MCF_CUDA_TRY(cudaGetLastError());
+    }
+    if (!f_on_dev && n > 0)
+        MCF_CUDA_TRY(cudaMemcpyAsync(F, F_dev, (size_t)(n * n) * sizeof(double), cudaMemcpyDeviceToHost, st));
+    mcf_status rc = finish_stats(stats, P.counters, e0, e1, st);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (rc != MCF_OK) return rc;
+    if (!f_on_dev) MCF_CUDA_TRY(cudaStreamSynchronize(st));
+    return MCF_OK;
+}
+
+// ====================================================================== classical Monte Carlo (Algorithm 1)
+// y_t = (1/N) sum over N walks from row i = nodes[t] of sum_k zeta_k W^(k)
+// v_{l_k}: every step samples one entry of the current row with probability
+// |a_lj| / sum_j |a_lj| and multiplies W by sign(a_lj) sum_j |a'_lj| (the same
+// chain as the row-sampling walks, Definition 1).  Walk ids are i * N + s.
+// Walks are laid out t-major; every warp takes 32 consecutive walks, sums each
+// walk in float64 and adds the walks of one output with one atomic.
+template <bool WEIGHTED>
+__global__ void __launch_bounds__(256) mc_classic_kernel(
+    int64_t m, const int64_t* __restrict__ nodes, int64_t N, const Rec<true>* __restrict__ rec,
+    const int32_t* __restrict__ col, const WEntry* __restrict__ went, const double* __restrict__ v,
+    const double* __restrict__ zeta_g, int K, double wc, uint2 key, uint32_t req, double* __restrict__ acc,
+    unsigned long long* __restrict__ counters) {
+    __shared__ double zeta[MCF_MAX_COEFFS];
+    for (int k = threadIdx.x; k <= K; k += blockDim.x) zeta[k] = zeta_g[k];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t total = m * N;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    uint32_t steps = 0, walks = 0;
+    for (int64_t base = warp0 * 32; base < total; base += nwarps * 32) {
+        const int64_t w = base + lane;
+        const bool valid = w < total;
+        double sum = 0.0;
+        uint32_t t = 0;
+        if (valid) {
+            t = (uint32_t)(w / N);
+            const int64_t s = w - (int64_t)t * N;
+            const int64_t i = nodes ? nodes[t] : (int64_t)t;
+            const uint64_t g = (uint64_t)i * (uint64_t)N + (uint64_t)s;
+            const uint32_t glo = (uint32_t)g, ghi = (uint32_t)(g >> 32);
+            uint32_t l = (uint32_t)i;
+            double W = 1.0;
+            uint4 u = make_uint4(0u, 0u, 0u, 0u);
+            ++walks;
+            for (int k = 0;; ++k) {
+                if (!(fabs(W) > wc)) break;
+                sum = __dadd_rn(sum, __dmul_rn(__dmul_rn(zeta[k], W), v ? v[l] : 1.0));
+                if (k >= K) break;
+                const Rec<true> x = rec[l];
+                if (x.deg == 0) break;
+                uint32_t w0, w1;
+                walk_words<WEIGHTED>(u, k, glo, ghi, req, key, w0, w1);
+                double mult;
+                const uint32_t nl = next_state<true, WEIGHTED>(x, w0, w1, col, went, mult);
+                W = __dmul_rn(W, mult);
+                l = nl;
+                ++steps;
+            }
+        }
+        warp_merge_add(t, sum, valid, lane, acc);
+    }
+    unsigned long long ws = steps, ww = walks;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        ws += __shfl_down_sync(0xffffffffu, ws, d);
+        ww += __shfl_down_sync(0xffffffffu, ww, d);
+    }
+    if (lane == 0) {
+        atomicAdd(&counters[C_STEPS], ws);
+        atomicAdd(&counters[C_WALKS], ww);
+    }
+}
+
+__global__ void mc_classic_finish(int64_t m, const double* __restrict__ acc, int64_t N, double* __restrict__ y) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x)
+        y[t] = acc[t] / (double)N;
+}
+
+static mcf_status solve_mc_classic(mcf_graph* g, const mcf_params* p, const double* v, const int64_t* nodes,
+                                   int64_t n_nodes, double* y, mcf_stats* stats) {
+    set_error("");
+    MCF_TRY(check_params(g, p));
+    if (!y) return fail(MCF_ERR_INVALID_ARG, "y is NULL");
+    if (p->precision != MCF_F64) return fail(MCF_ERR_UNSUPPORTED, "the classical method runs in float64 only");
+    if (p->walks_per_node < 1) return fail(MCF_ERR_INVALID_ARG, "walks_per_node (walks per entry) must be >= 1");
+    if (nodes && n_nodes < 0) return fail(MCF_ERR_INVALID_ARG, "n_nodes must be >= 0");
+    cudaStream_t st = (cudaStream_t)p->stream;
+    const int64_t n = g->n;
+    const int64_t m = nodes ? n_nodes : n;
+    const int64_t N = p->walks_per_node;
+    if (m > 0xffffffffLL) return fail(MCF_ERR_UNSUPPORTED, "at most 2^32 - 1 entries per call");
+    if (m > 0 && N > INT64_MAX / m) return fail(MCF_ERR_INVALID_ARG, "too many walks");
+    const double gamma = p->scale == 0.0 ? 1.0 : p->scale;
+    const int K = p->n_coeffs - 1;
+    keep_pool_memory();
+    Scratch sc(st);
+    const int64_t* nodes_dev = nullptr;
+    unsigned long long* counters;
+    MCF_TRY(sc.get(&counters, N_COUNTERS));
+    MCF_CUDA_TRY(cudaMemsetAsync(counters, 0, N_COUNTERS * sizeof(unsigned long long), st));
+    if (nodes && m > 0) {
+        if (is_device_ptr(nodes)) {
+            nodes_dev = nodes;
+            check_nodes<<<grid_for(m, 256), 256, 0, st>>>(m, nodes_dev, n, counters);
+            unsigned long long h = 0;
+            MCF_CUDA_TRY(cudaMemcpyAsync(&h, &counters[C_FLAGS], sizeof(h), cudaMemcpyDeviceToHost, st));
+            MCF_CUDA_TRY(cudaStreamSynchronize(st));
+            if (h & 2ull) return fail(MCF_ERR_INVALID_ARG, "node index out of range");
+        } else {
+            for (int64_t t = 0; t < m; ++t)
+                if (nodes[t] < 0 || nodes[t] >= n) return fail(MCF_ERR_INVALID_ARG, "node index out of range");
+            int64_t* nd;
+            MCF_TRY(sc.get(&nd, m));
+            MCF_CUDA_TRY(cudaMemcpyAsync(nd, nodes, m * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+            nodes_dev = nd;
+        }
+    }
+    const double* v_dev = v;
+    if (v && !is_device_ptr(v) && n > 0) {
+        double* vd;
+        MCF_TRY(sc.get(&vd, n));
+        MCF_CUDA_TRY(cudaMemcpyAsync(vd, v, n * sizeof(double), cudaMemcpyHostToDevice, st));
+        v_dev = vd;
+    }
+    const bool y_on_dev = is_device_ptr(y);
+    double* y_dev = y;
+    if (!y_on_dev) MCF_TRY(sc.get(&y_dev, std::max<int64_t>(m, 1)));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (m > 0) {
+        Rec<true>* rec;
+        double *acc, *zeta;
+        MCF_TRY(sc.get(&rec, n));
+        MCF_TRY(sc.get(&acc, m));
+        MCF_TRY(sc.get(&zeta, MCF_MAX_COEFFS));
+        MCF_CUDA_TRY(cudaMemcpyAsync(zeta, p->coeffs, p->n_coeffs * sizeof(double), cudaMemcpyHostToDevice, st));
+        MCF_CUDA_TRY(cudaMemsetAsync(acc, 0, m * sizeof(double), st));
+        build_records<true><<<grid_for(n, 256), 256, 0, st>>>(n, g->row_ptr, g->row_abs, gamma, nullptr, rec);
+        if (stats) {
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+            cudaEventRecord(e0, st);
+        }
+        const uint2 key = philox_key(p->seed);
+        if (g->weighted) {
+            auto kern = mc_classic_kernel<true>;
+            kern<<<persistent_grid(kern, 256, 0), 256, 0, st>>>(m, nodes_dev, N, rec, g->col_idx, g->went, v_dev,
+                                                                zeta, K, p->w_cutoff, key, p->request_id, acc,
+                                                                counters);
+        } else {
+            auto kern = mc_classic_kernel<false>;
+            kern<<<persistent_grid(kern, 256, 0), 256, 0, st>>>(m, nodes_dev, N, rec, g->col_idx, g->went, v_dev,
+                                                                zeta, K, p->w_cutoff, key, p->request_id, acc,
+                                                                counters);
+        }
+        MCF_CUDA_TRY(cudaGetLastError());
+        if (stats) cudaEventRecord(e1, st);
+        mc_classic_finish<<<grid_for(m, 256), 256, 0, st>>>(m, acc, N, y_dev);
+        MCF_CUDA_TRY(cudaGetLastError());
+    }
+    if (!y_on_dev && m > 0) MCF_CUDA_TRY(cudaMemcpyAsync(y, y_dev, m * sizeof(double), cudaMemcpyDeviceToHost, st));
+    mcf_status rc = finish_stats(stats, counters, e0, e1, st);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (rc != MCF_OK) return rc;
+    if (!y_on_dev) MCF_CUDA_TRY(cudaStreamSynchronize(st));
+    return MCF_OK;
+}
+
 // ====================================================================== allocation-free entry
 // mcf_total_communicability_noalloc runs the same kernels as
 // mcf_total_communicability, but every scratch buffer is carved from one
@@ -1084,6 +1670,7 @@ static mcf_status solve_tc_noalloc(int64_t n, int64_t nnz, const int64_t* row_pt
     double* acc = cv.take<double>(NOALLOC_MAX_NODES);
     P.starts = cv.take<int32_t>(NOALLOC_MAX_NODES);
     P.soff = cv.take<int64_t>(NOALLOC_MAX_NODES + 1);
+    P.cof = P.soff;   // every start is walked: walk ids and walked space coincide
     P.rec = cv.take<Rec<true>>(NOALLOC_MAX_NODES);
     uint32_t* chunk_s0 = cv.take<uint32_t>(NOALLOC_MAX_WALKS / WARP_CHUNK + 2);
     P.scan_bytes = 8 * ((NOALLOC_MAX_NODES + 4095) / 4096 + 1);
@@ -1145,6 +1732,12 @@ mcf_status mcf_action(mcf_graph_t g, const mcf_params* params, const double* v, 
     return solve_action(g, params, v, y, stats, false);
 }
 
+mcf_status mcf_action_nodes(mcf_graph_t g, const mcf_params* params, const double* v, const int64_t* nodes,
+                            int64_t n_nodes, double* y, mcf_stats* stats) {
+    if (!nodes) return fail(MCF_ERR_INVALID_ARG, "nodes is NULL");
+    return solve_action(g, params, v, y, stats, v == nullptr, nodes, n_nodes);
+}
+
 mcf_status mcf_total_communicability(mcf_graph_t g, const mcf_params* params, double* y, mcf_stats* stats) {
     return solve_action(g, params, nullptr, y, stats, true);
 }
@@ -1177,6 +1770,15 @@ mcf_status mcf_katz(mcf_graph_t g, double gamma, int32_t K, const mcf_params* pa
     p.n_coeffs = K + 1;
     p.scale = gamma;
     return solve_action(g, &p, nullptr, y, stats, true);
+}
+
+mcf_status mcf_funm_full(mcf_graph_t g, const mcf_params* params, double* F, mcf_stats* stats) {
+    return solve_full(g, params, F, stats);
+}
+
+mcf_status mcf_mc_classic(mcf_graph_t g, const mcf_params* params, const double* v, const int64_t* nodes,
+                          int64_t n_nodes, double* y, mcf_stats* stats) {
+    return solve_mc_classic(g, params, v, nodes, n_nodes, y, stats);
 }
 
 mcf_status mcf_total_communicability_noalloc(int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,

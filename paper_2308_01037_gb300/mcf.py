@@ -89,9 +89,12 @@ SIGNATURES = {
     "mcf_spectral_radius": ([_P, _D, _I32, _P], ctypes.c_int),
     "mcf_gershgorin": ([_P, _P], ctypes.c_int),
     "mcf_action": ([_P, _P, _P, _P, _P], ctypes.c_int),
+    "mcf_action_nodes": ([_P, _P, _P, _P, _I64, _P, _P], ctypes.c_int),
     "mcf_total_communicability": ([_P, _P, _P, _P], ctypes.c_int),
     "mcf_subgraph_centrality": ([_P, _P, _P, _I64, _P, _P], ctypes.c_int),
     "mcf_katz": ([_P, _D, _I32, _P, _P, _P], ctypes.c_int),
+    "mcf_funm_full": ([_P, _P, _P, _P], ctypes.c_int),
+    "mcf_mc_classic": ([_P, _P, _P, _P, _I64, _P, _P], ctypes.c_int),
     "mcf_batch_create": ([_P, _I32, _U32, _P, _P], ctypes.c_int),
     "mcf_batch_run": ([_P, _P, _P], ctypes.c_int),
     "mcf_batch_destroy": ([_P], ctypes.c_int),
@@ -252,6 +255,19 @@ def mcf_action(g: GraphHandle, v, coeffs, out=None, device_out=None, stats=False
     return (y, st.as_dict()) if stats else y
 
 
+def mcf_action_nodes(g: GraphHandle, nodes, coeffs, v=None, out=None, device_out=None, stats=False, **kw):
+    """Entries ``nodes`` of f(A')v (v = None: total communicability), walking only their neighbours."""
+    y = _output(out, len(nodes), device_out if device_out is not None else nodes)
+    vp, kv = _ptr(v, np.float64)
+    npt, kn = _ptr(nodes, np.int64)
+    yp, ky = _ptr(y, np.float64)
+    st = mcf_stats()
+    p, kc = _params(coeffs, stream=kw.pop("stream", None) or _stream_of(nodes, y), **kw)
+    _check(load().mcf_action_nodes(g.handle, ctypes.byref(p), vp, npt, int(len(nodes)), yp,
+                                   ctypes.byref(st) if stats else None))
+    return (y, st.as_dict()) if stats else y
+
+
 def mcf_total_communicability(g: GraphHandle, coeffs, out=None, device_out=None, stats=False, **kw):
     """f(A')1 (total communicability)."""
     y = _output(out, g.n, device_out)
@@ -283,6 +299,37 @@ def mcf_katz(g: GraphHandle, gamma, K=0, out=None, device_out=None, stats=False,
     p, kc = _params([1.0], stream=kw.pop("stream", None) or _stream_of(y), **kw)
     _check(load().mcf_katz(g.handle, float(gamma), int(K), ctypes.byref(p), yp,
                            ctypes.byref(st) if stats else None))
+    return (y, st.as_dict()) if stats else y
+
+
+MCF_FULL_MAX_NODES = 16384
+
+
+def mcf_funm_full(g: GraphHandle, coeffs, out=None, device_out=None, stats=False, **kw):
+    """Dense estimate F (n x n, row-major) of f(A') by RandFunm (Algorithm 2)."""
+    F = _output(out, g.n * g.n, device_out)
+    Fp, kf = _ptr(F, np.float64)
+    st = mcf_stats()
+    p, kc = _params(coeffs, stream=kw.pop("stream", None) or _stream_of(F), **kw)
+    _check(load().mcf_funm_full(g.handle, ctypes.byref(p), Fp, ctypes.byref(st) if stats else None))
+    F = F.reshape(g.n, g.n)
+    return (F, st.as_dict()) if stats else F
+
+
+def mcf_mc_classic(g: GraphHandle, coeffs, walks_per_row, v=None, nodes=None, out=None, device_out=None,
+                   stats=False, **kw):
+    """Entries of f(A')v by the classical Monte Carlo method (Algorithm 1), float64."""
+    m = g.n if nodes is None else len(nodes)
+    y = _output(out, m, device_out if device_out is not None else (nodes if nodes is not None else v))
+    vp, kv = _ptr(v, np.float64)
+    npt, kn = _ptr(nodes, np.int64)
+    yp, ky = _ptr(y, np.float64)
+    st = mcf_stats()
+    kw.setdefault("precision", MCF_F64)
+    p, kc = _params(coeffs, walks_per_node=int(walks_per_row), stream=kw.pop("stream", None) or _stream_of(v, nodes, y),
+                    **kw)
+    _check(load().mcf_mc_classic(g.handle, ctypes.byref(p), vp, npt, int(m), yp,
+                                 ctypes.byref(st) if stats else None))
     return (y, st.as_dict()) if stats else y
 
 

@@ -123,6 +123,26 @@ def test_weighted_signed_matrix(precision):
     assert_parity(d, refd["d"])
 
 
+@pytest.mark.parametrize("precision", [M.MCF_F64, M.MCF_F32W_F64ACC])
+def test_action_node_subset_equals_full_run(rmat12, precision):
+    """Single-entry / subset total communicability (Section 4.3): the entries equal the
+    full run's (same walk ids) and the oracle's subset computation."""
+    g, h, gam = rmat12
+    c = R.exp_coeffs(30)
+    hub = int(np.argmax(g.degree))
+    nodes = np.array([hub, 3, 3, g.n - 1, 100, 2047], dtype=np.int64)
+    kw = dict(scale=gam, n_walks=200000, w_cutoff=1e-6, seed=6, precision=precision)
+    sub, st = M.mcf_action_nodes(h, nodes, c, stats=True, **kw)
+    full = M.mcf_total_communicability(h, c, **kw)
+    assert_parity(sub, full[nodes])
+    ref = E.action(g, c, gamma=gam, n_walks=200000, w_cutoff=1e-6, seed=6, precision=precision, nodes=nodes)
+    assert_parity(sub, ref["y"])
+    assert st["walks"] == ref["walks"] and st["walk_steps"] == ref["steps"]
+    v = np.random.default_rng(5).standard_normal(g.n)
+    dsub = M.mcf_action_nodes(h, torch.from_numpy(nodes).cuda(), c, v=torch.from_numpy(v).cuda(), **kw)
+    assert_parity(dsub.cpu().numpy(), M.mcf_action(h, v, c, **kw)[nodes])
+
+
 # ------------------------------------------------------------------ subgraph centrality
 @pytest.mark.parametrize("precision", [M.MCF_F64, M.MCF_F32W_F64ACC])
 def test_subgraph_centrality_dense_row(ba1000, precision):
@@ -136,9 +156,9 @@ def test_subgraph_centrality_dense_row(ba1000, precision):
 
 @pytest.mark.parametrize("precision", [M.MCF_F64, M.MCF_F32W_F64ACC])
 def test_subgraph_centrality_hashed_row_with_flushes(precision):
-    # n > 12288 selects the shared-memory hash; 3000 walks of up to 28 steps from a
-    # hub overflow its 8192 slots, exercising the flush-and-replay path
-    g = I.rmat(14, 16, seed=7)
+    # n > 16384 selects the hashed row Q_k (at most 2^14 slots); 3000 walks of up
+    # to 28 steps from a hub overflow it, exercising the flush-and-replay path
+    g = I.rmat(15, 16, seed=7)
     gam = 1.0 / R.lambda_max(g)
     h = upload(g)
     c = R.exp_coeffs(30)
