@@ -385,6 +385,78 @@ def run_serving(M, R, I, scales, n_requests, rate=200.0, seed=5):
             "walk_budgets": "TC 16 n walks, Katz (gamma 0.85/Gershgorin) 16 per node, SC 32 per node on 1e4 sampled nodes"}
 
 
+def run_funm_full(M, R, I, n=16384, m=8, wpn=100, reps=3):
+    """Dense RandFunm (Algorithm 2) at the largest supported n: time of one
+    solve (walks + the A'QA' epilogue), and the error of F 1 and of diag F on
+    sampled nodes against the float64 series."""
+    import torch
+
+    g = I.barabasi_albert(n, m, 31)
+    h = M.mcf_create_graph(g.n, g.row_ptr, g.col_idx)
+    gam = 1.0 / M.mcf_spectral_radius(h)
+    c = exp_coeffs(30)
+    out = torch.empty(g.n * g.n, dtype=torch.float64, device="cuda")
+    kw = dict(scale=gam, walks_per_node=wpn, w_cutoff=1e-6, seed=2, precision=M.MCF_F32W_F64ACC)
+    M.mcf_funm_full(h, c, out=out, **kw)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    walk_ms = []
+    for i in range(reps):
+        _, st = M.mcf_funm_full(h, c, out=out, stats=True, request_id=i, **kw)
+        walk_ms.append(st["kernel_ms"])
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    F = out.view(g.n, g.n)
+    ones = torch.ones(g.n, dtype=torch.float64, device="cuda")
+    y = (F @ ones).cpu().numpy()
+    ref = R.series_action(g, c, gam)
+    nodes = np.arange(0, g.n, g.n // 128)
+    dref = R.series_diag(g, c, nodes, gam)
+    d = torch.diagonal(F).cpu().numpy()[nodes]
+    res = {"graph": f"BA n={n} m={m}", "nnz": g.nnz, "walks_per_node": wpn, "ms_per_solve": ms,
+           "walk_kernel_ms": float(np.mean(walk_ms)), "walk_steps": st["walk_steps"],
+           "epilogue_min_hbm_bytes": int(g.nnz * g.n * 8 + g.n * g.n * 8),
+           "rel_err_F1_vs_fp64": float(np.abs(y - ref).max() / np.abs(ref).max()),
+           "rel_err_diag_vs_fp64": float(np.abs(d - dref).max() / np.abs(dref).max())}
+    del F, out
+    h.close()
+    return res
+
+
+def run_mc_classic(M, R, I, n=1000, m=3, wpn=10_000):
+    """The classical method (Algorithm 1) against row sampling (Algorithm 3)
+    at the same number of walks per node, float64 both: error of f(A')1
+    against the float64 series and walk-steps/s."""
+    import torch
+
+    g = I.barabasi_albert(n, m, 0)
+    h = M.mcf_create_graph(g.n, g.row_ptr, g.col_idx)
+    gam = 1.0 / M.mcf_spectral_radius(h)
+    c = exp_coeffs(30)
+    ref = R.series_action(g, c, gam)
+    res = {"graph": f"BA n={n} m={m}", "walks_per_node": wpn}
+    for name, fn in (("classic", lambda i: M.mcf_mc_classic(h, c, wpn, scale=gam, seed=3, request_id=i, stats=True)),
+                     ("row_sampling", lambda i: M.mcf_total_communicability(
+                         h, c, scale=gam, walks_per_node=wpn, seed=3, request_id=i, precision=M.MCF_F64,
+                         stats=True))):
+        fn(100)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        errs, steps = [], 0
+        for i in range(3):
+            y, st = fn(i)
+            steps += st["walk_steps"]
+            errs.append(float(np.abs(y - ref).max() / np.abs(ref).max()))
+        el = time.perf_counter() - t0
+        res[name] = {"rel_err_vs_fp64": float(np.mean(errs)), "walk_steps_per_s": steps / el,
+                     "solves_per_s": 3 / el}
+    res["error_ratio_classic_over_row_sampling"] = res["classic"]["rel_err_vs_fp64"] / res["row_sampling"]["rel_err_vs_fp64"]
+    h.close()
+    return res
+
+
 def run_reference(args, w):
     """--impl reference: the oracle as it stands, timed on the host cores."""
     rank = int(os.environ.get("RANK", "0"))
@@ -426,15 +498,27 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
-    ap.add_argument("--no-batch", action="store_true", help="skip the batched and serving measurements")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched, serving, dense RandFunm and classical-method measurements")
     ap.add_argument("--batch-graphs", type=int, default=64)
     ap.add_argument("--batch-log-n-max", type=float, default=5.0)
     ap.add_argument("--serve-scales", default="14-20")
     ap.add_argument("--serve-requests", type=int, default=600)
+    ap.add_argument("--section", default="main", choices=["main", "funm_full", "mc_classic"],
+                    help="funm_full / mc_classic: run only that measurement (1 GPU) and print its JSON")
+    ap.add_argument("--funm-n", type=int, default=16384, help="nodes of the dense RandFunm measurement")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, w)
+    if args.section != "main":
+        from oracle import reference as R
+        from paper_2308_01037_gb300 import inputs as I
+        from paper_2308_01037_gb300 import mcf as M
+
+        M.load()
+        res = run_funm_full(M, R, I, n=args.funm_n) if args.section == "funm_full" else run_mc_classic(M, R, I)
+        print(json.dumps({"section": args.section, **res}), flush=True)
+        return
 
     import torch
 
@@ -539,7 +623,7 @@ def main():
             dist.all_reduce(t)
             e2e["value"] = float(t.item())
 
-    batched = serving = None
+    batched = serving = funm_full = mc_classic = None
     if rank == 0 and world == 1 and not args.no_batch:
         from oracle import reference as R
         from paper_2308_01037_gb300 import inputs as I
@@ -547,6 +631,8 @@ def main():
         batched = run_batched(M, R, I, args.batch_graphs, args.batch_log_n_max)
         lo, hi = (int(x) for x in args.serve_scales.split("-"))
         serving = run_serving(M, R, I, list(range(lo, hi + 1)), args.serve_requests)
+        funm_full = run_funm_full(M, R, I)
+        mc_classic = run_mc_classic(M, R, I)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(g, lam, w)
@@ -570,7 +656,7 @@ def main():
                          "the R-MAT scale 21 case (one 32-B sector per random step) x the walk steps of a launch"},
             "clocks": clk.summary(), "e2e": e2e, "gpu_launches": args.steps * LAUNCHES_PER_SOLVE[w["query"]],
             "cpu_baseline": cpu,
-            "batched": batched, "serving": serving,
+            "batched": batched, "serving": serving, "funm_full": funm_full, "mc_classic": mc_classic,
         }
         print(json.dumps(line), flush=True)
     h.close()

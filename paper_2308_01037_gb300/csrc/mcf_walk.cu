@@ -1280,37 +1280,97 @@ __global__ void __launch_bounds__(128) walk_full_kernel(
     }
 }
 
+// ce[p] = gamma a_p / N_{col p}: the entries of A' diag(1/N) that scale the
+// rows of N Q (Eq. rand_funm_Q); 0 where column col p has no walks (its row
+// of Q is zero).
+__global__ void full_edge_coeffs(int64_t nnz, const int32_t* __restrict__ col, const float* __restrict__ val,
+                                 const int64_t* __restrict__ nw, double gamma, double* __restrict__ ce) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t Nm = nw[col[p]];
+        ce[p] = Nm == 0 ? 0.0 : (gamma * (val ? (double)val[p] : 1.0)) / (double)Nm;
+    }
+}
+
 // F = zeta_0 I + zeta_1 A' + A' Q A' (Algorithm 2, last step) one row i at a
 // time: row i of A'Q is formed in shared memory from the rows of N Q of i's
-// neighbours, each divided by its N_m (Eq. rand_funm_Q); then
+// neighbours (each scaled by ce), then
 // F_ij = zeta_0 [i == j] + sum_{m in N(j)} a'_jm (A'Q)_im (a'_jm = a'_mj for a
 // symmetric A, so row j of A' serves as column j), and finally
-// zeta_1 a'_ij is added for the entries of row i.
-__global__ void __launch_bounds__(512) full_epilogue(int64_t n, const int64_t* __restrict__ rp,
-                                                     const int32_t* __restrict__ col, const float* __restrict__ val,
-                                                     const double* __restrict__ Q, const int64_t* __restrict__ nw,
-                                                     double gamma, double z0, double z1, int K,
-                                                     double* __restrict__ F) {
+// zeta_1 a'_ij is added for the entries of row i.  Both products cost one
+// float64 FMA per (i, j, entry): the kernel is bound by the float64 pipe, so
+// no float64 division is left in its loops.  Each thread accumulates four
+// columns j at once so that four row loads are in flight.
+constexpr int FULL_THREADS = 1024;
+
+// sum_{p in row} a_p x[col p] for the 32 rows base + lane (warp_row_sums with
+// the binary case specialised: one float64 add per entry instead of a
+// multiply and an add).
+template <bool WEIGHTED>
+__device__ __forceinline__ double full_row_sums(int64_t base, int64_t n, const int64_t* __restrict__ rp,
+                                                const int32_t* __restrict__ col, const float* __restrict__ val,
+                                                const double* __restrict__ x) {
+    if constexpr (WEIGHTED) {
+        return warp_row_sums<32>(base, n, rp, col, val, x);
+    } else {
+        const int lane = threadIdx.x & 31;
+        const int64_t row = base + lane;
+        int64_t b = 0, e = 0;
+        if (row < n) {
+            b = rp[row];
+            e = rp[row + 1];
+        }
+        double s = 0.0;
+        const bool is_short = e - b <= 32;
+        if (is_short)
+            for (int64_t p = b; p < e; ++p) s += x[col[p]];
+        unsigned longs = __ballot_sync(0xffffffffu, !is_short);
+        while (longs) {
+            const int t = __ffs(longs) - 1;
+            longs &= longs - 1;
+            const int64_t lb = __shfl_sync(0xffffffffu, b, t);
+            const int64_t le = __shfl_sync(0xffffffffu, e, t);
+            double part = 0.0;
+            for (int64_t p = lb + lane; p < le; p += 32) part += x[col[p]];
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) part += __shfl_xor_sync(0xffffffffu, part, d);
+            if (lane == t) s = part;
+        }
+        return s;
+    }
+}
+
+template <bool WEIGHTED>
+__global__ void __launch_bounds__(FULL_THREADS) full_epilogue(
+    int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const float* __restrict__ val,
+    const double* __restrict__ Q, const double* __restrict__ ce, double gamma, double z0, double z1, int K,
+    double* __restrict__ F) {
     extern __shared__ double aq[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int64_t B = blockDim.x;
     for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
         const int64_t b = rp[i], e = rp[i + 1];
-        for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
-            double a = 0.0;
-            if (K >= 2)
+        for (int64_t j0 = threadIdx.x; j0 < n; j0 += 4 * B) {
+            double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+            if (K >= 2) {
+                const bool h1 = j0 + B < n, h2 = j0 + 2 * B < n, h3 = j0 + 3 * B < n;
                 for (int64_t p = b; p < e; ++p) {
-                    const int32_t m = col[p];
-                    const int64_t Nm = nw[m];
-                    if (Nm == 0) continue;   // no walks from column m: its row of Q is zero
-                    const double q = __ddiv_rn(__ldcs(Q + (int64_t)m * n + j), (double)Nm);
-                    a = __dadd_rn(a, __dmul_rn(__dmul_rn(gamma, val ? (double)val[p] : 1.0), q));
+                    const double c = ce[p];
+                    const double* row = Q + (int64_t)col[p] * n + j0;
+                    a0 = fma(c, __ldg(row), a0);
+                    if (h1) a1 = fma(c, __ldg(row + B), a1);
+                    if (h2) a2 = fma(c, __ldg(row + 2 * B), a2);
+                    if (h3) a3 = fma(c, __ldg(row + 3 * B), a3);
                 }
-            aq[j] = a;
+            }
+            aq[j0] = a0;
+            if (j0 + B < n) aq[j0 + B] = a1;
+            if (j0 + 2 * B < n) aq[j0 + 2 * B] = a2;
+            if (j0 + 3 * B < n) aq[j0 + 3 * B] = a3;
         }
         __syncthreads();
         double* Fi = F + i * n;
         for (int64_t base = (int64_t)wid * 32; base < n; base += (int64_t)nwarp * 32) {
-            const double s = warp_row_sums<32>(base, n, rp, col, val, aq);
+            const double s = full_row_sums<WEIGHTED>(base, n, rp, col, val, aq);
             const int64_t j = base + lane;
             if (j < n) Fi[j] = (j == i ? z0 : 0.0) + gamma * s;
         }
@@ -1373,12 +1433,19 @@ static mcf_status solve_full(mcf_graph* g, const mcf_params* p, double* F, mcf_s
             MCF_CUDA_TRY(cudaGetLastError());
             if (stats) cudaEventRecord(e1, st);
         }
+        double* ce;
+        MCF_TRY(sc.get(&ce, (size_t)std::max<int64_t>(g->nnz, 1)));
+        if (K >= 2 && g->nnz > 0)
+            full_edge_coeffs<<<grid_for(g->nnz, 256), 256, 0, st>>>(g->nnz, g->col_idx, g->values, P.nw, gamma, ce);
+        // two CTAs per SM (one works while the other waits at a barrier)
+        // when two rows of A'Q fit in shared memory, else one larger CTA
         const size_t smem = (size_t)n * sizeof(double);
-        MCF_CUDA_TRY(cudaFuncSetAttribute(full_epilogue, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        const int grid = (int)std::min<int64_t>(n, persistent_grid(full_epilogue, 512, smem));
+        const int threads = 2 * smem <= 200 * 1024 ? FULL_THREADS / 2 : FULL_THREADS;
         const double z0 = p->coeffs[0], z1 = K >= 1 ? p->coeffs[1] : 0.0;
-        full_epilogue<<<grid, 512, smem, st>>>(n, g->row_ptr, g->col_idx, g->values, Q, P.nw, gamma, z0, z1, K,
-                                               F_dev);
+        auto kern = g->weighted ? full_epilogue<true> : full_epilogue<false>;
+        MCF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const int grid = (int)std::min<int64_t>(n, persistent_grid(kern, threads, smem));
+        kern<<<grid, threads, smem, st>>>(n, g->row_ptr, g->col_idx, g->values, Q, ce, gamma, z0, z1, K, F_dev);
         MCF_CUDA_TRY(cudaGetLastError());
     }
     if (!f_on_dev && n > 0)
@@ -1397,7 +1464,8 @@ static mcf_status solve_full(mcf_graph* g, const mcf_params* p, double* F, mcf_s
 // |a_lj| / sum_j |a_lj| and multiplies W by sign(a_lj) sum_j |a'_lj| (the same
 // chain as the row-sampling walks, Definition 1).  Walk ids are i * N + s.
 // Walks are laid out t-major; every warp takes 32 consecutive walks, sums each
-// walk in float64 and adds the walks of one output with one atomic.
+// walk in float64 (one FMA per visit) and adds the walks of one output with
+// one atomic.
 template <bool WEIGHTED>
 __global__ void __launch_bounds__(256) mc_classic_kernel(
     int64_t m, const int64_t* __restrict__ nodes, int64_t N, const Rec<true>* __restrict__ rec,
@@ -1408,6 +1476,7 @@ __global__ void __launch_bounds__(256) mc_classic_kernel(
     for (int k = threadIdx.x; k <= K; k += blockDim.x) zeta[k] = zeta_g[k];
     __syncthreads();
     const int lane = threadIdx.x & 31;
+    const long long wc_bits = __double_as_longlong(wc);   // wc >= 0
     const int64_t total = m * N;
     const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -1428,8 +1497,12 @@ __global__ void __launch_bounds__(256) mc_classic_kernel(
             uint4 u = make_uint4(0u, 0u, 0u, 0u);
             ++walks;
             for (int k = 0;; ++k) {
-                if (!(fabs(W) > wc)) break;
-                sum = __dadd_rn(sum, __dmul_rn(__dmul_rn(zeta[k], W), v ? v[l] : 1.0));
+                // |W| > W_c on the bit patterns (ordered like the values for
+                // non-negative doubles), keeping the float64 pipe for the sums
+                const long long wb = __double_as_longlong(W) & 0x7fffffffffffffffLL;
+                if (!(wb > wc_bits && wb <= 0x7ff0000000000000LL)) break;
+                if (v) sum = fma(zeta[k] * W, v[l], sum);
+                else sum = fma(zeta[k], W, sum);
                 if (k >= K) break;
                 const Rec<true> x = rec[l];
                 if (x.deg == 0) break;
