@@ -31,9 +31,12 @@
  *    2(k % 2) + 1 of block k / 2, bucket b = (w0 * deg) >> 32 and
  *    x = (w1 >> 8) * 2^-24 for Vose's alias table.
  *  - For a binary A the row sums and column norms are evaluated in closed
- *    form: sum_j |a'_ij| = gamma * deg_i, ||C_i||_2 = gamma * sqrt(deg_i).
- *    For a weighted A: gamma * (sum_j |a_ij|) and gamma * sqrt(sum_j a_ij^2),
- *    the inner sums in CSR order.  A is symmetric, so column i equals row i.
+ *    form: sum_j |a'_ij| = gamma * deg_i, ||C_i||_2 = gamma * sqrt(indeg_i).
+ *    For a weighted A: gamma * (sum_j |a_ij|) in CSR order and
+ *    gamma * sqrt(sum_j a_ji^2) over column i in increasing row order.  A
+ *    need not be symmetric: columns are read from a column-major copy (for
+ *    a symmetric A with sorted rows it holds the same values in the same
+ *    order as the rows).
  *  - r = A' v is evaluated as gamma * (sum_j a_ij v_j), the sum in CSR order.
  *  - Precision 0: every quantity is double.  Precision 1: walk weight W,
  *    coefficients, r and row-sum multipliers are float (round to nearest, no
@@ -89,10 +92,14 @@ typedef struct {
     int64_t* off;       /* exclusive prefix of N_i: walk ids of start i are off[i] .. off[i+1]-1 */
     float* prob;        /* alias tables for weighted rows (nnz) */
     int32_t* alias;
+    int64_t* cp;        /* column-major copy of A: column i holds rows ri[cp[i] .. cp[i+1]) */
+    int32_t* ri;        /* in increasing row order, with values cv (NULL when binary)      */
+    float* cv;
 } chain_t;
 
 static void chain_free(chain_t* c) {
     free(c->rowabs); free(c->colnorm); free(c->nw); free(c->off); free(c->prob); free(c->alias);
+    free(c->cp); free(c->ri); free(c->cv);
     memset(c, 0, sizeof(*c));
 }
 
@@ -133,17 +140,38 @@ static int chain_build(chain_t* c, int64_t n, const int64_t* rp, const int32_t* 
     c->colnorm = (double*)malloc((size_t)(n + 1) * sizeof(double));
     c->nw = (int64_t*)malloc((size_t)(n + 1) * sizeof(int64_t));
     c->off = (int64_t*)malloc((size_t)(n + 1) * sizeof(int64_t));
-    if (!c->rowabs || !c->colnorm || !c->nw || !c->off) { chain_free(c); return -2; }
+    /* column-major copy by counting sort; rows are visited in increasing order */
+    int64_t nnz = rp[n];
+    c->cp = (int64_t*)calloc((size_t)(n + 2), sizeof(int64_t));
+    c->ri = (int32_t*)malloc((size_t)(nnz + 1) * sizeof(int32_t));
+    c->cv = val ? (float*)malloc((size_t)(nnz + 1) * sizeof(float)) : NULL;
+    int64_t* cur = (int64_t*)malloc((size_t)(n + 1) * sizeof(int64_t));
+    if (!c->rowabs || !c->colnorm || !c->nw || !c->off || !c->cp || !c->ri || (val && !c->cv) || !cur) {
+        free(cur); chain_free(c); return -2;
+    }
+    for (int64_t p = 0; p < nnz; ++p) {
+        if (ci[p] < 0 || ci[p] >= n) { free(cur); chain_free(c); return -1; }
+        c->cp[ci[p] + 1] += 1;
+    }
+    for (int64_t i = 0; i < n; ++i) c->cp[i + 1] += c->cp[i];
+    for (int64_t i = 0; i < n; ++i) cur[i] = c->cp[i];
+    for (int64_t r = 0; r < n; ++r)
+        for (int64_t p = rp[r]; p < rp[r + 1]; ++p) {
+            int64_t q = cur[ci[p]]++;
+            c->ri[q] = (int32_t)r;
+            if (val) c->cv[q] = val[p];
+        }
+    free(cur);
     for (int64_t i = 0; i < n; ++i) {
         int64_t d = rp[i + 1] - rp[i];
         if (!val) {
             c->rowabs[i] = gamma * (double)d;
-            c->colnorm[i] = gamma * sqrt((double)d);
+            c->colnorm[i] = gamma * sqrt((double)(c->cp[i + 1] - c->cp[i]));
         } else {
             double sa = 0.0, sq = 0.0;
-            for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
-                double a = (double)val[p];
-                sa += fabs(a);
+            for (int64_t p = rp[i]; p < rp[i + 1]; ++p) sa += fabs((double)val[p]);
+            for (int64_t q = c->cp[i]; q < c->cp[i + 1]; ++q) {
+                double a = (double)c->cv[q];
                 sq += a * a;
             }
             c->rowabs[i] = gamma * sa;
@@ -386,15 +414,14 @@ int orc_diag(int64_t n, const int64_t* rp, const int32_t* ci, const float* val, 
                 steps += run_walk(&c, k, c.off[k] + s, zeta, K, w_cutoff, seed, req, precision, diag_visit, &dc);
                 ++walks;
             }
-            /* d_i += a'_ik <Q_k, C'_i> for every i with a_ik != 0 */
-            for (int64_t p = rp[k]; p < rp[k + 1]; ++p) {
-                int64_t i = ci[p];
+            /* d_i += a'_ik <Q_k, C'_i> for every i with a_ik != 0 (the rows i of column k) */
+            for (int64_t p = c.cp[k]; p < c.cp[k + 1]; ++p) {
+                int64_t i = c.ri[p];
                 if (pos[i] < 0) continue;
                 double dot = 0.0;
-                for (int64_t t = rp[i]; t < rp[i + 1]; ++t)
-                    dot += (gamma * (val ? (double)val[t] : 1.0)) * dc.Q[ci[t]];
-                /* a'_ik = a'_ki by symmetry */
-                double aik = gamma * (val ? (double)val[p] : 1.0);
+                for (int64_t t = c.cp[i]; t < c.cp[i + 1]; ++t)   /* column i: entries a_ji */
+                    dot += (gamma * (c.cv ? (double)c.cv[t] : 1.0)) * dc.Q[c.ri[t]];
+                double aik = gamma * (c.cv ? (double)c.cv[p] : 1.0);
                 acc[i] += (aik * dot) / (double)c.nw[k];
             }
             for (int64_t t = 0; t < dc.ntouched; ++t) { dc.Q[dc.touched[t]] = 0.0; dc.seen[dc.touched[t]] = 0; }
@@ -462,10 +489,10 @@ int orc_funm_full(int64_t n, const int64_t* rp, const int32_t* ci, const float* 
             if (K >= 1) F[i * n + ci[p]] += zeta[1] * a;
         }
     }
-    for (int64_t j = 0; j < n; ++j)           /* column j of A' equals row j */
-        for (int64_t p = rp[j]; p < rp[j + 1]; ++p) {
-            double a = gamma * (val ? (double)val[p] : 1.0);
-            int64_t m = ci[p];
+    for (int64_t j = 0; j < n; ++j)           /* column j of A': entries a'_mj */
+        for (int64_t p = c.cp[j]; p < c.cp[j + 1]; ++p) {
+            double a = gamma * (c.cv ? (double)c.cv[p] : 1.0);
+            int64_t m = c.ri[p];
             for (int64_t i = 0; i < n; ++i) F[i * n + j] += AQ[i * n + m] * a;
         }
     free(Qm); free(AQ); free(dc.touched); free(dc.seen);

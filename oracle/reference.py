@@ -34,6 +34,13 @@ def katz_coeffs(K: int) -> np.ndarray:
     return np.ones(K + 1, dtype=np.float64)
 
 
+def mittag_leffler_coeffs(K: int, alpha: float, beta: float = 1.0) -> np.ndarray:
+    """zeta_k = 1 / Gamma(alpha k + beta), k = 0..K: the Mittag-Leffler function
+    E_{alpha,beta} (Section 1 names it among the functions the power series covers)."""
+    return np.array([math.exp(-math.lgamma(alpha * k + beta)) if alpha * k + beta > 0 else 0.0
+                     for k in range(K + 1)], dtype=np.float64)
+
+
 def katz_terms_for_tail(rho: float, tol: float) -> int:
     """Smallest K with rho^(K+1) / (1 - rho) <= tol (geometric tail of the Neumann series)."""
     if not (0.0 < rho < 1.0):
@@ -119,6 +126,7 @@ def _chain(g, values, gamma):
     nbr, aval, tval = [], [], []
     rowabs = np.zeros(n)
     colnorm = np.zeros(n)
+    colsq = np.zeros(n)
     for i in range(n):
         cols = g.col_idx[g.row_ptr[i]:g.row_ptr[i + 1]].tolist()
         a = ([1.0] * len(cols)) if values is None else [float(x) for x in values[g.row_ptr[i]:g.row_ptr[i + 1]]]
@@ -128,7 +136,9 @@ def _chain(g, values, gamma):
         aval.append(a)
         tval.append([abs(x) / s for x in a] if s > 0 else [])
         rowabs[i] = s
-        colnorm[i] = math.sqrt(sum(x * x for x in a))   # column i = row i (symmetric)
+        for j, x in zip(cols, a):
+            colsq[j] += x * x            # column j collects a'_ij over the rows i
+    colnorm = np.sqrt(colsq)
     return nbr, aval, tval, rowabs, colnorm
 
 
@@ -207,20 +217,21 @@ def enumerate_diag(g, coeffs, gamma: float = 1.0, w_cutoff: float = 0.0, values=
     K = len(coeffs) - 1
     n = g.n
     nbr, aval, tval, rowabs, colnorm = _chain(g, values, gamma)
-    # column i of A' as a dense vector (symmetric: equals row i)
-    Acol = np.zeros((n, n))
+    # Arow[l] = row l of A' (a'_li for every i): what a visit of l adds to Y_{k, .}
+    Arow = np.zeros((n, n))
     for i in range(n):
         for j, a in zip(nbr[i], aval[i]):
-            Acol[i, j] = a
-    mean = np.array([coeffs[0] + (coeffs[1] * Acol[i, i] if K >= 1 else 0.0) for i in range(n)])
+            Arow[i, j] += a
+    mean = np.array([coeffs[0] + (coeffs[1] * Arow[i, i] if K >= 1 else 0.0) for i in range(n)])
     var = np.zeros(n)
     if K >= 2:
         for k in range(n):
             if colnorm[k] == 0:
                 continue
             # contribution vector of visiting l: Y_{k,i} += zeta W a'_li for every i
-            e1, e2 = _walk_moments(nbr, aval, tval, k, coeffs, w_cutoff, lambda l: Acol[l])
-            for i, a in zip(nbr[k], aval[k]):
+            e1, e2 = _walk_moments(nbr, aval, tval, k, coeffs, w_cutoff, lambda l: Arow[l])
+            for i in np.nonzero(Arow[:, k])[0]:        # the rows i of column k: a'_ik != 0
+                a = Arow[i, k]
                 mean[i] += a * e1[i]
                 if nw is not None and nw[k] > 0:
                     var[i] += a * a * max(e2[i] - e1[i] ** 2, 0.0) / nw[k]

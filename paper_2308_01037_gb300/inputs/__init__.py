@@ -2,10 +2,12 @@
 tests and the benchmark.
 
 This module draws graphs only; it contains none of the Monte Carlo method's
-arithmetic.  Every generator returns a :class:`Graph` holding a symmetric,
-loop-free, duplicate-free CSR adjacency structure (``row_ptr`` int64 of length
-n+1, ``col_idx`` int32, rows sorted) -- the matrix class of the paper's
-Section 2.1.  The C implementation lives in ``graphgen.c`` and is compiled on
+arithmetic.  Every undirected generator returns a :class:`Graph` holding a
+symmetric, loop-free, duplicate-free CSR adjacency structure (``row_ptr``
+int64 of length n+1, ``col_idx`` int32, rows sorted) -- the matrix class of the
+paper's Section 2.1; the ``directed_*`` generators return a general
+(non-symmetric) A in the same layout, and ``bipartite_symmetrization`` turns
+one into the symmetric B of the paper's Section 4.  The C implementation lives in ``graphgen.c`` and is compiled on
 first use with the host C compiler.
 """
 from __future__ import annotations
@@ -171,3 +173,54 @@ def symmetric_weights(g: Graph, seed: int = 0, signed: bool = False, low: float 
     mag = rng.uniform(low, high, size=len(uniq))
     sgn = np.where(rng.random(len(uniq)) < 0.5, -1.0, 1.0) if signed else np.ones(len(uniq))
     return (mag * sgn)[inv].astype(np.float32)
+
+
+# ---------------------------------------------------------------- directed graphs
+def directed_from_edges(n: int, src, dst, name: str = "") -> Graph:
+    """Directed CSR (row i lists the heads j of the arcs i -> j, sorted, no
+    duplicates; loops kept): a general, non-symmetric A."""
+    src = np.asarray(src, dtype=np.int64)
+    dst = np.asarray(dst, dtype=np.int64)
+    key = np.unique(src * n + dst)
+    rows, cols = key // n, key % n
+    rp = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(rp, rows + 1, 1)
+    return Graph(n, np.cumsum(rp), cols.astype(np.int32), name or f"digraph_n{n}")
+
+
+def directed_erdos_renyi(n: int, mean_out_degree: float, seed: int, loops: bool = False) -> Graph:
+    """Directed G(n, p), p = mean_out_degree / n: arcs drawn independently."""
+    rng = np.random.default_rng(seed)
+    m = rng.binomial(n * n, min(1.0, mean_out_degree / n))
+    key = np.unique(rng.integers(0, n * n, size=m, dtype=np.int64))
+    src, dst = key // n, key % n
+    if not loops:
+        keep = src != dst
+        src, dst = src[keep], dst[keep]
+    return directed_from_edges(n, src, dst, f"dER_n{n}_k{mean_out_degree:g}_s{seed}")
+
+
+def directed_cycle(n: int) -> Graph:
+    """Directed cycle i -> i + 1 (mod n): the permutation matrix P with P^n = I."""
+    i = np.arange(n)
+    return directed_from_edges(n, i, (i + 1) % n, f"dC{n}")
+
+
+def bipartite_symmetrization(g: Graph, values=None):
+    """B = [0 A; A^T 0] of a directed graph (Section 4, Eq. digraph_sym): node
+    i keeps the out-arcs of i, node n + i its in-arcs.  Returns the symmetric
+    graph on 2n nodes and, if ``values`` is given, B's values in CSR order."""
+    n = g.n
+    rows = np.repeat(np.arange(n, dtype=np.int64), np.diff(g.row_ptr))
+    cols = g.col_idx.astype(np.int64)
+    src = np.concatenate([rows, n + cols])
+    dst = np.concatenate([n + cols, rows])
+    order = np.lexsort((dst, src))
+    src, dst = src[order], dst[order]
+    rp = np.zeros(2 * n + 1, dtype=np.int64)
+    np.add.at(rp, src + 1, 1)
+    b = Graph(2 * n, np.cumsum(rp), dst.astype(np.int32), f"B({g.name})")
+    if values is None:
+        return b
+    w = np.concatenate([np.asarray(values, np.float32)] * 2)[order]
+    return b, w
