@@ -71,6 +71,12 @@ typedef enum { MCF_F64 = 0, MCF_F32W_F64ACC = 1 } mcf_precision;
 
 /* mcf_create_graph flags */
 #define MCF_GRAPH_DEVICE_PTRS 1u   /* row_ptr/col_idx/values are device pointers (copied device to device) */
+#define MCF_GRAPH_NONSYMMETRIC 2u  /* A is a general (e.g. directed) matrix: the symmetry check is skipped and a
+                                      column-major copy is kept, since Definition 1 draws start columns from the
+                                      column norms ||C_i|| and Eq. rand_funm_formula_diag and Algorithm 2 read
+                                      columns of A.  The copy is built on the host at creation (a device-resident
+                                      CSR is read back for it).  mcf_spectral_radius is then unsupported: pass
+                                      the scale explicitly (mcf_gershgorin bounds the spectral radius). */
 
 typedef struct {
     const double* coeffs;   /* zeta_0..zeta_K of Eq. power_series (host memory), K = n_coeffs - 1;
@@ -120,7 +126,8 @@ mcf_status mcf_graph_info(mcf_graph_t g, int64_t* n, int64_t* nnz, int64_t* max_
  * on A + I in float64 on the device, until the Rayleigh quotient changes by
  * at most tol (relative) or max_iter iterations; used to set
  * scale = 1/lambda_max (the configurations of Section 4 scale A by gamma).
- * Cached on the graph.  Errors: MCF_ERR_INVALID_ARG, MCF_ERR_CUDA. */
+ * Cached on the graph.  Errors: MCF_ERR_INVALID_ARG, MCF_ERR_CUDA,
+ * MCF_ERR_UNSUPPORTED (graph created with MCF_GRAPH_NONSYMMETRIC). */
 mcf_status mcf_spectral_radius(mcf_graph_t g, double tol, int32_t max_iter, double* lambda_max);
 
 /* Gershgorin bound max_i sum_k |a_ik| on the spectral radius of A (Section 4.5). */
@@ -164,8 +171,10 @@ mcf_status mcf_subgraph_centrality(mcf_graph_t g, const mcf_params* params, cons
  * (Section 4.5) through RandFunmAction with zeta_k = 1 and scale = gamma;
  * params->coeffs and params->scale are ignored.  K = 0 picks the smallest K
  * with rho^(K+1) / (1 - rho) <= 1e-4, rho = gamma * lambda_max (computed
- * with mcf_spectral_radius if not cached); the series needs rho < 1.
- * Errors: MCF_ERR_INVALID_ARG (gamma <= 0, rho >= 1, K too large), as mcf_action. */
+ * with mcf_spectral_radius if not cached); the series needs rho < 1.  A graph
+ * created with MCF_GRAPH_NONSYMMETRIC needs an explicit K > 0.
+ * Errors: MCF_ERR_INVALID_ARG (gamma <= 0, rho >= 1, K too large),
+ * MCF_ERR_UNSUPPORTED (K = 0 on a non-symmetric graph), as mcf_action. */
 mcf_status mcf_katz(mcf_graph_t g, double gamma, int32_t K, const mcf_params* params, double* y, mcf_stats* stats);
 
 /* Largest n accepted by mcf_funm_full (its dense row of A'Q is staged in

@@ -48,6 +48,8 @@ struct BQuery {
     int64_t n_out;      // outputs: n, or the size of the SC subset
     const int64_t* rp;
     const int32_t* col;
+    const int64_t* cp;     // column-major copy of A (== rp/col for a symmetric A)
+    const int32_t* ri;
     const uint2* nod;
     const uint2* eod;
     const double* diag;
@@ -82,7 +84,7 @@ __global__ void bq_colnorm(const BQuery* __restrict__ desc, double* __restrict__
     const BQuery& d = desc[blockIdx.y];
     double s = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < d.n; i += (int64_t)gridDim.x * blockDim.x) {
-        const double c = __dmul_rn(d.gamma, sqrt((double)(d.rp[i + 1] - d.rp[i])));
+        const double c = __dmul_rn(d.gamma, sqrt((double)(d.cp[i + 1] - d.cp[i])));
         colnorm[d.node_off + i] = c;
         s += c;
     }
@@ -390,6 +392,8 @@ __global__ void __launch_bounds__(256, MINB) bwalk_tc_kernel(
 struct CtaQuery {
     const int64_t* rp;
     const int32_t* col;
+    const int64_t* cp;
+    const int32_t* ri;
     const uint8_t* want;
     const Rec<false>* rec;
     double* dacc;
@@ -431,7 +435,7 @@ __device__ void bdiag_start(const CtaQuery& cq, DiagTable& t, uint32_t k0, int64
         }
         if (!__syncthreads_or(stopped)) break;
         __threadfence_block();
-        diag_apply<DENSE>(t, k0, Nk, cq.rp, cq.col, nullptr, cq.want, cq.gamma, cq.dacc);
+        diag_apply<DENSE>(t, k0, Nk, cq.cp, cq.ri, nullptr, cq.want, cq.gamma, cq.dacc);
         __syncthreads();
         diag_clear<DENSE>(t, cq.n);
         __syncthreads();
@@ -439,7 +443,7 @@ __device__ void bdiag_start(const CtaQuery& cq, DiagTable& t, uint32_t k0, int64
         __syncthreads();
     }
     __threadfence_block();
-    diag_apply<DENSE>(t, k0, Nk, cq.rp, cq.col, nullptr, cq.want, cq.gamma, cq.dacc);
+    diag_apply<DENSE>(t, k0, Nk, cq.cp, cq.ri, nullptr, cq.want, cq.gamma, cq.dacc);
     __syncthreads();
     diag_clear<DENSE>(t, cq.n);
     __syncthreads();
@@ -475,6 +479,8 @@ __global__ void __launch_bounds__(256) bwalk_diag_kernel(
         if (threadIdx.x == 0) {
             cq.rp = d.rp;
             cq.col = d.col;
+            cq.cp = d.cp;
+            cq.ri = d.ri;
             cq.want = d.subset ? want_sc + (d.node_off - sc_node0) : nullptr;
             cq.rec = rec_sc + (d.node_off - sc_node0);
             cq.dacc = dacc + d.node_off;
@@ -847,6 +853,8 @@ mcf_status mcf_batch_create(const mcf_query* queries, int32_t n_queries, uint32_
             x.n = g->n;
             x.rp = g->row_ptr;
             x.col = g->col_idx;
+            x.cp = g->col_ptr;
+            x.ri = g->row_idx;
             x.nod = g->node_od;
             x.eod = g->edge_od;
             x.diag = g->diag;

@@ -347,7 +347,9 @@ __device__ int diag_walk(const DiagTable& t, uint32_t k0, int64_t g, int from, i
     return -1;
 }
 
-// d_i += a'_ik <Q_k, C'_i> / N_k for the neighbours i of k (warp per neighbour).
+// d_i += a'_ik <Q_k, C'_i> / N_k for the rows i of column k (warp per row),
+// read from the column-major copy of A (rp/col/val: column pointers, row
+// indices and values; for a symmetric A the row arrays themselves).
 template <bool DENSE>
 __device__ __forceinline__ void diag_apply(const DiagTable& t, uint32_t k0, int64_t Nk, const int64_t* __restrict__ rp,
                                            const int32_t* __restrict__ col, const float* __restrict__ val,

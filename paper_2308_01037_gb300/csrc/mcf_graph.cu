@@ -349,6 +349,80 @@ extern "C" {
 const char* mcf_last_error(void) { return get_error(); }
 const char* mcf_version(void) { return "mcf 0.1 (sm_103a)"; }
 
+// sum_j a_ji^2 of every column i, over the column-major copy in increasing
+// row order, each product and sum rounded on its own.
+__global__ void column_sq(int64_t n, const int64_t* __restrict__ cp, const float* __restrict__ cv,
+                          double* __restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double sq = 0.0;
+        for (int64_t q = cp[i]; q < cp[i + 1]; ++q) {
+            const double a = (double)cv[q];
+            sq = __dadd_rn(sq, __dmul_rn(a, a));
+        }
+        out[i] = sq;
+    }
+}
+
+namespace {
+
+// The column-major copy of a general A: a counting sort over the rows, done
+// on the host (it visits the rows in order, so every column lists its rows
+// in increasing order, deterministically), then copied to the device.
+mcf_status build_columns(mcf_graph* g, const int64_t* row_ptr, const int32_t* col_idx, const float* values,
+                         bool dev_in) {
+    const int64_t n = g->n, nnz = g->nnz;
+    std::vector<int64_t> h_rp;
+    std::vector<int32_t> h_ci;
+    std::vector<float> h_va;
+    const int64_t* rp = row_ptr;
+    const int32_t* ci = col_idx;
+    const float* va = values;
+    if (dev_in) {
+        h_rp.resize((size_t)n + 1);
+        h_ci.resize((size_t)std::max<int64_t>(nnz, 1));
+        MCF_CUDA_TRY(cudaMemcpy(h_rp.data(), g->row_ptr, (size_t)(n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
+        if (nnz > 0)
+            MCF_CUDA_TRY(cudaMemcpy(h_ci.data(), g->col_idx, (size_t)nnz * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        rp = h_rp.data();
+        ci = h_ci.data();
+        if (values) {
+            h_va.resize((size_t)std::max<int64_t>(nnz, 1));
+            if (nnz > 0)
+                MCF_CUDA_TRY(cudaMemcpy(h_va.data(), g->values, (size_t)nnz * sizeof(float), cudaMemcpyDeviceToHost));
+            va = h_va.data();
+        }
+    }
+    std::vector<int64_t> cp((size_t)n + 1, 0);
+    for (int64_t p = 0; p < nnz; ++p) ++cp[(size_t)ci[p] + 1];
+    for (int64_t i = 0; i < n; ++i) cp[(size_t)i + 1] += cp[(size_t)i];
+    std::vector<int64_t> cur(cp.begin(), cp.end() - 1);
+    std::vector<int32_t> ri((size_t)std::max<int64_t>(nnz, 1));
+    std::vector<float> cv(values ? (size_t)std::max<int64_t>(nnz, 1) : 0);
+    for (int64_t r = 0; r < n; ++r)
+        for (int64_t p = rp[r]; p < rp[r + 1]; ++p) {
+            const int64_t q = cur[(size_t)ci[p]]++;
+            ri[(size_t)q] = (int32_t)r;
+            if (values) cv[(size_t)q] = va[p];
+        }
+    if (cudaMalloc(&g->col_ptr, (size_t)(n + 1) * sizeof(int64_t)) != cudaSuccess ||
+        cudaMalloc(&g->row_idx, ri.size() * sizeof(int32_t)) != cudaSuccess ||
+        (values && cudaMalloc(&g->col_values, cv.size() * sizeof(float)) != cudaSuccess) ||
+        (values && cudaMalloc(&g->col_sq, (size_t)std::max<int64_t>(n, 1) * sizeof(double)) != cudaSuccess)) {
+        cudaGetLastError();
+        return fail(MCF_ERR_OOM, "device allocation of the column-major copy failed");
+    }
+    MCF_CUDA_TRY(cudaMemcpy(g->col_ptr, cp.data(), (size_t)(n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+    MCF_CUDA_TRY(cudaMemcpy(g->row_idx, ri.data(), ri.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    if (values) {
+        MCF_CUDA_TRY(cudaMemcpy(g->col_values, cv.data(), cv.size() * sizeof(float), cudaMemcpyHostToDevice));
+        if (n > 0) column_sq<<<grid_for(n, 256), 256>>>(n, g->col_ptr, g->col_values, g->col_sq);
+        MCF_CUDA_TRY(cudaGetLastError());
+    }
+    return MCF_OK;
+}
+
+}  // namespace
+
 mcf_status mcf_create_graph(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const float* values,
                             uint32_t flags, mcf_graph_t* out) {
     set_error("");
@@ -411,7 +485,8 @@ mcf_status mcf_create_graph(int64_t n, const int64_t* row_ptr, const int32_t* co
     cudaError_t e = cudaMemcpy(&hf, dflags, sizeof(Flags), cudaMemcpyDeviceToHost);
     cudaFree(dflags);
     if (e != cudaSuccess) return cleanup(fail(MCF_ERR_CUDA, std::string("validation: ") + cudaGetErrorString(e)));
-    if (!(hf.bad & (BAD_ROWPTR | BAD_COLUMN)) && hf.sums[0] != hf.sums[1]) hf.bad |= BAD_SYMMETRY;
+    const bool general = (flags & MCF_GRAPH_NONSYMMETRIC) != 0;
+    if (!general && !(hf.bad & (BAD_ROWPTR | BAD_COLUMN)) && hf.sums[0] != hf.sums[1]) hf.bad |= BAD_SYMMETRY;
     if (hf.bad) {
         std::string why;
         if (hf.bad & BAD_ROWPTR) why += " row_ptr not non-decreasing within [0, nnz];";
@@ -450,6 +525,16 @@ mcf_status mcf_create_graph(int64_t n, const int64_t* row_ptr, const int32_t* co
         memcpy(&gm, &hm, sizeof(gm));
         g->gershgorin = gm;
     }
+    if (general) {
+        g->symmetric = false;
+        mcf_status rc = build_columns(g, row_ptr, col_idx, values, dev_in);
+        if (rc != MCF_OK) return cleanup(rc);
+    } else {
+        g->col_ptr = g->row_ptr;
+        g->row_idx = g->col_idx;
+        g->col_values = g->values;
+        g->col_sq = g->row_sq;
+    }
     e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cleanup(fail(MCF_ERR_CUDA, std::string("create_graph: ") + cudaGetErrorString(e)));
     *out = g;
@@ -468,6 +553,12 @@ mcf_status mcf_destroy_graph(mcf_graph_t g) {
     cudaFree(g->went);
     cudaFree(g->node_od);
     cudaFree(g->edge_od);
+    if (!g->symmetric) {
+        cudaFree(g->col_ptr);
+        cudaFree(g->row_idx);
+        cudaFree(g->col_values);
+        cudaFree(g->col_sq);
+    }
     delete g;
     return MCF_OK;
 }
@@ -490,6 +581,8 @@ mcf_status mcf_gershgorin(mcf_graph_t g, double* bound) {
 mcf_status mcf_spectral_radius(mcf_graph_t g, double tol, int32_t max_iter, double* lambda_max) {
     set_error("");
     if (!g || !lambda_max) return fail(MCF_ERR_INVALID_ARG, "NULL argument");
+    if (!g->symmetric)
+        return fail(MCF_ERR_UNSUPPORTED, "the power iteration needs a symmetric A; pass the scale explicitly");
     static std::mutex mu;   // one power iteration at a time (it caches its result on the graph)
     std::lock_guard<std::mutex> lk(mu);
     if (!(tol > 0.0) || max_iter < 1) return fail(MCF_ERR_INVALID_ARG, "tol must be > 0 and max_iter >= 1");

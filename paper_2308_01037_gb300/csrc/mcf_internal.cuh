@@ -70,6 +70,15 @@ struct mcf_graph {
     // column index and then a node record.
     uint2* node_od = nullptr;     // n
     uint2* edge_od = nullptr;     // nnz
+    // Column-major copy of A (column i: rows row_idx[col_ptr[i] .. col_ptr[i+1])
+    // in increasing order, values col_values) and sum_j a_ji^2 per column.
+    // For a symmetric A these alias the row arrays; a general A (created with
+    // MCF_GRAPH_NONSYMMETRIC) owns them.
+    bool symmetric = true;
+    int64_t* col_ptr = nullptr;   // n + 1
+    int32_t* row_idx = nullptr;   // nnz
+    float* col_values = nullptr;  // nnz (weighted only)
+    double* col_sq = nullptr;     // n (weighted only)
     double lambda_max = 0.0;      // cached by mcf_spectral_radius (0 = unknown)
     double gershgorin = 0.0;
     int device = 0;

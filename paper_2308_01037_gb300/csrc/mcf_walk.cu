@@ -40,13 +40,14 @@ __global__ void r_kernel(int64_t n, const int64_t* __restrict__ rp, const int32_
     r[i] = __dmul_rn(gamma, s);
 }
 
-// colnorm_i = ||C'_i||_2 (Eq. initial_prob; symmetric A: column = row) and
+// colnorm_i = ||C'_i||_2 (Eq. initial_prob) from the column-major copy (cp:
+// column pointers, col_sq: sum_j a_ji^2, null for a binary A) and
 // fixed-partition partial sums of it.
-__global__ void colnorm_kernel(int64_t n, const int64_t* __restrict__ rp, const double* __restrict__ row_sq,
+__global__ void colnorm_kernel(int64_t n, const int64_t* __restrict__ cp, const double* __restrict__ col_sq,
                                double gamma, double* __restrict__ colnorm, double* __restrict__ part) {
     double s = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const double sq = row_sq ? row_sq[i] : (double)(rp[i + 1] - rp[i]);
+        const double sq = col_sq ? col_sq[i] : (double)(cp[i + 1] - cp[i]);
         const double c = __dmul_rn(gamma, sqrt(sq));
         colnorm[i] = c;
         s += c;
@@ -674,8 +675,9 @@ __global__ void action_epilogue_nodes(int64_t m, const int64_t* __restrict__ nod
 // linearly).
 template <bool F64, bool WEIGHTED, bool DENSE>
 __global__ void __launch_bounds__(256) walk_diag_kernel(
-    const Rec<F64>* __restrict__ rec, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-    const float* __restrict__ val, const WEntry* __restrict__ went, const int32_t* __restrict__ starts,
+    const Rec<F64>* __restrict__ rec, const int64_t* __restrict__ cp, const int32_t* __restrict__ ri,
+    const float* __restrict__ cv, const int32_t* __restrict__ col, const WEntry* __restrict__ went,
+    const int32_t* __restrict__ starts,
     const int64_t* __restrict__ woff, const int64_t* __restrict__ nw, const uint8_t* __restrict__ want, double gamma,
     const double* __restrict__ zeta_g, int K, double wc, float wc32, uint2 key, uint32_t req, int64_t n, int cap_log2,
     double* __restrict__ qval, double* __restrict__ dacc, unsigned long long* __restrict__ counters) {
@@ -742,7 +744,7 @@ __global__ void __launch_bounds__(256) walk_diag_kernel(
             if (!__syncthreads_or(stopped)) break;
             // the table filled up: apply the partial row, clear it, resume
             __threadfence_block();
-            diag_apply<DENSE>(t, k0, Nk, rp, col, val, want, gamma, dacc);
+            diag_apply<DENSE>(t, k0, Nk, cp, ri, cv, want, gamma, dacc);
             __syncthreads();
             diag_clear<DENSE>(t, n);
             __syncthreads();
@@ -750,7 +752,7 @@ __global__ void __launch_bounds__(256) walk_diag_kernel(
             __syncthreads();
         }
         __threadfence_block();
-        diag_apply<DENSE>(t, k0, Nk, rp, col, val, want, gamma, dacc);
+        diag_apply<DENSE>(t, k0, Nk, cp, ri, cv, want, gamma, dacc);
         __syncthreads();
         diag_clear<DENSE>(t, n);
         __syncthreads();
@@ -864,7 +866,7 @@ static mcf_status prepare(const mcf_graph* g, const mcf_params* p, double gamma,
     MCF_CUDA_TRY(cudaMemcpyAsync(P.zeta, p->coeffs, p->n_coeffs * sizeof(double), cudaMemcpyHostToDevice, st));
     if (n == 0) return MCF_OK;
     r_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, g->row_ptr, g->col_idx, g->values, v_dev, gamma, P.r);
-    colnorm_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, g->row_ptr, g->row_sq, gamma, P.colnorm, P.part);
+    colnorm_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, g->col_ptr, g->col_sq, gamma, P.colnorm, P.part);
     sum_partials<<<1, RED_THREADS, 0, st>>>(P.part, RED_BLOCKS, P.part + RED_BLOCKS);
     alloc_kernel<<<grid_for(n, 256), 256, 0, st>>>(n, P.colnorm, P.part + RED_BLOCKS, p->n_walks, p->walks_per_node,
                                                    need, P.nw, P.flag);
@@ -1121,9 +1123,9 @@ static mcf_status launch_diag(const mcf_graph* g, const Prep& P, const uint8_t* 
     double* qval;
     MCF_TRY(sc.get(&qval, (size_t)grid * (size_t)std::max<int64_t>(cap, 1)));
     ScopedL2Fetch fetch(walk_tuning().l2_fetch);
-    kern<<<grid, threads, smem, st>>>((const Rec<F64>*)P.rec, g->row_ptr, g->col_idx, g->values, g->went, P.starts,
-                                      P.woff, P.nw, want, gamma, P.zeta, K, wc, cutoff_f32(wc), key, req, g->n,
-                                      cap_log2, qval, dacc, P.counters);
+    kern<<<grid, threads, smem, st>>>((const Rec<F64>*)P.rec, g->col_ptr, g->row_idx, g->col_values, g->col_idx,
+                                      g->went, P.starts, P.woff, P.nw, want, gamma, P.zeta, K, wc, cutoff_f32(wc), key,
+                                      req, g->n, cap_log2, qval, dacc, P.counters);
     MCF_CUDA_TRY(cudaGetLastError());
     return MCF_OK;
 }
@@ -1293,10 +1295,9 @@ __global__ void full_edge_coeffs(int64_t nnz, const int32_t* __restrict__ col, c
 
 // F = zeta_0 I + zeta_1 A' + A' Q A' (Algorithm 2, last step) one row i at a
 // time: row i of A'Q is formed in shared memory from the rows of N Q of i's
-// neighbours (each scaled by ce), then
-// F_ij = zeta_0 [i == j] + sum_{m in N(j)} a'_jm (A'Q)_im (a'_jm = a'_mj for a
-// symmetric A, so row j of A' serves as column j), and finally
-// zeta_1 a'_ij is added for the entries of row i.  Both products cost one
+// neighbours (each scaled by ce), then F_ij = zeta_0 [i == j] +
+// sum_m (A'Q)_im a'_mj over column j of A' (the column-major copy), and
+// finally zeta_1 a'_ij is added for the entries of row i.  Both products cost one
 // float64 FMA per (i, j, entry): the kernel is bound by the float64 pipe, so
 // no float64 division is left in its loops.  Each thread accumulates four
 // columns j at once so that four row loads are in flight.
@@ -1342,6 +1343,7 @@ __device__ __forceinline__ double full_row_sums(int64_t base, int64_t n, const i
 template <bool WEIGHTED>
 __global__ void __launch_bounds__(FULL_THREADS) full_epilogue(
     int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const float* __restrict__ val,
+    const int64_t* __restrict__ cp, const int32_t* __restrict__ ri, const float* __restrict__ cv,
     const double* __restrict__ Q, const double* __restrict__ ce, double gamma, double z0, double z1, int K,
     double* __restrict__ F) {
     extern __shared__ double aq[];
@@ -1370,7 +1372,7 @@ __global__ void __launch_bounds__(FULL_THREADS) full_epilogue(
         __syncthreads();
         double* Fi = F + i * n;
         for (int64_t base = (int64_t)wid * 32; base < n; base += (int64_t)nwarp * 32) {
-            const double s = full_row_sums<WEIGHTED>(base, n, rp, col, val, aq);
+            const double s = full_row_sums<WEIGHTED>(base, n, cp, ri, cv, aq);   // column j of A
             const int64_t j = base + lane;
             if (j < n) Fi[j] = (j == i ? z0 : 0.0) + gamma * s;
         }
@@ -1445,7 +1447,8 @@ static mcf_status solve_full(mcf_graph* g, const mcf_params* p, double* F, mcf_s
         auto kern = g->weighted ? full_epilogue<true> : full_epilogue<false>;
         MCF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         const int grid = (int)std::min<int64_t>(n, persistent_grid(kern, threads, smem));
-        kern<<<grid, threads, smem, st>>>(n, g->row_ptr, g->col_idx, g->values, Q, ce, gamma, z0, z1, K, F_dev);
+        kern<<<grid, threads, smem, st>>>(n, g->row_ptr, g->col_idx, g->values, g->col_ptr, g->row_idx,
+                                          g->col_values, Q, ce, gamma, z0, z1, K, F_dev);
         MCF_CUDA_TRY(cudaGetLastError());
     }
     if (!f_on_dev && n > 0)

@@ -21,6 +21,7 @@ MCF_OK = 0
 MCF_F64 = 0
 MCF_F32W_F64ACC = 1
 MCF_GRAPH_DEVICE_PTRS = 1
+MCF_GRAPH_NONSYMMETRIC = 2
 MCF_MAX_COEFFS = 256
 
 STATUS_NAMES = {
@@ -199,15 +200,17 @@ class GraphHandle:
 
 
 # ---------------------------------------------------------------- entry points
-def mcf_create_graph(n, row_ptr, col_idx, values=None) -> GraphHandle:
-    """Uploads a symmetric CSR matrix (numpy or torch; device tensors copied device to device)."""
+def mcf_create_graph(n, row_ptr, col_idx, values=None, symmetric=True) -> GraphHandle:
+    """Uploads a CSR matrix (numpy or torch; device tensors copied device to device);
+    ``symmetric=False`` accepts a general A (MCF_GRAPH_NONSYMMETRIC)."""
     lib = load()
     rp, krp = _ptr(row_ptr, np.int64)
     ci, kci = _ptr(col_idx if len(col_idx) else np.zeros(1, np.int32), np.int32)
     va, kva = _ptr(values, np.float32)
     dev = 1 if (_is_torch(row_ptr) and row_ptr.is_cuda) else 0
+    flags = (MCF_GRAPH_DEVICE_PTRS if dev else 0) | (0 if symmetric else MCF_GRAPH_NONSYMMETRIC)
     h = ctypes.c_void_p()
-    _check(lib.mcf_create_graph(int(n), rp, ci, va, MCF_GRAPH_DEVICE_PTRS if dev else 0, ctypes.byref(h)))
+    _check(lib.mcf_create_graph(int(n), rp, ci, va, flags, ctypes.byref(h)))
     nnz = int(krp[-1])
     return GraphHandle(h.value, int(n), nnz)
 

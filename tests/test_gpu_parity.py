@@ -277,3 +277,14 @@ def test_repeat_calls_identical_and_request_ids_differ(ba1000):
     assert_parity(a, b, rtol=1e-13, atol=0)
     other = M.mcf_total_communicability(h, c, request_id=2, **kw)
     assert np.abs(other - a).max() > 1e-9
+
+
+def test_mittag_leffler_coefficients(ba1000):
+    """Other functions come through the coefficient list: E_{0.8,1.2}(A') v."""
+    g, h, gam = ba1000
+    c = R.mittag_leffler_coeffs(30, 0.8, 1.2)
+    v = np.random.default_rng(5).uniform(0.5, 1.5, g.n)
+    y = M.mcf_action(h, v, c, scale=gam, walks_per_node=64, seed=9, precision=M.MCF_F32W_F64ACC)
+    assert_parity(y, E.action(g, c, v=v, gamma=gam, walks_per_node=64, seed=9, precision=1)["y"])
+    ref = R.series_action(g, c, gam, v=v)
+    assert np.abs(y - ref).max() / np.abs(ref).max() < 0.02
