@@ -385,6 +385,34 @@ def run_serving(M, R, I, scales, n_requests, rate=200.0, seed=5):
             "walk_budgets": "TC 16 n walks, Katz (gamma 0.85/Gershgorin) 16 per node, SC 32 per node on 1e4 sampled nodes"}
 
 
+def run_subset(M, h, g, c, base, full_out, reps=5):
+    """Single-entry and subset total communicability on the resident graph
+    (Section 4.3, Table 3): only the columns adjacent to the requested nodes
+    are walked, with the full run's walk ids, so each entry equals the full
+    solve's entry; time per call and walks taken against the full solve."""
+    import torch
+
+    full_y, full_st = M.mcf_total_communicability(h, c, out=full_out, request_id=77, stats=True, **base)
+    full_y = full_y.cpu().numpy()
+    res = {}
+    rng = np.random.default_rng(11)
+    for name, nodes in (("max_degree_node", np.array([int(np.argmax(g.degree))], np.int64)),
+                        ("1000_random_nodes", rng.choice(g.n, size=1000, replace=False).astype(np.int64))):
+        nd = torch.from_numpy(nodes).cuda()
+        M.mcf_action_nodes(h, nd, c, request_id=77, **base)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            y, st = M.mcf_action_nodes(h, nd, c, request_id=77, stats=True, **base)
+        torch.cuda.synchronize()
+        ms = 1e3 * (time.perf_counter() - t0) / reps
+        y = y.cpu().numpy()
+        res[name] = {"ms_per_call": ms, "walks": st["walks"], "walk_steps": st["walk_steps"],
+                     "max_rel_diff_vs_full_solve": float(np.max(np.abs(y - full_y[nodes]) / np.abs(full_y[nodes])))}
+    res["full_solve_walks"] = full_st["walks"]
+    return res
+
+
 def run_funm_full(M, R, I, n=16384, m=8, wpn=100, reps=3):
     """Dense RandFunm (Algorithm 2) at the largest supported n: time of one
     solve (walks + the A'QA' epilogue), and the error of F 1 and of diag F on
@@ -503,8 +531,8 @@ def main():
     ap.add_argument("--batch-log-n-max", type=float, default=5.0)
     ap.add_argument("--serve-scales", default="14-20")
     ap.add_argument("--serve-requests", type=int, default=600)
-    ap.add_argument("--section", default="main", choices=["main", "funm_full", "mc_classic"],
-                    help="funm_full / mc_classic: run only that measurement (1 GPU) and print its JSON")
+    ap.add_argument("--section", default="main", choices=["main", "funm_full", "mc_classic", "batched", "serving"],
+                    help="run only that measurement (1 GPU) and print its JSON")
     ap.add_argument("--funm-n", type=int, default=16384, help="nodes of the dense RandFunm measurement")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
@@ -516,7 +544,15 @@ def main():
         from paper_2308_01037_gb300 import mcf as M
 
         M.load()
-        res = run_funm_full(M, R, I, n=args.funm_n) if args.section == "funm_full" else run_mc_classic(M, R, I)
+        if args.section == "funm_full":
+            res = run_funm_full(M, R, I, n=args.funm_n)
+        elif args.section == "mc_classic":
+            res = run_mc_classic(M, R, I)
+        elif args.section == "batched":
+            res = run_batched(M, R, I, args.batch_graphs, args.batch_log_n_max)
+        else:
+            lo, hi = (int(x) for x in args.serve_scales.split("-"))
+            res = run_serving(M, R, I, list(range(lo, hi + 1)), args.serve_requests)
         print(json.dumps({"section": args.section, **res}), flush=True)
         return
 
@@ -574,6 +610,7 @@ def main():
         tmax, steps_all = aggregate(ms, steps_total, device="cuda")
     value = steps_all / (tmax / 1000.0)
     solves_per_s = world * args.steps / (tmax / 1000.0)
+    log(f"[bench] timed: {tmax / args.steps:.2f} ms per step, {value:.3e} walk-steps/s")
     kernel_ms = float(np.mean(kern_ms))
     peak, peak_kind = measured_peak()
     steps_per_launch = steps_total / args.steps
@@ -593,7 +630,10 @@ def main():
             ref = R.series_action(g, c, gam)
             rel_err = float(np.abs(y - ref).max() / np.abs(ref).max())
         else:
-            nodes = np.random.default_rng(0).choice(g.n, size=min(g.n, 2000), replace=False)
+            # float64 series on the host costs K sparse products per sampled node:
+            # keep it near 1e10 multiply-adds (at least 16 nodes, at most 2000)
+            m = int(min(g.n, 2000, max(16, 1e10 // (w["K"] * max(g.nnz, 1)))))
+            nodes = np.random.default_rng(0).choice(g.n, size=m, replace=False)
             ref = R.series_diag(g, c, nodes, gam)
             rel_err = float(np.abs(y[nodes] - ref).max() / np.abs(ref).max())
         log(f"[bench] rel l_inf error vs float64 series: {rel_err:.3e} ({time.time() - t:.1f}s)")
@@ -623,6 +663,9 @@ def main():
             dist.all_reduce(t)
             e2e["value"] = float(t.item())
 
+    subset = None
+    if rank == 0 and world == 1 and w["query"] == "tc" and not args.no_batch:
+        subset = run_subset(M, h, g, c, base, out)
     batched = serving = funm_full = mc_classic = None
     if rank == 0 and world == 1 and not args.no_batch:
         from oracle import reference as R
@@ -656,7 +699,8 @@ def main():
                          "the R-MAT scale 21 case (one 32-B sector per random step) x the walk steps of a launch"},
             "clocks": clk.summary(), "e2e": e2e, "gpu_launches": args.steps * LAUNCHES_PER_SOLVE[w["query"]],
             "cpu_baseline": cpu,
-            "batched": batched, "serving": serving, "funm_full": funm_full, "mc_classic": mc_classic,
+            "subset": subset, "batched": batched, "serving": serving, "funm_full": funm_full,
+            "mc_classic": mc_classic,
         }
         print(json.dumps(line), flush=True)
     h.close()

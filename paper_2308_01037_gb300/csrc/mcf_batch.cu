@@ -56,6 +56,7 @@ struct BQuery {
     const int64_t* nodes;  // SC subset (device) or null
     double* out;           // device output
     const double* zeta;    // K + 1 coefficients (device)
+    const float* zf;       // the same, rounded to float32 (the walk kernels' precision)
     double gamma, z0, z1, wc;
     int64_t n_walks, wpn;
     uint2 key;
@@ -229,7 +230,7 @@ struct WarpQuery {
     uint32_t req;
     float wc32;
     int32_t K;
-    float zeta[MCF_MAX_COEFFS];
+    const float* zeta;   // float32 coefficients in global memory (L1-resident)
 };
 
 template <int MINB>
@@ -294,8 +295,8 @@ __global__ void __launch_bounds__(256, MINB) bwalk_tc_kernel(
                         Wq.req = d.req;
                         Wq.wc32 = d.wc32;
                         Wq.K = d.K;
+                        Wq.zeta = d.zf;
                     }
-                    for (int t = lane; t <= d.K; t += 32) Wq.zeta[t] = (float)d.zeta[t];
                     __syncwarp();
                     cur_q = qn;
                 }
@@ -338,23 +339,21 @@ __global__ void __launch_bounds__(256, MINB) bwalk_tc_kernel(
         }
         bool done = false;
         if (active) {
-            // The next state's record depends only on this state's record and
-            // the random word, not on W: issue its read first, so the degree
-            // table lookup and the cutoff test overlap the random read.
+            // The next state's record is read only once the walk is known to
+            // go on (after the cutoff test): a read issued earlier is wasted
+            // DRAM work at every walk's end, and the kernel is bound by the
+            // rate of random DRAM reads.
             const bool last = k + 2 >= Wq.K || deg == 0;
-            uint2 nx = make_uint2(0u, 0u);
-            if (!last) {
-                uint32_t w0, w1;
-                walk_words<false>(u, k, (uint32_t)g, (uint32_t)((uint64_t)g >> 32), Wq.req, Wq.key, w0, w1);
-                nx = load_od(Wq.eod + (int64_t)off + __umulhi(w0, deg), policy_evict_first());
-            }
             done = !(fabsf(W) > Wq.wc32);
             if (!done) {
                 const float t = __ldg(Wq.rm + deg);
-                a32.add(__fmul_rn(__fmul_rn(Wq.zeta[k + 2], W), t));
+                a32.add(__fmul_rn(__fmul_rn(__ldg(Wq.zeta + k + 2), W), t));
                 if (last) {
                     done = true;
                 } else {
+                    uint32_t w0, w1;
+                    walk_words<false>(u, k, (uint32_t)g, (uint32_t)((uint64_t)g >> 32), Wq.req, Wq.key, w0, w1);
+                    const uint2 nx = load_od(Wq.eod + (int64_t)off + __umulhi(w0, deg), policy_evict_first());
                     W = __fmul_rn(W, t);
                     off = nx.x;
                     deg = nx.y;
@@ -581,7 +580,7 @@ struct mcf_batch {
     int cap_log2 = 10;
     int64_t region = 0;
     int diag_grid = 0, diag_threads = 256;
-    int tc_grid[3] = {0, 0, 0};   // persistent grids of the walk kernel for 5, 6 and 8 blocks per SM
+    int tc_grid[4] = {0, 0, 0, 0};   // persistent grids of the walk kernel for 5, 6, 8 and 4 blocks per SM
     size_t diag_smem = 0;
     BatchTuning tune;
     std::vector<void*> bufs;
@@ -589,6 +588,8 @@ struct mcf_batch {
     BQuery* desc = nullptr;
     int64_t *qoff = nullptr, *rmoff = nullptr, *boff = nullptr, *wbase = nullptr;
     double *colnorm = nullptr, *part = nullptr, *tot = nullptr, *acc = nullptr, *zeta = nullptr, *qval = nullptr;
+    float* zf = nullptr;
+    std::vector<float> zf_host;
     int64_t *nw = nullptr, *flag = nullptr, *gw = nullptr, *spos = nullptr, *soff = nullptr;
     uint32_t *starts = nullptr, *chunk_s0 = nullptr;
     float* rm = nullptr;
@@ -668,6 +669,7 @@ static mcf_status record(mcf_batch* b, cudaStream_t st) {
         };
         if (b->tune.minb == 8) launch(bwalk_tc_kernel<8>, b->tc_grid[2]);
         else if (b->tune.minb == 6) launch(bwalk_tc_kernel<6>, b->tc_grid[1]);
+        else if (b->tune.minb == 4) launch(bwalk_tc_kernel<4>, b->tc_grid[3]);
         else launch(bwalk_tc_kernel<5>, b->tc_grid[0]);
         MCF_CUDA_TRY(cudaGetLastError());
         bq_finalize<<<grid_for(b->NT_tc, 256), 256, 0, st>>>(b->NT_tc, b->acc, b->nw);
@@ -731,7 +733,7 @@ static mcf_status autotune(mcf_batch* b, cudaStream_t st) {
             return MCF_OK;
         }
     }
-    const BatchTuning cands[] = {{5, 1}, {5, 4}, {6, 4}, {8, 4}};
+    const BatchTuning cands[] = {{4, 1}, {4, 4}, {5, 1}, {5, 4}, {6, 4}, {8, 4}};
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -907,7 +909,7 @@ mcf_status mcf_batch_create(const mcf_query* queries, int32_t n_queries, uint32_
             b->cap_log2 = 10;
             if (any_hash) {
                 const int64_t want_slots = std::max<int64_t>(16 * nk_hint, 1024);
-                while (b->cap_log2 < 14 && ((int64_t)1 << b->cap_log2) < want_slots) ++b->cap_log2;
+                while (b->cap_log2 < 12 && ((int64_t)1 << b->cap_log2) < want_slots) ++b->cap_log2;
             }
             b->region = std::max<int64_t>(dense_max, (int64_t)1 << b->cap_log2);
             b->diag_smem = ((size_t)1 << b->cap_log2) * 2 * sizeof(int32_t);
@@ -920,6 +922,7 @@ mcf_status mcf_batch_create(const mcf_query* queries, int32_t n_queries, uint32_
         b->tc_grid[0] = persistent_grid(bwalk_tc_kernel<5>, 256, 0);
         b->tc_grid[1] = persistent_grid(bwalk_tc_kernel<6>, 256, 0);
         b->tc_grid[2] = persistent_grid(bwalk_tc_kernel<8>, 256, 0);
+        b->tc_grid[3] = persistent_grid(bwalk_tc_kernel<4>, 256, 0);
         // ---- device buffers
         mcf_status rc = MCF_OK;
         auto A = [&](auto** p, size_t count) {
@@ -944,6 +947,7 @@ mcf_status mcf_batch_create(const mcf_query* queries, int32_t n_queries, uint32_
         A(&b->chunk_s0, b->max_chunks);
         A(&b->rm, b->rm_total);
         A(&b->zeta, (size_t)b->Q * MCF_MAX_COEFFS);
+        A(&b->zf, (size_t)b->Q * MCF_MAX_COEFFS);
         A(&b->rec_sc, b->sc_nodes);
         A(&b->need, b->sc_nodes);
         A(&b->want, b->sc_nodes);
@@ -956,8 +960,16 @@ mcf_status mcf_batch_create(const mcf_query* queries, int32_t n_queries, uint32_
             const int i = b->fused[f];
             const mcf_query& q = b->queries[i];
             d[f].zeta = b->zeta + (size_t)f * MCF_MAX_COEFFS;
+            d[f].zf = b->zf + (size_t)f * MCF_MAX_COEFFS;
             if (cudaMemcpyAsync((void*)d[f].zeta, b->coeffs[i].data(), b->coeffs[i].size() * sizeof(double),
                                 cudaMemcpyHostToDevice, st) != cudaSuccess)
+                return bail(fail(MCF_ERR_CUDA, "coefficient upload failed"));
+            if (f == 0) b->zf_host.assign((size_t)b->Q * MCF_MAX_COEFFS, 0.f);
+            for (size_t k = 0; k < b->coeffs[i].size(); ++k)
+                b->zf_host[(size_t)f * MCF_MAX_COEFFS + k] = (float)b->coeffs[i][k];
+            if (f == b->Q - 1 &&
+                cudaMemcpyAsync(b->zf, b->zf_host.data(), b->zf_host.size() * sizeof(float), cudaMemcpyHostToDevice,
+                                st) != cudaSuccess)
                 return bail(fail(MCF_ERR_CUDA, "coefficient upload failed"));
             if (d[f].subset && d[f].n_out > 0) {
                 for (int64_t t = 0; t < q.n_nodes && !is_device_ptr(q.nodes); ++t)

@@ -171,7 +171,7 @@ __global__ void validate_rows(int64_t n, int64_t nnz, const int64_t* __restrict_
     const int lane = threadIdx.x & 31;
     int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    unsigned long long s_lo = 0, s_hi = 0;
+    unsigned long long s_lo = 0, s_hi = 0, dmax = 0, nloops = 0;
     uint32_t flags = 0;
     for (int64_t i = warp; i < n; i += nwarps) {
         int64_t b = rp[i], e = rp[i + 1];
@@ -179,7 +179,7 @@ __global__ void validate_rows(int64_t n, int64_t nnz, const int64_t* __restrict_
             flags |= BAD_ROWPTR;
             continue;
         }
-        if (lane == 0) atomicMax(maxdeg, (unsigned long long)(e - b));
+        dmax = max(dmax, (unsigned long long)(e - b));
         for (int64_t p = b + lane; p < e; p += 32) {
             int32_t j = col[p];
             if (j < 0 || j >= n) { flags |= BAD_COLUMN; continue; }
@@ -187,7 +187,7 @@ __global__ void validate_rows(int64_t n, int64_t nnz, const int64_t* __restrict_
             float a = val ? val[p] : 1.0f;
             if (!isfinite(a)) flags |= BAD_VALUE;
             if (j == i) {
-                atomicAdd(loops, 1ull);
+                ++nloops;
                 diag[i] = (double)a;
                 continue;
             }
@@ -200,11 +200,15 @@ __global__ void validate_rows(int64_t n, int64_t nnz, const int64_t* __restrict_
     for (int d = 16; d > 0; d >>= 1) {
         s_lo += __shfl_down_sync(0xffffffffu, s_lo, d);
         s_hi += __shfl_down_sync(0xffffffffu, s_hi, d);
+        nloops += __shfl_down_sync(0xffffffffu, nloops, d);
         flags |= __shfl_down_sync(0xffffffffu, flags, d);
     }
+    // one atomic per warp for each total (per-row atomics on one address serialise)
     if (lane == 0) {
         if (s_lo) atomicAdd(&sums[0], s_lo);
         if (s_hi) atomicAdd(&sums[1], s_hi);
+        if (nloops) atomicAdd(loops, nloops);
+        if (dmax) atomicMax(maxdeg, dmax);
         if (flags) atomicOr(bad, flags);
     }
 }
@@ -404,10 +408,10 @@ mcf_status build_columns(mcf_graph* g, const int64_t* row_ptr, const int32_t* co
             ri[(size_t)q] = (int32_t)r;
             if (values) cv[(size_t)q] = va[p];
         }
-    if (cudaMalloc(&g->col_ptr, (size_t)(n + 1) * sizeof(int64_t)) != cudaSuccess ||
-        cudaMalloc(&g->row_idx, ri.size() * sizeof(int32_t)) != cudaSuccess ||
-        (values && cudaMalloc(&g->col_values, cv.size() * sizeof(float)) != cudaSuccess) ||
-        (values && cudaMalloc(&g->col_sq, (size_t)std::max<int64_t>(n, 1) * sizeof(double)) != cudaSuccess)) {
+    if (graph_alloc(&g->col_ptr, (size_t)(n + 1) * sizeof(int64_t)) != cudaSuccess ||
+        graph_alloc(&g->row_idx, ri.size() * sizeof(int32_t)) != cudaSuccess ||
+        (values && graph_alloc(&g->col_values, cv.size() * sizeof(float)) != cudaSuccess) ||
+        (values && graph_alloc(&g->col_sq, (size_t)std::max<int64_t>(n, 1) * sizeof(double)) != cudaSuccess)) {
         cudaGetLastError();
         return fail(MCF_ERR_OOM, "device allocation of the column-major copy failed");
     }
@@ -453,9 +457,9 @@ mcf_status mcf_create_graph(int64_t n, const int64_t* row_ptr, const int32_t* co
         return s;
     };
     const cudaMemcpyKind kind = dev_in ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    if (cudaMalloc(&g->row_ptr, (size_t)(n + 1) * sizeof(int64_t)) != cudaSuccess ||
-        cudaMalloc(&g->col_idx, (size_t)std::max<int64_t>(nnz, 1) * sizeof(int32_t)) != cudaSuccess ||
-        cudaMalloc(&g->diag, (size_t)std::max<int64_t>(n, 1) * sizeof(double)) != cudaSuccess) {
+    if (graph_alloc(&g->row_ptr, (size_t)(n + 1) * sizeof(int64_t)) != cudaSuccess ||
+        graph_alloc(&g->col_idx, (size_t)std::max<int64_t>(nnz, 1) * sizeof(int32_t)) != cudaSuccess ||
+        graph_alloc(&g->diag, (size_t)std::max<int64_t>(n, 1) * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
         return cleanup(fail(MCF_ERR_OOM, "device allocation of the CSR failed"));
     }
@@ -463,7 +467,7 @@ mcf_status mcf_create_graph(int64_t n, const int64_t* row_ptr, const int32_t* co
         (nnz > 0 && cudaMemcpy(g->col_idx, col_idx, (size_t)nnz * sizeof(int32_t), kind) != cudaSuccess))
         return cleanup(fail(MCF_ERR_CUDA, std::string("CSR copy failed: ") + cudaGetErrorString(cudaGetLastError())));
     if (g->weighted) {
-        if (cudaMalloc(&g->values, (size_t)std::max<int64_t>(nnz, 1) * sizeof(float)) != cudaSuccess) {
+        if (graph_alloc(&g->values, (size_t)std::max<int64_t>(nnz, 1) * sizeof(float)) != cudaSuccess) {
             cudaGetLastError();
             return cleanup(fail(MCF_ERR_OOM, "device allocation of the values failed"));
         }
@@ -473,7 +477,7 @@ mcf_status mcf_create_graph(int64_t n, const int64_t* row_ptr, const int32_t* co
     // validation
     struct Flags { uint32_t bad; uint32_t pad; unsigned long long maxdeg; unsigned long long loops; unsigned long long sums[2]; };
     Flags* dflags = nullptr;
-    if (cudaMalloc(&dflags, sizeof(Flags)) != cudaSuccess) { cudaGetLastError(); return cleanup(fail(MCF_ERR_OOM, "alloc")); }
+    if (graph_alloc(&dflags, sizeof(Flags)) != cudaSuccess) { cudaGetLastError(); return cleanup(fail(MCF_ERR_OOM, "alloc")); }
     cudaMemset(dflags, 0, sizeof(Flags));
     cudaMemset(g->diag, 0, (size_t)std::max<int64_t>(n, 1) * sizeof(double));
     if (n > 0) {
@@ -483,7 +487,7 @@ mcf_status mcf_create_graph(int64_t n, const int64_t* row_ptr, const int32_t* co
     }
     Flags hf;
     cudaError_t e = cudaMemcpy(&hf, dflags, sizeof(Flags), cudaMemcpyDeviceToHost);
-    cudaFree(dflags);
+    graph_free(dflags);
     if (e != cudaSuccess) return cleanup(fail(MCF_ERR_CUDA, std::string("validation: ") + cudaGetErrorString(e)));
     const bool general = (flags & MCF_GRAPH_NONSYMMETRIC) != 0;
     if (!general && !(hf.bad & (BAD_ROWPTR | BAD_COLUMN)) && hf.sums[0] != hf.sums[1]) hf.bad |= BAD_SYMMETRY;
@@ -503,23 +507,23 @@ mcf_status mcf_create_graph(int64_t n, const int64_t* row_ptr, const int32_t* co
         double* s_buf = nullptr;
         int32_t *sm = nullptr, *lg = nullptr;
         size_t m = (size_t)std::max<int64_t>(nnz, 1);
-        if (cudaMalloc(&g->row_abs, (size_t)n * sizeof(double)) != cudaSuccess ||
-            cudaMalloc(&g->row_sq, (size_t)n * sizeof(double)) != cudaSuccess ||
-            cudaMalloc(&g->went, m * sizeof(WEntry)) != cudaSuccess || cudaMalloc(&s_buf, m * sizeof(double)) != cudaSuccess ||
-            cudaMalloc(&sm, m * sizeof(int32_t)) != cudaSuccess || cudaMalloc(&lg, m * sizeof(int32_t)) != cudaSuccess) {
+        if (graph_alloc(&g->row_abs, (size_t)n * sizeof(double)) != cudaSuccess ||
+            graph_alloc(&g->row_sq, (size_t)n * sizeof(double)) != cudaSuccess ||
+            graph_alloc(&g->went, m * sizeof(WEntry)) != cudaSuccess || graph_alloc(&s_buf, m * sizeof(double)) != cudaSuccess ||
+            graph_alloc(&sm, m * sizeof(int32_t)) != cudaSuccess || graph_alloc(&lg, m * sizeof(int32_t)) != cudaSuccess) {
             cudaGetLastError();
-            cudaFree(s_buf); cudaFree(sm); cudaFree(lg);
+            graph_free(s_buf); graph_free(sm); graph_free(lg);
             return cleanup(fail(MCF_ERR_OOM, "device allocation of the alias tables failed"));
         }
         weighted_rows<<<(unsigned)((n + 127) / 128), 128>>>(n, g->row_ptr, g->col_idx, g->values, g->row_abs, g->row_sq,
                                                              g->went, s_buf, sm, lg);
         unsigned long long* dm = nullptr;
-        cudaMalloc(&dm, sizeof(unsigned long long));
+        graph_alloc(&dm, sizeof(unsigned long long));
         cudaMemset(dm, 0, sizeof(unsigned long long));
         max_f64<<<num_sms(), 256>>>(n, g->row_abs, dm);
         unsigned long long hm = 0;
         e = cudaMemcpy(&hm, dm, sizeof(hm), cudaMemcpyDeviceToHost);
-        cudaFree(dm); cudaFree(s_buf); cudaFree(sm); cudaFree(lg);
+        graph_free(dm); graph_free(s_buf); graph_free(sm); graph_free(lg);
         if (e != cudaSuccess) return cleanup(fail(MCF_ERR_CUDA, std::string("alias tables: ") + cudaGetErrorString(e)));
         double gm;
         memcpy(&gm, &hm, sizeof(gm));
@@ -544,20 +548,21 @@ mcf_status mcf_create_graph(int64_t n, const int64_t* row_ptr, const int32_t* co
 mcf_status mcf_destroy_graph(mcf_graph_t g) {
     if (!g) return MCF_OK;
     cudaDeviceSynchronize();
-    cudaFree(g->row_ptr);
-    cudaFree(g->col_idx);
-    cudaFree(g->values);
-    cudaFree(g->row_abs);
-    cudaFree(g->row_sq);
-    cudaFree(g->diag);
-    cudaFree(g->went);
-    cudaFree(g->node_od);
-    cudaFree(g->edge_od);
+    graph_free(g->row_ptr);
+    graph_free(g->col_idx);
+    graph_free(g->values);
+    graph_free(g->row_abs);
+    graph_free(g->row_sq);
+    graph_free(g->diag);
+    graph_free(g->went);
+    graph_free(g->node_od);
+    graph_free(g->edge_od);
+    graph_free(g->edge_rec);
     if (!g->symmetric) {
-        cudaFree(g->col_ptr);
-        cudaFree(g->row_idx);
-        cudaFree(g->col_values);
-        cudaFree(g->col_sq);
+        graph_free(g->col_ptr);
+        graph_free(g->row_idx);
+        graph_free(g->col_values);
+        graph_free(g->col_sq);
     }
     delete g;
     return MCF_OK;

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <stdlib.h>
+#include <string.h>
 
 #include <algorithm>
 #include <string>
@@ -70,6 +71,10 @@ struct mcf_graph {
     // column index and then a node record.
     uint2* node_od = nullptr;     // n
     uint2* edge_od = nullptr;     // nnz
+    // Binary graphs, built on the first subgraph-centrality solve: per CSR
+    // entry the neighbour's {row offset, degree, node id, 0} (16 bytes), so a
+    // RandFunmDiag step is one random read that also names the visited node.
+    uint4* edge_rec = nullptr;    // nnz
     // Column-major copy of A (column i: rows row_idx[col_ptr[i] .. col_ptr[i+1])
     // in increasing order, values col_values) and sum_j a_ji^2 per column.
     // For a symmetric A these alias the row arrays; a general A (created with
@@ -250,6 +255,8 @@ struct WalkTuning {
     int l2_fetch = 32;     // MCF_L2_FETCH_BYTES: L2 fetch granularity for walk kernels (0 = leave as is)
     bool prefetch = false; // MCF_WALK_PREFETCH=1: issue the next random read before the cutoff test
     int walks_per_thread = 1;  // MCF_WALK_PER_THREAD=2: two walks per thread in the TC kernel
+    bool tc_col = false;   // MCF_WALK_TC_READ=col: column index + node record instead of the per-entry record
+    bool diag_edge = true; // MCF_DIAG_EDGE=0: subgraph-centrality walks read node record + column index
 };
 inline const WalkTuning& walk_tuning() {
     static WalkTuning t = [] {
@@ -258,6 +265,8 @@ inline const WalkTuning& walk_tuning() {
         if (const char* e = getenv("MCF_WALK_PREFETCH")) w.prefetch = atoi(e) != 0;
         if (const char* e = getenv("MCF_WALK_PER_THREAD")) w.walks_per_thread = atoi(e) == 2 ? 2 : 1;
         if (const char* e = getenv("MCF_WALK_TC_PATH")) w.tc_path = atoi(e) != 0;
+        if (const char* e = getenv("MCF_WALK_TC_READ")) w.tc_col = strcmp(e, "col") == 0;
+        if (const char* e = getenv("MCF_DIAG_EDGE")) w.diag_edge = atoi(e) != 0;
         if (const char* e = getenv("MCF_WALK_MINB")) w.minb = atoi(e) >= 8 ? 8 : (atoi(e) <= 5 ? 5 : 6);
         if (const char* e = getenv("MCF_WALK_GRAB")) w.grab = std::max(1, std::min(64, atoi(e)));
         return w;
@@ -267,7 +276,23 @@ inline const WalkTuning& walk_tuning() {
 
 // Builds the graph's node_od / edge_od arrays on first use (binary, nnz < 2^32).
 mcf_status ensure_edge_od(mcf_graph* g, cudaStream_t st);
+mcf_status ensure_edge_rec(mcf_graph* g, cudaStream_t st);
 // Keeps freed stream-ordered scratch in the device's default pool.
 void keep_pool_memory();
+
+// A graph's device arrays come from the device's stream-ordered pool, which
+// keeps freed memory (keep_pool_memory), so creating and destroying graphs of
+// similar sizes reuses memory instead of mapping new pages every time.
+inline cudaError_t graph_alloc(void** p, size_t bytes, cudaStream_t st = 0) {
+    keep_pool_memory();
+    return cudaMallocAsync(p, bytes, st);
+}
+template <class T>
+inline cudaError_t graph_alloc(T** p, size_t bytes, cudaStream_t st = 0) {
+    return graph_alloc(reinterpret_cast<void**>(p), bytes, st);
+}
+inline void graph_free(void* p, cudaStream_t st = 0) {
+    if (p) cudaFreeAsync(p, st);
+}
 
 }  // namespace mcf

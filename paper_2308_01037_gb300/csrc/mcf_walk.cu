@@ -310,9 +310,10 @@ __global__ void degree_table(int64_t max_deg, double gamma, float* __restrict__ 
 // Same walk schedule, Philox streams, float32 arithmetic and accumulation as
 // walk_action_kernel<false, false, MINB> (so the same result up to float64
 // summation order), with the per-step state reduced to {offset, degree}.
-template <int MINB, bool PREFETCH>
+template <int MINB, bool PREFETCH, bool VIA_COL>
 __global__ void __launch_bounds__(256, MINB) walk_tc_kernel(
-    const uint2* __restrict__ nod, const uint2* __restrict__ eod, const float* __restrict__ rm,
+    const uint2* __restrict__ nod, const uint2* __restrict__ eod, const int32_t* __restrict__ col,
+    const float* __restrict__ rm,
     const int32_t* __restrict__ starts, const int64_t* __restrict__ soff, const int64_t* __restrict__ goff,
     const uint32_t* __restrict__ chunk_s0,
     const double* __restrict__ zeta_g, int K, float wc32, uint2 key, uint32_t req, int grab,
@@ -338,6 +339,18 @@ __global__ void __launch_bounds__(256, MINB) walk_tc_kernel(
     uint4 u = make_uint4(0u, 0u, 0u, 0u);
     F2Acc a32;
     uint32_t my_steps = 0, my_walks = 0, flags = 0;
+    // The {offset, degree} of entry j's neighbour: one random read of the
+    // per-entry record, or (VIA_COL) the column index and then the
+    // neighbour's node record, which stays in L2 (half the bytes of DRAM
+    // array per entry, one more dependent read per step).
+    auto next_od = [&](uint32_t j) -> uint2 {
+        if constexpr (VIA_COL) {
+            const int32_t nb = load_col(col + (int64_t)off + j, policy_evict_first());
+            return load_od(nod + nb, policy_evict_last());
+        } else {
+            return load_od(eod + (int64_t)off + j, policy_evict_first());
+        }
+    };
     for (;;) {
         unsigned idle = __ballot_sync(FULL, !active);
         while (idle && !exhausted) {
@@ -399,7 +412,7 @@ __global__ void __launch_bounds__(256, MINB) walk_tc_kernel(
             if (PREFETCH && !last) {
                 uint32_t w0, w1;
                 walk_words<false>(u, k, (uint32_t)g, (uint32_t)((uint64_t)g >> 32), req, key, w0, w1);
-                nx = load_od(eod + (int64_t)off + __umulhi(w0, deg), policy_evict_first());
+                nx = next_od(__umulhi(w0, deg));
             }
             done = !(fabsf(W) > wc32);
             if (!done) {
@@ -411,7 +424,7 @@ __global__ void __launch_bounds__(256, MINB) walk_tc_kernel(
                     if (!PREFETCH) {
                         uint32_t w0, w1;
                         walk_words<false>(u, k, (uint32_t)g, (uint32_t)((uint64_t)g >> 32), req, key, w0, w1);
-                        nx = load_od(eod + (int64_t)off + __umulhi(w0, deg), policy_evict_first());
+                        nx = next_od(__umulhi(w0, deg));
                     }
                     W = __fmul_rn(W, t);
                     off = nx.x;
@@ -673,15 +686,17 @@ __global__ void action_epilogue_nodes(int64_t m, const int64_t* __restrict__ nod
 // partial row and the stopped walks resume from their first unrecorded visit
 // (walks are deterministic in their Philox counters and Q_k enters d
 // linearly).
-template <bool F64, bool WEIGHTED, bool DENSE>
+template <bool F64, bool WEIGHTED, bool DENSE, bool EDGE>
 __global__ void __launch_bounds__(256) walk_diag_kernel(
     const Rec<F64>* __restrict__ rec, const int64_t* __restrict__ cp, const int32_t* __restrict__ ri,
     const float* __restrict__ cv, const int32_t* __restrict__ col, const WEntry* __restrict__ went,
+    const uint4* __restrict__ erec, const uint2* __restrict__ nod, const float* __restrict__ rm,
     const int32_t* __restrict__ starts,
     const int64_t* __restrict__ woff, const int64_t* __restrict__ nw, const uint8_t* __restrict__ want, double gamma,
     const double* __restrict__ zeta_g, int K, double wc, float wc32, uint2 key, uint32_t req, int64_t n, int cap_log2,
     double* __restrict__ qval, double* __restrict__ dacc, unsigned long long* __restrict__ counters) {
     using real = typename std::conditional<F64, double, float>::type;
+    static_assert(!EDGE || (!F64 && !WEIGHTED), "neighbour records serve binary float32 walks");
     extern __shared__ int32_t smem_i[];
     __shared__ real zeta[MCF_MAX_COEFFS];
     __shared__ int64_t cur;
@@ -715,6 +730,8 @@ __global__ void __launch_bounds__(256) walk_diag_kernel(
         const uint32_t k0 = (uint32_t)starts[s];
         const int64_t Nk = nw[k0];
         const int64_t g0 = woff[k0];
+        uint2 od0 = make_uint2(0u, 0u);
+        if constexpr (EDGE) od0 = nod[k0];
         if (threadIdx.x == 0 && visit0 && K >= 2) {
             double z2;
             if constexpr (F64) z2 = zeta[2];
@@ -729,8 +746,13 @@ __global__ void __launch_bounds__(256) walk_diag_kernel(
         for (;;) {
             bool stopped = false;
             while (w < Nk) {
-                const int f = diag_walk<F64, WEIGHTED, DENSE>(t, k0, g0 + w, from, cfrom, rec, col, went, zeta, K, wc,
-                                                              wc32, key, req, steps, flags);
+                int f;
+                if constexpr (EDGE)
+                    f = diag_walk_edge<DENSE>(t, k0, od0, g0 + w, from, cfrom, erec, rm, zeta, K, wc32, key, req, steps,
+                                              flags);
+                else
+                    f = diag_walk<F64, WEIGHTED, DENSE>(t, k0, g0 + w, from, cfrom, rec, col, went, zeta, K, wc, wc32,
+                                                        key, req, steps, flags);
                 if (f >= 0) {
                     from = f;
                     cfrom = f;
@@ -924,26 +946,63 @@ static void launch_action_walks_t(const mcf_graph* g, const Prep& P, uint32_t* c
 }
 
 // Builds the graph's node_od / edge_od arrays on first use (binary, nnz < 2^32).
-mcf_status ensure_edge_od(mcf_graph* g, cudaStream_t st) {
-    // built once per graph; concurrent callers on other streams must not see
-    // the pointers before the arrays are complete
-    static std::mutex mu;
-    std::lock_guard<std::mutex> lk(mu);
-    if (g->edge_od) return MCF_OK;
-    uint2 *nod = nullptr, *eod = nullptr;
-    if (cudaMalloc(&nod, (size_t)std::max<int64_t>(g->n, 1) * sizeof(uint2)) != cudaSuccess ||
-        cudaMalloc(&eod, (size_t)std::max<int64_t>(g->nnz, 1) * sizeof(uint2)) != cudaSuccess) {
+// node_od (and the per-entry arrays below) are built once per graph;
+// concurrent callers on other streams must not see the pointers before the
+// arrays are complete, so each is published after a synchronisation.
+static std::mutex g_records_mu;
+
+static mcf_status ensure_node_od_locked(mcf_graph* g, cudaStream_t st) {
+    if (g->node_od) return MCF_OK;
+    uint2* nod = nullptr;
+    if (graph_alloc(&nod, (size_t)std::max<int64_t>(g->n, 1) * sizeof(uint2), st) != cudaSuccess) {
         cudaGetLastError();
-        cudaFree(nod);
-        cudaFree(eod);
-        return fail(MCF_ERR_OOM, "device allocation of the per-entry walk records failed");
+        return fail(MCF_ERR_OOM, "device allocation of the node records failed");
     }
     build_node_od<<<grid_for(g->n, 256), 256, 0, st>>>(g->n, g->row_ptr, nod);
-    build_edge_od<<<grid_for(g->nnz, 256), 256, 0, st>>>(g->nnz, g->col_idx, nod, eod);
     MCF_CUDA_TRY(cudaGetLastError());
     MCF_CUDA_TRY(cudaStreamSynchronize(st));
     g->node_od = nod;
+    return MCF_OK;
+}
+
+mcf_status ensure_edge_od(mcf_graph* g, cudaStream_t st) {
+    std::lock_guard<std::mutex> lk(g_records_mu);
+    if (g->edge_od) return MCF_OK;
+    MCF_TRY(ensure_node_od_locked(g, st));
+    uint2* eod = nullptr;
+    if (graph_alloc(&eod, (size_t)std::max<int64_t>(g->nnz, 1) * sizeof(uint2), st) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MCF_ERR_OOM, "device allocation of the per-entry walk records failed");
+    }
+    build_edge_od<<<grid_for(g->nnz, 256), 256, 0, st>>>(g->nnz, g->col_idx, g->node_od, eod);
+    MCF_CUDA_TRY(cudaGetLastError());
+    MCF_CUDA_TRY(cudaStreamSynchronize(st));
     g->edge_od = eod;
+    return MCF_OK;
+}
+
+__global__ void build_edge_rec(int64_t nnz, const int32_t* __restrict__ col, const uint2* __restrict__ nod,
+                               uint4* __restrict__ erec) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = col[p];
+        const uint2 od = nod[c];
+        erec[p] = make_uint4(od.x, od.y, (uint32_t)c, 0u);
+    }
+}
+
+mcf_status ensure_edge_rec(mcf_graph* g, cudaStream_t st) {
+    std::lock_guard<std::mutex> lk(g_records_mu);
+    if (g->edge_rec) return MCF_OK;
+    MCF_TRY(ensure_node_od_locked(g, st));
+    uint4* er = nullptr;
+    if (graph_alloc(&er, (size_t)std::max<int64_t>(g->nnz, 1) * sizeof(uint4), st) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MCF_ERR_OOM, "device allocation of the per-entry neighbour records failed");
+    }
+    build_edge_rec<<<grid_for(g->nnz, 256), 256, 0, st>>>(g->nnz, g->col_idx, g->node_od, er);
+    MCF_CUDA_TRY(cudaGetLastError());
+    MCF_CUDA_TRY(cudaStreamSynchronize(st));
+    g->edge_rec = er;
     return MCF_OK;
 }
 
@@ -958,10 +1017,12 @@ static void launch_tc_walks_t(const mcf_graph* g, const Prep& P, const float* rm
                                    cutoff_f32(wc), key, req, walk_tuning().grab, acc, P.counters);
         return;
     }
-    auto kern = walk_tuning().prefetch ? walk_tc_kernel<MINB, true> : walk_tc_kernel<MINB, false>;
+    const bool pf = walk_tuning().prefetch, vc = walk_tuning().tc_col;
+    auto kern = pf ? (vc ? walk_tc_kernel<MINB, true, true> : walk_tc_kernel<MINB, true, false>)
+                   : (vc ? walk_tc_kernel<MINB, false, true> : walk_tc_kernel<MINB, false, false>);
     const int grid = persistent_grid(kern, 256, 0);
     ScopedL2Fetch fetch(walk_tuning().l2_fetch);
-    kern<<<grid, 256, 0, st>>>(g->node_od, g->edge_od, rm, P.starts, P.cof, P.soff, chunk_s0, P.zeta, K,
+    kern<<<grid, 256, 0, st>>>(g->node_od, g->edge_od, g->col_idx, rm, P.starts, P.cof, P.soff, chunk_s0, P.zeta, K,
                                cutoff_f32(wc), key, req, walk_tuning().grab, acc, P.counters);
 }
 
@@ -1097,14 +1158,26 @@ static mcf_status solve_action(mcf_graph* g, const mcf_params* p, const double* 
 }
 
 constexpr int64_t DIAG_DENSE_MAX = 16384;   // dense row Q_k (global memory) up to this many nodes
+constexpr int DIAG_CAP_LOG2_MAX = 12;
+constexpr int64_t DIAG_EDGE_MIN_NNZ = (int64_t)1 << 20;
 
 // Launch shape of the diag kernel: threads per CTA follow the walks per start
-// (64 .. 256) and the hash holds about four visits per walk of a start (at
-// most 2^14 slots); a start with more distinct visits flushes its partial row.
+// (64 .. 256) and the hash holds about four visits per walk of a start, at
+// most 2^DIAG_CAP_LOG2_MAX slots (keys and slot list: 32 KB of shared memory,
+// so several CTAs share an SM and keep enough walks in flight); a start with
+// more distinct visits flushes its partial row.
 template <bool F64, bool WEIGHTED, bool DENSE>
 static mcf_status launch_diag(const mcf_graph* g, const Prep& P, const uint8_t* want, double gamma, int K, double wc,
                               uint2 key, uint32_t req, int64_t nk_hint, double* dacc, Scratch& sc, cudaStream_t st) {
-    auto kern = walk_diag_kernel<F64, WEIGHTED, DENSE>;
+    // binary float32 walks read 16-byte neighbour records when the graph has them
+    constexpr bool can_edge = !F64 && !WEIGHTED;
+    const bool edge = can_edge && g->edge_rec != nullptr;
+    auto kern = edge ? walk_diag_kernel<F64, WEIGHTED, DENSE, can_edge> : walk_diag_kernel<F64, WEIGHTED, DENSE, false>;
+    float* rm = nullptr;
+    if (edge) {
+        MCF_TRY(sc.get(&rm, (size_t)g->max_degree + 1));
+        degree_table<<<grid_for(g->max_degree + 1, 256), 256, 0, st>>>(g->max_degree, gamma, rm);
+    }
     int threads = 256;
     if (nk_hint > 0 && nk_hint <= 64) threads = 64;
     else if (nk_hint > 0 && nk_hint <= 128) threads = 128;
@@ -1114,7 +1187,7 @@ static mcf_status launch_diag(const mcf_graph* g, const Prep& P, const uint8_t* 
     if (!DENSE) {
         const int64_t want_slots = std::max<int64_t>(4 * std::max<int64_t>(nk_hint, 1) * 4, 4 * threads);
         cap_log2 = 10;
-        while (cap_log2 < 14 && ((int64_t)1 << cap_log2) < want_slots) ++cap_log2;
+        while (cap_log2 < DIAG_CAP_LOG2_MAX && ((int64_t)1 << cap_log2) < want_slots) ++cap_log2;
         cap = (int64_t)1 << cap_log2;
         smem = (size_t)cap * 2 * sizeof(int32_t);
     }
@@ -1124,8 +1197,8 @@ static mcf_status launch_diag(const mcf_graph* g, const Prep& P, const uint8_t* 
     MCF_TRY(sc.get(&qval, (size_t)grid * (size_t)std::max<int64_t>(cap, 1)));
     ScopedL2Fetch fetch(walk_tuning().l2_fetch);
     kern<<<grid, threads, smem, st>>>((const Rec<F64>*)P.rec, g->col_ptr, g->row_idx, g->col_values, g->col_idx,
-                                      g->went, P.starts, P.woff, P.nw, want, gamma, P.zeta, K, wc, cutoff_f32(wc), key,
-                                      req, g->n, cap_log2, qval, dacc, P.counters);
+                                      g->went, g->edge_rec, g->node_od, rm, P.starts, P.woff, P.nw, want, gamma, P.zeta,
+                                      K, wc, cutoff_f32(wc), key, req, g->n, cap_log2, qval, dacc, P.counters);
     MCF_CUDA_TRY(cudaGetLastError());
     return MCF_OK;
 }
@@ -1192,6 +1265,11 @@ static mcf_status solve_diag(mcf_graph* g, const mcf_params* p, const int64_t* n
             }
             const uint2 key = philox_key(p->seed);
             const bool dense = n <= DIAG_DENSE_MAX;
+            // larger graphs: one 16-byte neighbour record per step (on a small
+            // graph the node records and column indices stay in L1 and L2)
+            if (!f64 && !g->weighted && g->nnz >= DIAG_EDGE_MIN_NNZ && g->nnz < ((int64_t)1 << 32) &&
+                walk_tuning().diag_edge)
+                MCF_TRY(ensure_edge_rec(g, st));
             mcf_status rc;
             const int64_t nk_hint = p->walks_per_node > 0 ? p->walks_per_node : std::max<int64_t>(1, p->n_walks / std::max<int64_t>(n, 1));
 #define MCF_DIAG(F, W, D) rc = launch_diag<F, W, D>(g, P, want, gamma, K, p->w_cutoff, key, p->request_id, nk_hint, dacc, sc, st)

@@ -156,7 +156,7 @@ def test_subgraph_centrality_dense_row(ba1000, precision):
 
 @pytest.mark.parametrize("precision", [M.MCF_F64, M.MCF_F32W_F64ACC])
 def test_subgraph_centrality_hashed_row_with_flushes(precision):
-    # n > 16384 selects the hashed row Q_k (at most 2^14 slots); 3000 walks of up
+    # n > 16384 selects the hashed row Q_k (at most 2^12 slots); 3000 walks of up
     # to 28 steps from a hub overflow it, exercising the flush-and-replay path
     g = I.rmat(15, 16, seed=7)
     gam = 1.0 / R.lambda_max(g)
