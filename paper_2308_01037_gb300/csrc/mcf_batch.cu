@@ -1,8 +1,8 @@
 // Batched solves: many queries on many resident graphs in one pass.
 //
 // Total-communicability and Katz queries (RandFunmAction with v = 1,
-// Algorithm 3) on binary graphs in MCF_F32W_F64ACC share ONE persistent walk
-// launch; subgraph-centrality queries (RandFunmDiag, Section 3.3) on binary
+// Algorithm 3) on binary graphs in MCF_F32W_F64ACC with fewer than
+// B_FUSED_MAX_WALKS walks share ONE persistent walk launch; subgraph-centrality queries (RandFunmDiag, Section 3.3) on binary
 // graphs in MCF_F32W_F64ACC share one diag launch.  Their preparation
 // (Definition 1's allocation) and epilogues are segmented kernels over the
 // concatenation of all their node sets.  Each query keeps its own walk ids
@@ -30,6 +30,11 @@
 namespace mcf {
 
 constexpr int B_RED_BLOCKS = 256;    // must equal the single-query colnorm grid
+// A total-communicability or Katz query with this many walks fills the GPU on
+// its own; it runs through the single-query kernel (whose per-step parameters
+// are kernel arguments, measured about 12 % faster per step than the fused
+// kernel's per-warp query slot), the smaller ones share the fused launch.
+constexpr int64_t B_FUSED_MAX_WALKS = (int64_t)1 << 25;
 constexpr int B_RED_THREADS = 256;
 constexpr int B_CHUNK = 32;
 constexpr int64_t B_DENSE_MAX = 16384;
@@ -823,7 +828,9 @@ mcf_status mcf_batch_create(const mcf_query* queries, int32_t n_queries, uint32_
             return bail(fail(MCF_ERR_INVALID_ARG, "query " + std::to_string(i) + ": n_walks or walks_per_node must be > 0"));
         b->params[i] = p;
         const bool binary32 = !q.graph->weighted && p.precision == MCF_F32W_F64ACC && q.graph->nnz < ((int64_t)1 << 32);
-        if ((q.kind == MCF_QUERY_TOTAL_COMMUNICABILITY || q.kind == MCF_QUERY_KATZ) && binary32 && p.n_coeffs >= 3)
+        const int64_t tc_walks = p.walks_per_node > 0 ? p.walks_per_node * q.graph->n : p.n_walks;
+        if ((q.kind == MCF_QUERY_TOTAL_COMMUNICABILITY || q.kind == MCF_QUERY_KATZ) && binary32 && p.n_coeffs >= 3 &&
+            tc_walks < B_FUSED_MAX_WALKS)
             tc.push_back(i);
         else if (q.kind == MCF_QUERY_SUBGRAPH_CENTRALITY && binary32 && p.n_coeffs >= 3)
             sc.push_back(i);

@@ -69,6 +69,9 @@ def make_queries(graphs):
                    request_id=400, precision=M.MCF_F32W_F64ACC))
     qs.append(dict(graph=h, kind=M.MCF_QUERY_TOTAL_COMMUNICABILITY, coeffs=c30, scale=gam, n_walks=50000, seed=9,
                    request_id=500, precision=M.MCF_F64))
+    # a query large enough to run through the single-query kernel inside the batch
+    qs.append(dict(graph=h, kind=M.MCF_QUERY_TOTAL_COMMUNICABILITY, coeffs=c30, scale=gam, n_walks=1 << 25, seed=12,
+                   request_id=700, precision=M.MCF_F32W_F64ACC))
     gw, hw, gamw = graphs["weighted"]
     qs.append(dict(graph=hw, kind=M.MCF_QUERY_SUBGRAPH_CENTRALITY, coeffs=R.exp_coeffs(20), scale=gamw,
                    walks_per_node=40, seed=11, request_id=600, precision=M.MCF_F32W_F64ACC))
