@@ -529,7 +529,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched, serving, dense RandFunm and classical-method measurements")
     ap.add_argument("--batch-graphs", type=int, default=64)
     ap.add_argument("--batch-log-n-max", type=float, default=5.0)
-    ap.add_argument("--serve-scales", default="14-20")
+    ap.add_argument("--serve-scales", default="16-22")
     ap.add_argument("--serve-requests", type=int, default=600)
     ap.add_argument("--section", default="main", choices=["main", "funm_full", "mc_classic", "batched", "serving"],
                     help="run only that measurement (1 GPU) and print its JSON")

@@ -54,10 +54,10 @@ typedef enum {
     MCF_ERR_OOM = 3,              /* device or host allocation failed */
     MCF_ERR_CUDA = 4,             /* a CUDA runtime call failed; see mcf_last_error() */
     MCF_ERR_ADMISSION = 5,        /* a request does not fit the caller's memory budget */
-    MCF_ERR_TIMEOUT = 6,          /* a bounded device-side wait gave up */
-    MCF_ERR_CANCELLED = 7,
-    MCF_ERR_ACCURACY_BUDGET = 8,
-    MCF_WARN_OVERFLOW = 9,        /* a walk weight overflowed float32; result flagged */
+    MCF_ERR_TIMEOUT = 6,          /* mcf_server_wait gave up before the request completed */
+    MCF_ERR_CANCELLED = 7,        /* reserved (not returned by this build) */
+    MCF_ERR_ACCURACY_BUDGET = 8,  /* reserved (not returned by this build) */
+    MCF_WARN_OVERFLOW = 9,        /* reserved: a float32 weight overflow sets bit 0 of mcf_stats.flags */
     MCF_ERR_UNSUPPORTED = 10      /* a valid request this build does not implement */
 } mcf_status;
 

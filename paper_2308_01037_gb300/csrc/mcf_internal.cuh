@@ -257,6 +257,7 @@ struct WalkTuning {
     int walks_per_thread = 1;  // MCF_WALK_PER_THREAD=2: two walks per thread in the TC kernel
     bool tc_col = false;   // MCF_WALK_TC_READ=col: column index + node record instead of the per-entry record
     bool diag_edge = true; // MCF_DIAG_EDGE=0: subgraph-centrality walks read node record + column index
+    int diag_cap_log2 = 12; // MCF_DIAG_CAP_LOG2 (10..14): largest hashed row Q_k, log2 of its slots
 };
 inline const WalkTuning& walk_tuning() {
     static WalkTuning t = [] {
@@ -267,6 +268,7 @@ inline const WalkTuning& walk_tuning() {
         if (const char* e = getenv("MCF_WALK_TC_PATH")) w.tc_path = atoi(e) != 0;
         if (const char* e = getenv("MCF_WALK_TC_READ")) w.tc_col = strcmp(e, "col") == 0;
         if (const char* e = getenv("MCF_DIAG_EDGE")) w.diag_edge = atoi(e) != 0;
+        if (const char* e = getenv("MCF_DIAG_CAP_LOG2")) w.diag_cap_log2 = std::max(10, std::min(14, atoi(e)));
         if (const char* e = getenv("MCF_WALK_MINB")) w.minb = atoi(e) >= 8 ? 8 : (atoi(e) <= 5 ? 5 : 6);
         if (const char* e = getenv("MCF_WALK_GRAB")) w.grab = std::max(1, std::min(64, atoi(e)));
         return w;

@@ -1158,13 +1158,12 @@ static mcf_status solve_action(mcf_graph* g, const mcf_params* p, const double* 
 }
 
 constexpr int64_t DIAG_DENSE_MAX = 16384;   // dense row Q_k (global memory) up to this many nodes
-constexpr int DIAG_CAP_LOG2_MAX = 12;
 constexpr int64_t DIAG_EDGE_MIN_NNZ = (int64_t)1 << 20;
 
 // Launch shape of the diag kernel: threads per CTA follow the walks per start
 // (64 .. 256) and the hash holds about four visits per walk of a start, at
-// most 2^DIAG_CAP_LOG2_MAX slots (keys and slot list: 32 KB of shared memory,
-// so several CTAs share an SM and keep enough walks in flight); a start with
+// most 2^12 slots by default (keys and slot list: 32 KB of shared memory, so
+// several CTAs share an SM and keep enough walks in flight); a start with
 // more distinct visits flushes its partial row.
 template <bool F64, bool WEIGHTED, bool DENSE>
 static mcf_status launch_diag(const mcf_graph* g, const Prep& P, const uint8_t* want, double gamma, int K, double wc,
@@ -1187,7 +1186,7 @@ static mcf_status launch_diag(const mcf_graph* g, const Prep& P, const uint8_t* 
     if (!DENSE) {
         const int64_t want_slots = std::max<int64_t>(4 * std::max<int64_t>(nk_hint, 1) * 4, 4 * threads);
         cap_log2 = 10;
-        while (cap_log2 < DIAG_CAP_LOG2_MAX && ((int64_t)1 << cap_log2) < want_slots) ++cap_log2;
+        while (cap_log2 < walk_tuning().diag_cap_log2 && ((int64_t)1 << cap_log2) < want_slots) ++cap_log2;
         cap = (int64_t)1 << cap_log2;
         smem = (size_t)cap * 2 * sizeof(int32_t);
     }
