@@ -664,8 +664,12 @@ def main():
             e2e["value"] = float(t.item())
 
     subset = None
+    max_rel_se = None
     if rank == 0 and world == 1 and w["query"] == "tc" and not args.no_batch:
         subset = run_subset(M, h, g, c, base, out)
+        # the library's own standard-error estimate of one solve (Section 3.5)
+        _, st_se = solve(h, c, out=out, request_id=88, stats=True, error_estimate=True, **base)
+        max_rel_se = st_se["max_rel_se"]
     batched = serving = funm_full = mc_classic = None
     if rank == 0 and world == 1 and not args.no_batch:
         from oracle import reference as R
@@ -688,7 +692,7 @@ def main():
             "config": {"workload": w["label"], "n": g.n, "nnz": g.nnz, "lambda_max": lam,
                        "walks_per_solve": walks_total // args.steps, "l2": "inputs larger than L2 (CSR > 129 MB)",
                        "parallelism": f"{world} independent solves per step" if world > 1 else "1 GPU"},
-            "solves_per_s": solves_per_s, "rel_err_vs_fp64": rel_err,
+            "solves_per_s": solves_per_s, "rel_err_vs_fp64": rel_err, "max_rel_se_estimate": max_rel_se,
             "walk_steps_per_solve": steps_total / args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,

@@ -91,6 +91,9 @@ typedef struct {
     uint32_t request_id;    /* fourth Philox counter word: independent streams per request       */
     int32_t precision;      /* mcf_precision                                                     */
     int32_t deterministic;  /* reserved, must be 0                                               */
+    int32_t error_estimate; /* 1: also estimate the standard error (mcf_stats.max_rel_se) of a
+                               single-query RandFunmAction solve (mcf_action, mcf_action_nodes,
+                               mcf_total_communicability, mcf_katz); 0: off. Ignored elsewhere. */
     void* stream;           /* cudaStream_t                                                      */
 } mcf_params;
 
@@ -101,6 +104,13 @@ typedef struct {
     int64_t walk_steps;     /* transitions l_k -> l_{k+1} taken by all walks    */
     double kernel_ms;       /* device time of the walk kernel (CUDA events)     */
     uint32_t flags;         /* bit 0: float32 weight overflow seen              */
+    /* With params.error_estimate = 1 (RandFunmAction solves): the largest
+     * relative standard error max_j sqrt(V_j) / |y_j| over the entries with
+     * y_j != 0, where V_j = sum_i a'_ji^2 s_i^2 / N_i is the variance of
+     * y_j = ... + sum_i a'_ji q_i for independent walks (the estimator's
+     * variance, Section 3.5) and s_i^2 the sample variance of the N_i walk
+     * sums from column i (columns with N_i = 1 contribute 0); else 0. */
+    double max_rel_se;
 } mcf_stats;
 
 /* ------------------------------------------------------------------ graphs */

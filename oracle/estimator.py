@@ -48,11 +48,12 @@ def _lib_():
             lib.orc_action.argtypes = [i64, P, P, P, dbl, P, P, i32, i64, i64, dbl, u64, u32, i32, P, i64, P, P, P]
             lib.orc_diag.argtypes = [i64, P, P, P, dbl, P, i32, i64, i64, dbl, u64, u32, i32, P, i64, P, P]
             lib.orc_funm_full.argtypes = [i64, P, P, P, dbl, P, i32, i64, i64, dbl, u64, u32, i32, P]
+            lib.orc_action_se.argtypes = [i64, P, P, P, dbl, P, P, i32, i64, i64, dbl, u64, u32, i32, P, i64, P]
             lib.orc_mc_classic_action.argtypes = [i64, P, P, P, dbl, P, P, i32, i64, dbl, u64, u32, P, i64, P]
             lib.orc_allocation.argtypes = [i64, P, P, P, dbl, i64, i64, P, P, P, P]
             lib.orc_alias_row.argtypes = [i64, P, P, P]
             for f in ("orc_action", "orc_diag", "orc_funm_full", "orc_mc_classic_action", "orc_allocation",
-                      "orc_alias_row"):
+                      "orc_alias_row", "orc_action_se"):
                 getattr(lib, f).restype = i32
             _lib = lib
     return _lib
@@ -142,6 +143,21 @@ def diag(g, coeffs, gamma=1.0, n_walks=0, walks_per_node=0, w_cutoff=0.0, seed=0
                             seed, request_id, precision, _p(nd), 0 if nd is None else len(nd), _p(d), _p(stats)),
            "diag")
     return {"d": d[:m], "walks": int(stats[0]), "steps": int(stats[1])}
+
+
+def action_se(g, coeffs, v=None, gamma=1.0, n_walks=0, walks_per_node=0, w_cutoff=0.0, seed=0, request_id=0,
+              precision=0, nodes=None, values=None):
+    """Per-entry standard error of RandFunmAction from the sample variance of the walks (Section 3.5)."""
+    rp, ci, val = _csr(g, values)
+    n = g.n
+    vv = np.ones(n) if v is None else np.ascontiguousarray(v, dtype=np.float64)
+    z = np.ascontiguousarray(coeffs, dtype=np.float64)
+    nd = None if nodes is None else np.ascontiguousarray(nodes, dtype=np.int64)
+    se = np.zeros(n if nd is None else len(nd))
+    _check(_lib_().orc_action_se(n, _p(rp), _p(ci), _p(val), gamma, _p(vv), _p(z), len(z), n_walks, walks_per_node,
+                                 w_cutoff, seed, request_id, precision, _p(nd), 0 if nd is None else len(nd),
+                                 _p(se)), "action_se")
+    return se
 
 
 def funm_full(g, coeffs, gamma=1.0, n_walks=0, walks_per_node=0, w_cutoff=0.0, seed=0, request_id=0,

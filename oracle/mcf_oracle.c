@@ -356,6 +356,66 @@ int orc_action(int64_t n, const int64_t* rp, const int32_t* ci, const float* val
 }
 
 /* ------------------------------------------------------------------------ */
+/* Standard error of RandFunmAction (the estimator's variance, Section 3.5).  */
+/* q_i is the mean of N_i independent walk sums X_s from column i, so        */
+/* Var(y_j) = sum_i a'_ji^2 Var(X_i) / N_i.  Var(X_i) is estimated by the     */
+/* sample variance s_i^2 = (sum_s X_s^2 - N_i q_i^2) / (N_i - 1), clamped at  */
+/* 0, and taken as 0 when N_i < 2.  se[t] = sqrt(Var(y_j)) for j = nodes[t]   */
+/* (or t); the walks, ids and precision are those of orc_action.            */
+/* ------------------------------------------------------------------------ */
+int orc_action_se(int64_t n, const int64_t* rp, const int32_t* ci, const float* val, double gamma, const double* v,
+                  const double* zeta, int n_coeffs, int64_t n_walks, int64_t walks_per_node, double w_cutoff,
+                  uint64_t seed, uint32_t req, int precision, const int64_t* nodes, int64_t n_nodes, double* se) {
+    if (n_coeffs < 1 || !zeta || !v || !se || (precision != 0 && precision != 1)) return -1;
+    if (nodes) for (int64_t t = 0; t < n_nodes; ++t) if (nodes[t] < 0 || nodes[t] >= n) return -1;
+    int K = n_coeffs - 1;
+    chain_t c;
+    int rc = chain_build(&c, n, rp, ci, val, gamma, n_walks, walks_per_node);
+    if (rc) return rc;
+    double* r = (double*)malloc((size_t)(n + 1) * sizeof(double));
+    float* r32 = (float*)malloc((size_t)(n + 1) * sizeof(float));
+    double* w = (double*)calloc((size_t)(n + 1), sizeof(double));   /* s_i^2 / N_i */
+    unsigned char* mark = needed_starts(n, rp, ci, nodes, n_nodes);
+    if (!r || !r32 || !w || !mark) { free(r); free(r32); free(w); free(mark); chain_free(&c); return -2; }
+    for (int64_t i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int64_t p = rp[i]; p < rp[i + 1]; ++p) s += (val ? (double)val[p] : 1.0) * v[ci[p]];
+        r[i] = gamma * s;
+        r32[i] = (float)r[i];
+    }
+    if (K >= 2) {
+        for (int64_t i = 0; i < n; ++i) {
+            int64_t N = c.nw[i];
+            if (!mark[i] || N < 2) continue;
+            double sum = 0.0, sum2 = 0.0;
+            for (int64_t s = 0; s < N; ++s) {
+                action_ctx a = {r, precision == 1 ? r32 : NULL, 0.0};   /* one walk's sum X_s */
+                run_walk(&c, i, c.off[i] + s, zeta, K, w_cutoff, seed, req, precision, action_visit, &a);
+                sum += a.acc;
+                sum2 += a.acc * a.acc;
+            }
+            double mean = sum / (double)N;
+            double ss = sum2 - (double)N * mean * mean;
+            if (ss < 0.0) ss = 0.0;
+            w[i] = ss / ((double)(N - 1) * (double)N);
+        }
+    }
+    int64_t cnt = nodes ? n_nodes : n;
+    for (int64_t t = 0; t < cnt; ++t) {
+        int64_t j = nodes ? nodes[t] : t;
+        double var = 0.0;
+        for (int64_t p = rp[j]; p < rp[j + 1]; ++p) {
+            double a = gamma * (val ? (double)val[p] : 1.0);
+            var += a * a * w[ci[p]];
+        }
+        se[t] = sqrt(var);
+    }
+    free(r); free(r32); free(w); free(mark);
+    chain_free(&c);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* RandFunmDiag (Section 3.3, Eq. rand_funm_formula_diag):                   */
 /* d_i = zeta_0 + zeta_1 a'_ii + sum_k a'_ik <Q_k, C'_i>.                    */
 /* ------------------------------------------------------------------------ */

@@ -243,6 +243,7 @@ __global__ void __launch_bounds__(256, MINB) bwalk_tc_kernel(
     const BQuery* __restrict__ desc, int Q_tc, const float* __restrict__ rm_all, const int64_t* __restrict__ rmoff,
     const uint32_t* __restrict__ starts, const int64_t* __restrict__ soff, const uint32_t* __restrict__ chunk_s0,
     const int64_t* __restrict__ wbase, int grab, double* __restrict__ acc, unsigned long long* __restrict__ counters) {
+    double* const acc2 = nullptr;   // batches estimate no standard errors
     __shared__ WarpQuery wq[256 / 32];
     __shared__ WalkResults<float2> rbuf[256 / 32];
     const unsigned FULL = 0xffffffffu;
@@ -372,9 +373,9 @@ __global__ void __launch_bounds__(256, MINB) bwalk_tc_kernel(
                 active = false;
             }
         }
-        rb_n = rb.push(done, node0, make_float2(a32.hi, a32.lo), rb_n, lane, lt_mask, acc);
+        rb_n = rb.push(done, node0, make_float2(a32.hi, a32.lo), rb_n, lane, lt_mask, acc, acc2);
     }
-    rb.flush(rb_n, lane, acc);
+    rb.flush(rb_n, lane, acc, acc2);
     unsigned long long ws = my_steps, ww = my_walks;
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {

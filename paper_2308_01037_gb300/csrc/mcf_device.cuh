@@ -193,22 +193,71 @@ __device__ __forceinline__ void warp_merge_add(uint32_t nd, double v, bool valid
     if (head && key != 0xffffffffu) atomicAdd(&acc[key], v);
 }
 
+// warp_merge_add that also adds the squares of the walk values to acc2[node]
+// (the per-start second moments behind the standard-error estimate).
+static __device__ __noinline__ void warp_merge_add2(uint32_t nd, double v, bool valid, int lane, double* __restrict__ acc,
+                                             double* __restrict__ acc2) {
+    const unsigned FULL = 0xffffffffu;
+    uint32_t key = valid ? nd : 0xffffffffu;
+    double v2 = v * v;
+#pragma unroll
+    for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            const uint32_t ok = __shfl_xor_sync(FULL, key, stride);
+            const double ov = __shfl_xor_sync(FULL, v, stride);
+            const double ov2 = __shfl_xor_sync(FULL, v2, stride);
+            const bool up = ((lane & size) == 0);
+            const bool lower = (lane & stride) == 0;
+            const bool take_min = (lower == up);
+            const bool swap = take_min ? (ok < key) : (ok > key);
+            if (swap) {
+                key = ok;
+                v = ov;
+                v2 = ov2;
+            }
+        }
+    }
+    const uint32_t prev = __shfl_up_sync(FULL, key, 1);
+    const bool head = lane == 0 || prev != key;
+    const unsigned heads = __ballot_sync(FULL, head);
+    const int run = __popc(heads & ((2u << lane) - 1u));
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const double o = __shfl_down_sync(FULL, v, d);
+        const double o2 = __shfl_down_sync(FULL, v2, d);
+        const int orun = __shfl_down_sync(FULL, run, d);
+        if (lane + d < 32 && orun == run) {
+            v += o;
+            v2 += o2;
+        }
+    }
+    if (head && key != 0xffffffffu) {
+        atomicAdd(&acc[key], v);
+        atomicAdd(&acc2[key], v2);
+    }
+}
+
 template <class T>
 struct WalkResults {
     uint32_t node[64];
     T val[64];
-    __device__ __forceinline__ void flush(int n, int lane, double* __restrict__ acc) {
+    // acc2 (may be null, warp-uniform): also accumulate the squared values
+    __device__ __forceinline__ void flush(int n, int lane, double* __restrict__ acc, double* __restrict__ acc2) {
         __syncwarp();
         for (int r = 0; r < n; r += 32) {
             const int e = r + lane;
             const bool valid = e < n;
-            warp_merge_add(valid ? node[e] : 0u, valid ? walk_value(val[e]) : 0.0, valid, lane, acc);
+            const uint32_t nd = valid ? node[e] : 0u;
+            const double x = valid ? walk_value(val[e]) : 0.0;
+            if (acc2) warp_merge_add2(nd, x, valid, lane, acc, acc2);
+            else warp_merge_add(nd, x, valid, lane, acc);
         }
         __syncwarp();
     }
     // Appends the results of the lanes with done set; returns the new count.
     __device__ __forceinline__ int push(bool done, uint32_t nd, T v, int n, int lane, unsigned lt_mask,
-                                        double* __restrict__ acc) {
+                                        double* __restrict__ acc, double* __restrict__ acc2) {
         const unsigned dm = __ballot_sync(0xffffffffu, done);
         if (!dm) return n;
         if (done) {
@@ -218,7 +267,7 @@ struct WalkResults {
         }
         n += __popc(dm);
         if (n >= 32) {
-            flush(n, lane, acc);
+            flush(n, lane, acc, acc2);
             n = 0;
         }
         return n;

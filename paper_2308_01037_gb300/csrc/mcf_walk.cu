@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(256, MINB) walk_action_kernel(
     const int32_t* __restrict__ starts, const int64_t* __restrict__ soff, const int64_t* __restrict__ goff,
     const uint32_t* __restrict__ chunk_s0,
     const double* __restrict__ zeta_g, int K, double wc, float wc32, uint2 key, uint32_t req, int grab,
-    double* __restrict__ acc, unsigned long long* __restrict__ counters) {
+    double* __restrict__ acc, double* __restrict__ acc2, unsigned long long* __restrict__ counters) {
     using real = typename std::conditional<F64, double, float>::type;
     using rtype = typename std::conditional<F64, double, float2>::type;
     __shared__ real zeta[MCF_MAX_COEFFS];
@@ -267,10 +267,10 @@ __global__ void __launch_bounds__(256, MINB) walk_action_kernel(
                 active = false;
             }
         }
-        if constexpr (F64) rb_n = rb.push(done, node0, a64, rb_n, lane, lt_mask, acc);
-        else rb_n = rb.push(done, node0, make_float2(a32.hi, a32.lo), rb_n, lane, lt_mask, acc);
+        if constexpr (F64) rb_n = rb.push(done, node0, a64, rb_n, lane, lt_mask, acc, acc2);
+        else rb_n = rb.push(done, node0, make_float2(a32.hi, a32.lo), rb_n, lane, lt_mask, acc, acc2);
     }
-    rb.flush(rb_n, lane, acc);
+    rb.flush(rb_n, lane, acc, acc2);
     unsigned long long ws = my_steps, ww = my_walks;
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(256, MINB) walk_tc_kernel(
     const int32_t* __restrict__ starts, const int64_t* __restrict__ soff, const int64_t* __restrict__ goff,
     const uint32_t* __restrict__ chunk_s0,
     const double* __restrict__ zeta_g, int K, float wc32, uint2 key, uint32_t req, int grab,
-    double* __restrict__ acc, unsigned long long* __restrict__ counters) {
+    double* __restrict__ acc, double* __restrict__ acc2, unsigned long long* __restrict__ counters) {
     __shared__ float zeta[MCF_MAX_COEFFS];
     __shared__ WalkResults<float2> rbuf[256 / 32];
     for (int k = threadIdx.x; k <= K; k += blockDim.x) zeta[k] = (float)zeta_g[k];
@@ -439,9 +439,9 @@ __global__ void __launch_bounds__(256, MINB) walk_tc_kernel(
                 active = false;
             }
         }
-        rb_n = rb.push(done, node0, make_float2(a32.hi, a32.lo), rb_n, lane, lt_mask, acc);
+        rb_n = rb.push(done, node0, make_float2(a32.hi, a32.lo), rb_n, lane, lt_mask, acc, acc2);
     }
-    rb.flush(rb_n, lane, acc);
+    rb.flush(rb_n, lane, acc, acc2);
     unsigned long long ws = my_steps, ww = my_walks;
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
@@ -539,6 +539,7 @@ __global__ void __launch_bounds__(256, MINB) walk_tc_multi_kernel(
     const uint32_t* __restrict__ chunk_s0,
     const double* __restrict__ zeta_g, int K, float wc32, uint2 key, uint32_t req, int grab,
     double* __restrict__ acc, unsigned long long* __restrict__ counters) {
+    double* const acc2 = nullptr;   // no second moments in this variant
     __shared__ float zeta[MCF_MAX_COEFFS];
     __shared__ WalkResults<float2> rbuf[256 / 32];
     for (int k = threadIdx.x; k <= K; k += blockDim.x) zeta[k] = (float)zeta_g[k];
@@ -596,10 +597,10 @@ __global__ void __launch_bounds__(256, MINB) walk_tc_multi_kernel(
                     L[s].active = false;
                 }
             }
-            rb_n = rb.push(done, L[s].node0, make_float2(L[s].a.hi, L[s].a.lo), rb_n, lane, lt_mask, acc);
+            rb_n = rb.push(done, L[s].node0, make_float2(L[s].a.hi, L[s].a.lo), rb_n, lane, lt_mask, acc, acc2);
         }
     }
-    rb.flush(rb_n, lane, acc);
+    rb.flush(rb_n, lane, acc, acc2);
     unsigned long long ws = my_steps, ww = my_walks;
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) {
@@ -668,6 +669,49 @@ __global__ void action_epilogue_nodes(int64_t m, const int64_t* __restrict__ nod
             y[t] = z0 * (v ? v[i] : 1.0) + z1 * r[i] + gamma * s;
         }
     }
+}
+
+// Standard error of RandFunmAction (the estimator's variance, Section 3.5):
+// y_j = ... + sum_i a'_ji q_i with q_i the mean of N_i independent walk sums,
+// so Var(y_j) = sum_i a'_ji^2 Var(X_i) / N_i.  w_i = s_i^2 / N_i from the
+// sample variance of column i's walk sums (q_i after finalize_q, sum of
+// squares acc2_i); 0 when N_i < 2.
+__global__ void se_node_var(int64_t n, const double* __restrict__ q, const double* __restrict__ acc2,
+                            const int64_t* __restrict__ nw, double* __restrict__ w) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t N = nw[i];
+        double x = 0.0;
+        if (N >= 2) {
+            const double ss = acc2[i] - (double)N * q[i] * q[i];
+            x = fmax(ss, 0.0) / ((double)(N - 1) * (double)N);
+        }
+        w[i] = x;
+    }
+}
+
+// max over the rows j = rows[t] (or t) of sqrt(sum_p (gamma a_jp)^2 w_{col p}) / |y_t|
+// (warp per row), as the bits of a non-negative double, which order like the values.
+__global__ void se_rows(int64_t m, const int64_t* __restrict__ rows, const int64_t* __restrict__ rp,
+                        const int32_t* __restrict__ col, const float* __restrict__ val, double gamma,
+                        const double* __restrict__ w, const double* __restrict__ y,
+                        unsigned long long* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    double best = 0.0;
+    for (int64_t t = warp; t < m; t += nwarps) {
+        const int64_t j = rows ? rows[t] : t;
+        double s = 0.0;
+        for (int64_t p = rp[j] + lane; p < rp[j + 1]; p += 32) {
+            const double a = val ? (double)val[p] : 1.0;
+            s += a * a * w[col[p]];
+        }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+        const double yt = fabs(y[t]);
+        if (yt > 0.0) best = fmax(best, gamma * sqrt(s) / yt);
+    }
+    if (lane == 0 && best > 0.0) atomicMax(out, (unsigned long long)__double_as_longlong(best));
 }
 
 // ====================================================================== RandFunmDiag walks
@@ -836,6 +880,7 @@ static mcf_status check_params(const mcf_graph* g, const mcf_params* p) {
     if (p->precision != MCF_F64 && p->precision != MCF_F32W_F64ACC)
         return fail(MCF_ERR_INVALID_ARG, "unknown precision");
     if (p->deterministic != 0) return fail(MCF_ERR_INVALID_ARG, "deterministic is reserved and must be 0");
+    if (p->error_estimate != 0 && p->error_estimate != 1) return fail(MCF_ERR_INVALID_ARG, "error_estimate is 0 or 1");
     if (!(p->scale >= 0.0) || !isfinite(p->scale)) return fail(MCF_ERR_INVALID_ARG, "scale must be finite and >= 0");
     for (int k = 0; k < p->n_coeffs; ++k)
         if (!isfinite(p->coeffs[k])) return fail(MCF_ERR_INVALID_ARG, "coefficients must be finite");
@@ -929,6 +974,7 @@ static mcf_status finish_stats(mcf_stats* stats, const unsigned long long* count
     stats->walks = (int64_t)h[C_WALKS];
     stats->walk_steps = (int64_t)h[C_STEPS];
     stats->flags = (uint32_t)h[C_FLAGS];
+    stats->max_rel_se = 0.0;
     float ms = 0.f;
     if (e0 && e1) cudaEventElapsedTime(&ms, e0, e1);
     stats->kernel_ms = ms;
@@ -937,12 +983,12 @@ static mcf_status finish_stats(mcf_stats* stats, const unsigned long long* count
 
 template <bool F64, bool WEIGHTED, int MINB>
 static void launch_action_walks_t(const mcf_graph* g, const Prep& P, uint32_t* chunk_s0, int K, double wc, uint2 key,
-                                  uint32_t req, double* acc, cudaStream_t st) {
+                                  uint32_t req, double* acc, double* acc2, cudaStream_t st) {
     auto kern = walk_action_kernel<F64, WEIGHTED, MINB>;
     const int grid = persistent_grid(kern, 256, 0);
     ScopedL2Fetch fetch(walk_tuning().l2_fetch);
     kern<<<grid, 256, 0, st>>>((const Rec<F64>*)P.rec, g->col_idx, g->went, P.starts, P.cof, P.soff, chunk_s0, P.zeta,
-                               K, wc, cutoff_f32(wc), key, req, walk_tuning().grab, acc, P.counters);
+                               K, wc, cutoff_f32(wc), key, req, walk_tuning().grab, acc, acc2, P.counters);
 }
 
 // Builds the graph's node_od / edge_od arrays on first use (binary, nnz < 2^32).
@@ -1008,8 +1054,8 @@ mcf_status ensure_edge_rec(mcf_graph* g, cudaStream_t st) {
 
 template <int MINB>
 static void launch_tc_walks_t(const mcf_graph* g, const Prep& P, const float* rm, uint32_t* chunk_s0, int K,
-                              double wc, uint2 key, uint32_t req, double* acc, cudaStream_t st) {
-    if (walk_tuning().walks_per_thread == 2) {
+                              double wc, uint2 key, uint32_t req, double* acc, double* acc2, cudaStream_t st) {
+    if (walk_tuning().walks_per_thread == 2 && !acc2) {
         auto kern = walk_tc_multi_kernel<(MINB > 4 ? 4 : MINB), 2>;
         const int grid = persistent_grid(kern, 256, 0);
         ScopedL2Fetch fetch(walk_tuning().l2_fetch);
@@ -1023,15 +1069,16 @@ static void launch_tc_walks_t(const mcf_graph* g, const Prep& P, const float* rm
     const int grid = persistent_grid(kern, 256, 0);
     ScopedL2Fetch fetch(walk_tuning().l2_fetch);
     kern<<<grid, 256, 0, st>>>(g->node_od, g->edge_od, g->col_idx, rm, P.starts, P.cof, P.soff, chunk_s0, P.zeta, K,
-                               cutoff_f32(wc), key, req, walk_tuning().grab, acc, P.counters);
+                               cutoff_f32(wc), key, req, walk_tuning().grab, acc, acc2, P.counters);
 }
 
 template <bool F64, bool WEIGHTED>
 static void launch_action_walks(const mcf_graph* g, const Prep& P, uint32_t* chunk_s0, int K, double wc, uint2 key,
-                                uint32_t req, double* acc, cudaStream_t st) {
-    if (walk_tuning().minb == 8) launch_action_walks_t<F64, WEIGHTED, 8>(g, P, chunk_s0, K, wc, key, req, acc, st);
-    else if (walk_tuning().minb == 5) launch_action_walks_t<F64, WEIGHTED, 5>(g, P, chunk_s0, K, wc, key, req, acc, st);
-    else launch_action_walks_t<F64, WEIGHTED, 6>(g, P, chunk_s0, K, wc, key, req, acc, st);
+                                uint32_t req, double* acc, double* acc2, cudaStream_t st) {
+    if (walk_tuning().minb == 8) launch_action_walks_t<F64, WEIGHTED, 8>(g, P, chunk_s0, K, wc, key, req, acc, acc2, st);
+    else if (walk_tuning().minb == 5)
+        launch_action_walks_t<F64, WEIGHTED, 5>(g, P, chunk_s0, K, wc, key, req, acc, acc2, st);
+    else launch_action_walks_t<F64, WEIGHTED, 6>(g, P, chunk_s0, K, wc, key, req, acc, acc2, st);
 }
 
 static mcf_status solve_action(mcf_graph* g, const mcf_params* p, const double* v, double* y, mcf_stats* stats,
@@ -1106,6 +1153,13 @@ static mcf_status solve_action(mcf_graph* g, const mcf_params* p, const double* 
     }
     double* acc;
     MCF_TRY(sc.get(&acc, n));
+    // per-start sums of squared walk values, for the standard error
+    const bool want_se = stats && p->error_estimate;
+    double* acc2 = nullptr;
+    if (want_se && n > 0) {
+        MCF_TRY(sc.get(&acc2, n));
+        MCF_CUDA_TRY(cudaMemsetAsync(acc2, 0, n * sizeof(double), st));
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (n > 0) {
         MCF_CUDA_TRY(cudaMemsetAsync(acc, 0, n * sizeof(double), st));
@@ -1129,13 +1183,20 @@ static mcf_status solve_action(mcf_graph* g, const mcf_params* p, const double* 
                 float* rm;
                 MCF_TRY(sc.get(&rm, g->max_degree + 1));
                 degree_table<<<grid_for(g->max_degree + 1, 256), 256, 0, st>>>(g->max_degree, gamma, rm);
-                if (walk_tuning().minb == 8) launch_tc_walks_t<8>(g, P, rm, chunk_s0, K, p->w_cutoff, key, p->request_id, acc, st);
-                else if (walk_tuning().minb == 5) launch_tc_walks_t<5>(g, P, rm, chunk_s0, K, p->w_cutoff, key, p->request_id, acc, st);
-                else launch_tc_walks_t<6>(g, P, rm, chunk_s0, K, p->w_cutoff, key, p->request_id, acc, st);
-            } else if (f64 && g->weighted) launch_action_walks<true, true>(g, P, chunk_s0, K, p->w_cutoff, key, p->request_id, acc, st);
-            else if (f64) launch_action_walks<true, false>(g, P, chunk_s0, K, p->w_cutoff, key, p->request_id, acc, st);
-            else if (g->weighted) launch_action_walks<false, true>(g, P, chunk_s0, K, p->w_cutoff, key, p->request_id, acc, st);
-            else launch_action_walks<false, false>(g, P, chunk_s0, K, p->w_cutoff, key, p->request_id, acc, st);
+                const uint32_t rq = p->request_id;
+                const double wc = p->w_cutoff;
+                if (walk_tuning().minb == 8) launch_tc_walks_t<8>(g, P, rm, chunk_s0, K, wc, key, rq, acc, acc2, st);
+                else if (walk_tuning().minb == 5) launch_tc_walks_t<5>(g, P, rm, chunk_s0, K, wc, key, rq, acc, acc2, st);
+                else launch_tc_walks_t<6>(g, P, rm, chunk_s0, K, wc, key, rq, acc, acc2, st);
+            } else if (f64 && g->weighted) {
+                launch_action_walks<true, true>(g, P, chunk_s0, K, p->w_cutoff, key, p->request_id, acc, acc2, st);
+            } else if (f64) {
+                launch_action_walks<true, false>(g, P, chunk_s0, K, p->w_cutoff, key, p->request_id, acc, acc2, st);
+            } else if (g->weighted) {
+                launch_action_walks<false, true>(g, P, chunk_s0, K, p->w_cutoff, key, p->request_id, acc, acc2, st);
+            } else {
+                launch_action_walks<false, false>(g, P, chunk_s0, K, p->w_cutoff, key, p->request_id, acc, acc2, st);
+            }
             if (stats) cudaEventRecord(e1, st);
         }
         finalize_q<<<grid_for(n, 256), 256, 0, st>>>(n, acc, P.nw);
@@ -1148,11 +1209,29 @@ static mcf_status solve_action(mcf_graph* g, const mcf_params* p, const double* 
                                                               v_dev, P.r, acc, y_dev);
         MCF_CUDA_TRY(cudaGetLastError());
     }
+    unsigned long long* se_max = nullptr;
+    if (want_se && n > 0) {
+        double* w;
+        MCF_TRY(sc.get(&w, n));
+        MCF_TRY(sc.get(&se_max, 1));
+        MCF_CUDA_TRY(cudaMemsetAsync(se_max, 0, sizeof(unsigned long long), st));
+        se_node_var<<<grid_for(n, 256), 256, 0, st>>>(n, acc, acc2, P.nw, w);
+        se_rows<<<grid_for(m * 32, 256), 256, 0, st>>>(m, nodes_dev, g->row_ptr, g->col_idx, g->values, gamma, w, y_dev,
+                                                        se_max);
+        MCF_CUDA_TRY(cudaGetLastError());
+    }
     if (!y_on_dev && m > 0) MCF_CUDA_TRY(cudaMemcpyAsync(y, y_dev, m * sizeof(double), cudaMemcpyDeviceToHost, st));
+    unsigned long long se_bits = 0;
+    if (se_max) MCF_CUDA_TRY(cudaMemcpyAsync(&se_bits, se_max, sizeof(se_bits), cudaMemcpyDeviceToHost, st));
     mcf_status rc = finish_stats(stats, P.counters, e0, e1, st);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (rc != MCF_OK) return rc;
+    if (stats && se_max) {
+        double v_se;
+        memcpy(&v_se, &se_bits, sizeof(v_se));
+        stats->max_rel_se = v_se;
+    }
     if (!y_on_dev) MCF_CUDA_TRY(cudaStreamSynchronize(st));
     return MCF_OK;
 }
@@ -1865,8 +1944,8 @@ static mcf_status solve_tc_noalloc(int64_t n, int64_t nnz, const int64_t* row_pt
         view.row_ptr = const_cast<int64_t*>(row_ptr);
         view.col_idx = const_cast<int32_t*>(col_idx);
         const uint2 key = philox_key(p->seed);
-        if (f64) launch_action_walks<true, false>(&view, P, chunk_s0, K, p->w_cutoff, key, p->request_id, acc, st);
-        else launch_action_walks<false, false>(&view, P, chunk_s0, K, p->w_cutoff, key, p->request_id, acc, st);
+        if (f64) launch_action_walks<true, false>(&view, P, chunk_s0, K, p->w_cutoff, key, p->request_id, acc, nullptr, st);
+        else launch_action_walks<false, false>(&view, P, chunk_s0, K, p->w_cutoff, key, p->request_id, acc, nullptr, st);
     }
     finalize_q<<<grid_for(n, 256), 256, 0, st>>>(n, acc, P.nw);
     const double z0 = p->coeffs[0], z1 = K >= 1 ? p->coeffs[1] : 0.0;

@@ -41,7 +41,7 @@ class mcf_params(ctypes.Structure):
     _fields_ = [("coeffs", ctypes.c_void_p), ("n_coeffs", ctypes.c_int32), ("scale", ctypes.c_double),
                 ("n_walks", ctypes.c_int64), ("walks_per_node", ctypes.c_int64), ("w_cutoff", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("request_id", ctypes.c_uint32), ("precision", ctypes.c_int32),
-                ("deterministic", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+                ("deterministic", ctypes.c_int32), ("error_estimate", ctypes.c_int32), ("stream", ctypes.c_void_p)]
 
 
 class mcf_query(ctypes.Structure):
@@ -75,10 +75,11 @@ class mcf_server_stats(ctypes.Structure):
 
 class mcf_stats(ctypes.Structure):
     _fields_ = [("walks", ctypes.c_int64), ("walk_steps", ctypes.c_int64), ("kernel_ms", ctypes.c_double),
-                ("flags", ctypes.c_uint32)]
+                ("flags", ctypes.c_uint32), ("max_rel_se", ctypes.c_double)]
 
     def as_dict(self):
-        return {"walks": self.walks, "walk_steps": self.walk_steps, "kernel_ms": self.kernel_ms, "flags": self.flags}
+        return {"walks": self.walks, "walk_steps": self.walk_steps, "kernel_ms": self.kernel_ms, "flags": self.flags,
+                "max_rel_se": self.max_rel_se}
 
 
 # Every entry point declared in include/mcf.h, with its ctypes signature.
@@ -171,11 +172,11 @@ def _stream_of(*arrays):
 
 
 def _params(coeffs, scale=0.0, n_walks=0, walks_per_node=0, w_cutoff=0.0, seed=0, request_id=0,
-            precision=MCF_F32W_F64ACC, stream=None):
+            precision=MCF_F32W_F64ACC, stream=None, error_estimate=False):
     c = np.ascontiguousarray(coeffs, dtype=np.float64)
     p = mcf_params(c.ctypes.data, len(c), float(scale), int(n_walks), int(walks_per_node), float(w_cutoff),
                    int(seed) & 0xFFFFFFFFFFFFFFFF, int(request_id) & 0xFFFFFFFF, int(precision), 0,
-                   stream if stream else None)
+                   1 if error_estimate else 0, stream if stream else None)
     return p, c
 
 

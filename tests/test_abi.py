@@ -55,11 +55,30 @@ def test_null_arguments_rejected_without_device(lib):
     assert lib.mcf_gershgorin(None, ctypes.byref(out)) == 1
 
 
-def test_params_struct_layout_matches_c():
-    # offsets of the C struct on LP64: pointer 0, int32 8, double 16, int64 24, int64 32,
-    # double 40, uint64 48, uint32 56, int32 60, int32 64, pointer 72
-    offs = {f[0]: getattr(M.mcf_params, f[0]).offset for f in M.mcf_params._fields_}
-    assert offs == {"coeffs": 0, "n_coeffs": 8, "scale": 16, "n_walks": 24, "walks_per_node": 32, "w_cutoff": 40,
-                    "seed": 48, "request_id": 56, "precision": 60, "deterministic": 64, "stream": 72}
-    assert ctypes.sizeof(M.mcf_params) == 80
-    assert ctypes.sizeof(M.mcf_stats) == 32
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every ctypes struct of the binding has the field offsets and size the
+    C compiler gives the header's struct (a small C program prints them)."""
+    import subprocess
+
+    structs = {"mcf_params": M.mcf_params, "mcf_stats": M.mcf_stats, "mcf_query": M.mcf_query,
+               "mcf_server_config": M.mcf_server_config, "mcf_server_stats": M.mcf_server_stats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "mcf.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for f in cls._fields_:
+            lines.append(f'printf("{name} {f[0]} %zu\\n", offsetof({name}, {f[0]}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.check_call(["gcc", "-std=c11", "-I", inc, str(src), "-o", str(exe)])
+    got = {}
+    for line in subprocess.check_output([str(exe)], text=True).splitlines():
+        name, field, val = line.split()
+        got[(name, field)] = int(val)
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for f in cls._fields_:
+            assert got[(name, f[0])] == getattr(cls, f[0]).offset, (name, f[0])
+

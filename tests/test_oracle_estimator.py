@@ -307,3 +307,34 @@ def test_randfunm_action_beats_classical_mc_single_entry():
         ymc = E.mc_classic_action(g, c, [i], walks_per_row=per * len(nbrs), gamma=gam, seed=s)[0]
         err_mc.append(abs(ymc - exact[i]))
     assert np.mean(err_rf) < 0.5 * np.mean(err_mc)
+
+
+# ------------------------------------------------------------ standard error (Section 3.5)
+@pytest.mark.parametrize("precision", [0, 1])
+def test_standard_error_matches_enumerated_variance(ba12, precision):
+    """Var(y_j) = sum_i a'_ji^2 Var(X_i) / N_i for independent walks; the
+    sample-variance estimate from 2e4 walks per node must match the exact
+    variance from the enumeration to a few percent (its own sampling error
+    is about sqrt(2 / N) = 1 %)."""
+    g = ba12
+    gam = 1 / R.lambda_max(g)
+    c = R.exp_coeffs(7)
+    v = np.random.default_rng(5).uniform(0.5, 1.5, g.n)
+    wpn = 20000
+    ex = R.enumerate_action(g, c, gamma=gam, v=v)
+    var = R.action_variance(ex, np.full(g.n, wpn))
+    se = E.action_se(g, c, v=v, gamma=gam, walks_per_node=wpn, seed=3, precision=precision)
+    assert np.max(np.abs(se ** 2 / var - 1)) < 0.04
+    sub = E.action_se(g, c, v=v, gamma=gam, walks_per_node=wpn, seed=3, precision=precision, nodes=[3, 0, 3])
+    assert np.array_equal(sub, se[[3, 0, 3]])
+
+
+def test_standard_error_vanishes_without_variance():
+    """On K_n every walk of total communicability has the same sum: the
+    estimate is exact and its standard error is zero up to the rounding of
+    the sum-of-squares formula."""
+    g = I.complete(7)
+    c = R.exp_coeffs(10)
+    y = E.action(g, c, gamma=0.2, walks_per_node=50, seed=1)["y"]
+    se = E.action_se(g, c, gamma=0.2, walks_per_node=50, seed=1)
+    assert np.all(se <= 1e-7 * y)
