@@ -182,6 +182,90 @@ def cpu_baseline(g, lam, w, seconds=15.0):
                       f"seed as the full run), {total_steps} walk-steps in {total_t:.1f} s"}
 
 
+# ---------------------------------------------------------------- the oracle on every host core
+# Worker processes are started with spawn (never forked from a process that
+# has used the GPU) and map the parent's CSR from shared memory; each task is
+# the unchanged oracle on one node sample.
+_ORC = {}
+
+
+def _oracle_worker_init(shm_names, n, nnz, w):
+    from multiprocessing import shared_memory
+
+    from paper_2308_01037_gb300 import inputs as I
+
+    rp_shm = shared_memory.SharedMemory(name=shm_names[0])
+    ci_shm = shared_memory.SharedMemory(name=shm_names[1])
+    rp = np.ndarray((n + 1,), dtype=np.int64, buffer=rp_shm.buf)
+    ci = np.ndarray((max(nnz, 1),), dtype=np.int32, buffer=ci_shm.buf)[:nnz]
+    _ORC.update(g=I.Graph(n, rp, ci, "shared"), w=w, shm=(rp_shm, ci_shm))
+
+
+def _oracle_worker_task(args):
+    from oracle import estimator as E
+
+    nodes, lam = args
+    g, w = _ORC["g"], _ORC["w"]
+    out = (E.action if w["query"] == "tc" else E.diag)(
+        g, exp_coeffs(w["K"]), gamma=1.0 / lam, n_walks=w["n_walks"], walks_per_node=w["walks_per_node"],
+        w_cutoff=w["w_cutoff"], seed=1, nodes=nodes, precision=1)
+    return int(out["steps"])
+
+
+class OraclePool:
+    """The oracle run by one spawn-started process per host core."""
+
+    def __init__(self, g, w, procs=None):
+        import multiprocessing as mp
+        from multiprocessing import shared_memory
+
+        self.procs = procs or max(1, len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity")
+                                   else os.cpu_count() or 1)
+        self.n = g.n
+        self.shm = [shared_memory.SharedMemory(create=True, size=max(8, g.row_ptr.nbytes)),
+                    shared_memory.SharedMemory(create=True, size=max(8, g.col_idx.nbytes))]
+        np.ndarray(g.row_ptr.shape, dtype=np.int64, buffer=self.shm[0].buf)[:] = g.row_ptr
+        np.ndarray(g.col_idx.shape, dtype=np.int32, buffer=self.shm[1].buf)[:] = g.col_idx
+        ctx = mp.get_context("spawn")
+        self.pool = ctx.Pool(self.procs, initializer=_oracle_worker_init,
+                             initargs=([m.name for m in self.shm], g.n, int(g.col_idx.size), w))
+
+    def run(self, lam, seconds, seed=123):
+        rng = np.random.default_rng(seed)
+        n_nodes, total_steps, total_t, entries = 8, 0, 0.0, 0
+        while total_t < seconds and n_nodes <= 1 << 14:
+            tasks = [(rng.choice(self.n, size=min(n_nodes, self.n), replace=False), lam) for _ in range(self.procs)]
+            t = time.perf_counter()
+            total_steps += sum(self.pool.map(_oracle_worker_task, tasks))
+            total_t += time.perf_counter() - t
+            entries += sum(len(x[0]) for x in tasks)
+            n_nodes *= 2
+        return {"value": total_steps / total_t, "unit": "walk-steps/s", "cores": self.procs, "kind": "oracle",
+                "sample": f"entries of {entries} random nodes on {self.procs} processes (walks from their neighbours, "
+                          f"same allocation and seed as the full run), {total_steps} walk-steps in {total_t:.1f} s"}
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+        for m in self.shm:
+            m.close()
+            m.unlink()
+
+
+def cpu_baseline_all_cores(g, lam, w, seconds=15.0):
+    """cpu_baseline on every host core, with the single-core rate beside it."""
+    one = cpu_baseline(g, lam, w, seconds=seconds / 3)
+    pool = OraclePool(g, w)
+    try:
+        pool.run(lam, 0.5)            # start-up of the workers
+        res = pool.run(lam, seconds)
+    finally:
+        pool.close()
+    res["single_core_value"] = one["value"]
+    res["single_core_sample"] = one["sample"]
+    return res
+
+
 def aggregate(ms, steps, device="cpu"):
     """Whole-job numbers over the ranks of the default process group: the
     slowest rank's time (ms) and the walk-steps of all ranks."""
@@ -495,22 +579,26 @@ def run_reference(args, w):
     g = make_graph(w)
     lam = R.lambda_max(g)
     per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
-    for _ in range(args.warmup):
-        cpu_baseline(g, lam, w, seconds=per_step / 4)
-    vals = []
-    t0 = time.perf_counter()
-    last = None
-    for _ in range(args.steps):
-        last = cpu_baseline(g, lam, w, seconds=per_step)
-        vals.append(last["value"])
-    el = time.perf_counter() - t0
+    pool = OraclePool(g, w)
+    try:
+        for i in range(args.warmup):
+            pool.run(lam, per_step / 4, seed=1000 + i)
+        vals = []
+        t0 = time.perf_counter()
+        last = None
+        for i in range(args.steps):
+            last = pool.run(lam, per_step, seed=2000 + i)
+            vals.append(last["value"])
+        el = time.perf_counter() - t0
+    finally:
+        pool.close()
     v = float(np.mean(vals))
     line = {"impl": "reference", "metric": "walk-steps/s", "value": v, "unit": "walk-steps/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000 * el / max(1, args.steps), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 walk weights, f64 accumulation", "data": "synthetic",
             "config": {"workload": w["label"]},
-            "cpu_baseline": {"value": v, "unit": "walk-steps/s", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": "walk-steps/s", "cores": pool.procs, "kind": "oracle",
                              "sample": last["sample"] if last else ""},
             "e2e": {"value": v, "unit": "walk-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -682,7 +770,7 @@ def main():
         mc_classic = run_mc_classic(M, R, I)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(g, lam, w)
+        cpu = cpu_baseline_all_cores(g, lam, w)
     if rank == 0:
         line = {
             "metric": "walk-steps/s", "value": value, "unit": "walk-steps/s", "n_gpus": world,

@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
 
 #include "../../include/mcf.h"
@@ -229,18 +230,41 @@ inline uint2 philox_key(uint64_t seed) { return make_uint2((uint32_t)seed, (uint
 // fetch granularity lowered to 32 bytes (a per-context launch limit), and the
 // previous value is put back right after the launch.
 struct ScopedL2Fetch {
-    size_t old = 0;
-    bool set = false;
+    // The limit belongs to the whole context: concurrent solves (server
+    // workers, user threads) share one setting, taken by the first entrant
+    // and restored by the last one to leave.
+    bool active = false;
     explicit ScopedL2Fetch(int bytes) {
         if (bytes <= 0) return;
-        if (cudaDeviceGetLimit(&old, cudaLimitMaxL2FetchGranularity) == cudaSuccess &&
-            cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, (size_t)bytes) == cudaSuccess)
-            set = true;
-        cudaGetLastError();
+        std::lock_guard<std::mutex> lk(state().mu);
+        State& s = state();
+        if (s.users++ == 0) {
+            s.saved = cudaDeviceGetLimit(&s.old, cudaLimitMaxL2FetchGranularity) == cudaSuccess &&
+                      cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, (size_t)bytes) == cudaSuccess;
+            cudaGetLastError();
+        }
+        active = true;
     }
     ~ScopedL2Fetch() {
-        if (set) cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, old);
-        cudaGetLastError();
+        if (!active) return;
+        std::lock_guard<std::mutex> lk(state().mu);
+        State& s = state();
+        if (--s.users == 0 && s.saved) {
+            cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, s.old);
+            cudaGetLastError();
+        }
+    }
+
+  private:
+    struct State {
+        std::mutex mu;
+        int users = 0;
+        size_t old = 0;
+        bool saved = false;
+    };
+    static State& state() {
+        static State s;
+        return s;
     }
 };
 
