@@ -578,7 +578,7 @@ def run_reference(args, w):
 
     g = make_graph(w)
     lam = R.lambda_max(g)
-    per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    per_step = max(min(2.0, args.ref_seconds), args.ref_seconds / max(1, args.steps + args.warmup))
     pool = OraclePool(g, w)
     try:
         for i in range(args.warmup):
@@ -622,6 +622,8 @@ def main():
     ap.add_argument("--section", default="main", choices=["main", "funm_full", "mc_classic", "batched", "serving"],
                     help="run only that measurement (1 GPU) and print its JSON")
     ap.add_argument("--funm-n", type=int, default=16384, help="nodes of the dense RandFunm measurement")
+    ap.add_argument("--ref-seconds", type=float, default=60.0,
+                    help="--impl reference: oracle time budget of the whole run, split over the steps")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":

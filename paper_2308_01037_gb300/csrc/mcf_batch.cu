@@ -740,7 +740,8 @@ static mcf_status autotune(mcf_batch* b, cudaStream_t st) {
         }
     }
     const BatchTuning cands[] = {{4, 1}, {4, 4}, {5, 1}, {5, 4}, {6, 4}, {8, 4}};
-    cudaEvent_t e0, e1;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    EventGuard event_guard{&e0, &e1};
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
@@ -760,8 +761,6 @@ static mcf_status autotune(mcf_batch* b, cudaStream_t st) {
             pick = c;
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     b->tune = pick;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune_cache[key] = pick;
@@ -1038,6 +1037,7 @@ mcf_status mcf_batch_run(mcf_batch_t b, void* stream, mcf_stats* stats) {
     if (!b) return fail(MCF_ERR_INVALID_ARG, "batch is NULL");
     cudaStream_t st = (cudaStream_t)stream;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
+    EventGuard event_guard{&e0, &e1};
     if (stats) {
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
@@ -1066,8 +1066,6 @@ mcf_status mcf_batch_run(mcf_batch_t b, void* stream, mcf_stats* stats) {
     if (stats) {
         MCF_CUDA_TRY(cudaEventSynchronize(e1));
         cudaEventElapsedTime(&ms, e0, e1);
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
     }
     for (int i : b->single) {
         const mcf_query& q = b->queries[i];

@@ -229,6 +229,16 @@ inline uint2 philox_key(uint64_t seed) { return make_uint2((uint32_t)seed, (uint
 // bytes the step uses.  The walk kernels are launched with the context's L2
 // fetch granularity lowered to 32 bytes (a per-context launch limit), and the
 // previous value is put back right after the launch.
+// Destroys the events it watches when the scope ends (also on early returns).
+struct EventGuard {
+    cudaEvent_t* a;
+    cudaEvent_t* b;
+    ~EventGuard() {
+        if (a && *a) cudaEventDestroy(*a);
+        if (b && *b) cudaEventDestroy(*b);
+    }
+};
+
 struct ScopedL2Fetch {
     // The limit belongs to the whole context: concurrent solves (server
     // workers, user threads) share one setting, taken by the first entrant

@@ -1161,6 +1161,7 @@ static mcf_status solve_action(mcf_graph* g, const mcf_params* p, const double* 
         MCF_CUDA_TRY(cudaMemsetAsync(acc2, 0, n * sizeof(double), st));
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
+    EventGuard event_guard{&e0, &e1};
     if (n > 0) {
         MCF_CUDA_TRY(cudaMemsetAsync(acc, 0, n * sizeof(double), st));
         if (K >= 2) {
@@ -1224,8 +1225,6 @@ static mcf_status solve_action(mcf_graph* g, const mcf_params* p, const double* 
     unsigned long long se_bits = 0;
     if (se_max) MCF_CUDA_TRY(cudaMemcpyAsync(&se_bits, se_max, sizeof(se_bits), cudaMemcpyDeviceToHost, st));
     mcf_status rc = finish_stats(stats, P.counters, e0, e1, st);
-    if (e0) cudaEventDestroy(e0);
-    if (e1) cudaEventDestroy(e1);
     if (rc != MCF_OK) return rc;
     if (stats && se_max) {
         double v_se;
@@ -1333,6 +1332,7 @@ static mcf_status solve_diag(mcf_graph* g, const mcf_params* p, const int64_t* n
     double* dacc;
     MCF_TRY(sc.get(&dacc, n));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
+    EventGuard event_guard{&e0, &e1};
     if (n > 0) {
         MCF_CUDA_TRY(cudaMemsetAsync(dacc, 0, n * sizeof(double), st));
         if (K >= 2) {
@@ -1368,8 +1368,6 @@ static mcf_status solve_diag(mcf_graph* g, const mcf_params* p, const int64_t* n
     }
     if (!d_on_dev && m > 0) MCF_CUDA_TRY(cudaMemcpyAsync(d, d_dev, m * sizeof(double), cudaMemcpyDeviceToHost, st));
     mcf_status rc = finish_stats(stats, P.counters, e0, e1, st);
-    if (e0) cudaEventDestroy(e0);
-    if (e1) cudaEventDestroy(e1);
     if (rc != MCF_OK) return rc;
     if (!d_on_dev) MCF_CUDA_TRY(cudaStreamSynchronize(st));
     return MCF_OK;
@@ -1563,6 +1561,7 @@ static mcf_status solve_full(mcf_graph* g, const mcf_params* p, double* F, mcf_s
     double* Q;
     MCF_TRY(sc.get(&Q, (size_t)std::max<int64_t>(n * n, 1)));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
+    EventGuard event_guard{&e0, &e1};
     if (n > 0) {
         if (K >= 2) {
             MCF_CUDA_TRY(cudaMemsetAsync(Q, 0, (size_t)(n * n) * sizeof(double), st));
@@ -1610,8 +1609,6 @@ static mcf_status solve_full(mcf_graph* g, const mcf_params* p, double* F, mcf_s
     if (!f_on_dev && n > 0)
         MCF_CUDA_TRY(cudaMemcpyAsync(F, F_dev, (size_t)(n * n) * sizeof(double), cudaMemcpyDeviceToHost, st));
     mcf_status rc = finish_stats(stats, P.counters, e0, e1, st);
-    if (e0) cudaEventDestroy(e0);
-    if (e1) cudaEventDestroy(e1);
     if (rc != MCF_OK) return rc;
     if (!f_on_dev) MCF_CUDA_TRY(cudaStreamSynchronize(st));
     return MCF_OK;
@@ -1743,6 +1740,7 @@ static mcf_status solve_mc_classic(mcf_graph* g, const mcf_params* p, const doub
     double* y_dev = y;
     if (!y_on_dev) MCF_TRY(sc.get(&y_dev, std::max<int64_t>(m, 1)));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
+    EventGuard event_guard{&e0, &e1};
     if (m > 0) {
         Rec<true>* rec;
         double *acc, *zeta;
@@ -1776,8 +1774,6 @@ static mcf_status solve_mc_classic(mcf_graph* g, const mcf_params* p, const doub
     }
     if (!y_on_dev && m > 0) MCF_CUDA_TRY(cudaMemcpyAsync(y, y_dev, m * sizeof(double), cudaMemcpyDeviceToHost, st));
     mcf_status rc = finish_stats(stats, counters, e0, e1, st);
-    if (e0) cudaEventDestroy(e0);
-    if (e1) cudaEventDestroy(e1);
     if (rc != MCF_OK) return rc;
     if (!y_on_dev) MCF_CUDA_TRY(cudaStreamSynchronize(st));
     return MCF_OK;

@@ -1,0 +1,50 @@
+"""Host-side parts of bench.py on the CPU: the oracle pool that times the
+oracle on several host processes, and the reference arm's JSON line."""
+import json
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+from oracle import estimator as E  # noqa: E402
+from oracle import reference as R  # noqa: E402
+from paper_2308_01037_gb300 import inputs as I  # noqa: E402
+
+
+def test_oracle_pool_counts_the_oracles_steps():
+    """Two spawn-started workers over the CSR in shared memory run the
+    unchanged oracle; the steps they report for a node sample are the steps
+    the oracle reports in this process for the same nodes."""
+    g = I.barabasi_albert(300, 3, 1)
+    w = dict(bench.WORKLOADS["ba1000_tc"], walks_per_node=50)
+    lam = R.lambda_max(g)
+    pool = bench.OraclePool(g, w, procs=2)
+    try:
+        nodes = np.array([0, 5, 299], np.int64)
+        got = pool.pool.map(bench._oracle_worker_task, [(nodes, lam), (nodes, lam)])
+        res = pool.run(lam, 0.2)
+    finally:
+        pool.close()
+    ref = E.action(g, bench.exp_coeffs(w["K"]), gamma=1.0 / lam, walks_per_node=50, seed=1, nodes=nodes,
+                   precision=1)["steps"]
+    assert got == [ref, ref]
+    assert res["cores"] == 2 and res["value"] > 0 and "2 processes" in res["sample"]
+
+
+@pytest.mark.timeout(300)
+def test_reference_arm_prints_one_json_line():
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", "ba1000_tc",
+           "--steps", "2", "--warmup", "0", "--ref-seconds", "3"]
+    out = subprocess.run(cmd, capture_output=True, text=True, timeout=280, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
+    assert d["cpu_baseline"]["cores"] >= 1 and d["e2e"]["h2d_bytes_per_step"] == 0
