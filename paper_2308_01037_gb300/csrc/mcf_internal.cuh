@@ -292,6 +292,7 @@ struct WalkTuning {
     bool tc_col = false;   // MCF_WALK_TC_READ=col: column index + node record instead of the per-entry record
     bool diag_edge = true; // MCF_DIAG_EDGE=0: subgraph-centrality walks read node record + column index
     int diag_cap_log2 = 12; // MCF_DIAG_CAP_LOG2 (10..14): largest hashed row Q_k, log2 of its slots
+    int refill_min = 16;    // MCF_WALK_REFILL_MIN (1..32): idle lanes a TC warp waits for before refilling
 };
 inline const WalkTuning& walk_tuning() {
     static WalkTuning t = [] {
@@ -303,6 +304,7 @@ inline const WalkTuning& walk_tuning() {
         if (const char* e = getenv("MCF_WALK_TC_READ")) w.tc_col = strcmp(e, "col") == 0;
         if (const char* e = getenv("MCF_DIAG_EDGE")) w.diag_edge = atoi(e) != 0;
         if (const char* e = getenv("MCF_DIAG_CAP_LOG2")) w.diag_cap_log2 = std::max(10, std::min(14, atoi(e)));
+        if (const char* e = getenv("MCF_WALK_REFILL_MIN")) w.refill_min = std::max(1, std::min(32, atoi(e)));
         if (const char* e = getenv("MCF_WALK_MINB")) w.minb = atoi(e) >= 8 ? 8 : (atoi(e) <= 5 ? 5 : 6);
         if (const char* e = getenv("MCF_WALK_GRAB")) w.grab = std::max(1, std::min(64, atoi(e)));
         return w;

@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(256, MINB) walk_tc_kernel(
     const float* __restrict__ rm,
     const int32_t* __restrict__ starts, const int64_t* __restrict__ soff, const int64_t* __restrict__ goff,
     const uint32_t* __restrict__ chunk_s0,
-    const double* __restrict__ zeta_g, int K, float wc32, uint2 key, uint32_t req, int grab,
+    const double* __restrict__ zeta_g, int K, float wc32, uint2 key, uint32_t req, int grab, int refill_min,
     double* __restrict__ acc, double* __restrict__ acc2, unsigned long long* __restrict__ counters) {
     __shared__ float zeta[MCF_MAX_COEFFS];
     __shared__ WalkResults<float2> rbuf[256 / 32];
@@ -353,6 +353,9 @@ __global__ void __launch_bounds__(256, MINB) walk_tc_kernel(
     };
     for (;;) {
         unsigned idle = __ballot_sync(FULL, !active);
+        // refill once at least refill_min lanes are idle (or all are): fewer
+        // refill passes against a few idle lanes for a step or two
+        if (idle != FULL && __popc(idle) < refill_min) idle = 0u;
         while (idle && !exhausted) {
             if (p >= valid) {
                 ++c;
@@ -1069,7 +1072,8 @@ static void launch_tc_walks_t(const mcf_graph* g, const Prep& P, const float* rm
     const int grid = persistent_grid(kern, 256, 0);
     ScopedL2Fetch fetch(walk_tuning().l2_fetch);
     kern<<<grid, 256, 0, st>>>(g->node_od, g->edge_od, g->col_idx, rm, P.starts, P.cof, P.soff, chunk_s0, P.zeta, K,
-                               cutoff_f32(wc), key, req, walk_tuning().grab, acc, acc2, P.counters);
+                               cutoff_f32(wc), key, req, walk_tuning().grab, walk_tuning().refill_min, acc, acc2,
+                               P.counters);
 }
 
 template <bool F64, bool WEIGHTED>
