@@ -68,9 +68,9 @@ KERNEL = {"tc": "walk_tc_kernel", "sc": "walk_diag_kernel"}
 # communicability) or walks and the finishing pass (subgraph centrality).
 LAUNCHES_PER_SOLVE = {"tc": 17, "sc": 14}
 # DRAM bytes (read + write) per walk step of walk_tc_kernel from one ncu
-# capture of the R-MAT scale 21 profiling case (7.720e9 B over 264,240,439
+# capture of the R-MAT scale 21 profiling case (7.785e9 B over 264,240,439
 # steps of one launch); a launch of the larger case is scaled by its steps.
-NCU_DRAM_BYTES_PER_STEP = {"rmat22_tc": 29.216, "rmat21_tc": 29.216}
+NCU_DRAM_BYTES_PER_STEP = {"rmat22_tc": 29.462, "rmat21_tc": 29.462}
 
 
 def log(*a):
