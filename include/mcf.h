@@ -297,7 +297,9 @@ mcf_status mcf_server_create(const mcf_server_config* config, mcf_server_t* out)
 
 /* Queues a copy of *query (its arrays must stay valid until the request
  * completes) and returns a ticket.  A request whose footprint alone exceeds
- * the budget completes immediately with MCF_ERR_ADMISSION. */
+ * the budget completes immediately with MCF_ERR_ADMISSION.  Completed
+ * requests stay listed, so every ticket can be polled or waited on again,
+ * until mcf_server_destroy releases them. */
 mcf_status mcf_server_submit(mcf_server_t s, const mcf_query* query, uint64_t* ticket);
 
 /* *done = 1 once the ticket's result is in query->out; *result is its status. */
