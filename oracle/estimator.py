@@ -49,11 +49,12 @@ def _lib_():
             lib.orc_diag.argtypes = [i64, P, P, P, dbl, P, i32, i64, i64, dbl, u64, u32, i32, P, i64, P, P]
             lib.orc_funm_full.argtypes = [i64, P, P, P, dbl, P, i32, i64, i64, dbl, u64, u32, i32, P]
             lib.orc_action_se.argtypes = [i64, P, P, P, dbl, P, P, i32, i64, i64, dbl, u64, u32, i32, P, i64, P]
+            lib.orc_sample_counts.argtypes = [i64, P, P, P, i64, i64, u64, u32, P]
             lib.orc_mc_classic_action.argtypes = [i64, P, P, P, dbl, P, P, i32, i64, dbl, u64, u32, P, i64, P]
             lib.orc_allocation.argtypes = [i64, P, P, P, dbl, i64, i64, P, P, P, P]
             lib.orc_alias_row.argtypes = [i64, P, P, P]
             for f in ("orc_action", "orc_diag", "orc_funm_full", "orc_mc_classic_action", "orc_allocation",
-                      "orc_alias_row", "orc_action_se"):
+                      "orc_alias_row", "orc_action_se", "orc_sample_counts"):
                 getattr(lib, f).restype = i32
             _lib = lib
     return _lib
@@ -158,6 +159,16 @@ def action_se(g, coeffs, v=None, gamma=1.0, n_walks=0, walks_per_node=0, w_cutof
                                  w_cutoff, seed, request_id, precision, _p(nd), 0 if nd is None else len(nd),
                                  _p(se)), "action_se")
     return se
+
+
+def sample_counts(g, row, n_draws, seed=0, request_id=0, values=None):
+    """How often SelectNextState picks each position of ``row`` in n_draws walk steps."""
+    rp, ci, val = _csr(g, values)
+    d = int(g.row_ptr[row + 1] - g.row_ptr[row])
+    counts = np.zeros(d, dtype=np.int64)
+    _check(_lib_().orc_sample_counts(g.n, _p(rp), _p(ci), _p(val), int(row), int(n_draws), seed, request_id,
+                                     _p(counts)), "sample_counts")
+    return counts
 
 
 def funm_full(g, coeffs, gamma=1.0, n_walks=0, walks_per_node=0, w_cutoff=0.0, seed=0, request_id=0,

@@ -604,6 +604,29 @@ int orc_mc_classic_action(int64_t n, const int64_t* rp, const int32_t* ci, const
     return 0;
 }
 
+/* Counts the positions SelectNextState picks in row l over the transitions
+ * k = 0 .. n_draws-1 of walk g (the random words every walk step uses), for
+ * a frequency test of the sampler against t_lj = |a_lj| / sum_k |a_lk|. */
+int orc_sample_counts(int64_t n, const int64_t* rp, const int32_t* ci, const float* val, int64_t l,
+                      int64_t n_draws, uint64_t seed, uint32_t req, int64_t* counts) {
+    if (l < 0 || l >= n || n_draws < 0 || !counts) return -1;
+    chain_t c;
+    int rc = chain_build(&c, n, rp, ci, val, 1.0, 0, 1);
+    if (rc) return rc;
+    int64_t d = rp[l + 1] - rp[l];
+    if (d <= 0) { chain_free(&c); return -1; }
+    for (int64_t j = 0; j < d; ++j) counts[j] = 0;
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    for (int64_t t = 0; t < n_draws; ++t) {
+        /* draw t: transition t % 256 of walk t / 256 */
+        uint32_t w[2];
+        draw_words(val != NULL, (uint64_t)(t / 256), (int)(t % 256), key, req, w);
+        counts[select_next(&c, l, w)] += 1;
+    }
+    chain_free(&c);
+    return 0;
+}
+
 /* Exposes the walk allocation of Definition 1 (for tests of the rule). */
 int orc_allocation(int64_t n, const int64_t* rp, const int32_t* ci, const float* val, double gamma,
                    int64_t n_walks, int64_t walks_per_node, double* rowabs, double* colnorm, int64_t* nw,

@@ -338,3 +338,31 @@ def test_standard_error_vanishes_without_variance():
     y = E.action(g, c, gamma=0.2, walks_per_node=50, seed=1)["y"]
     se = E.action_se(g, c, gamma=0.2, walks_per_node=50, seed=1)
     assert np.all(se <= 1e-7 * y)
+
+
+# ------------------------------------------------------------ SelectNextState frequencies
+@pytest.mark.parametrize("weighted", [False, True])
+def test_sampler_frequencies_chi_square(weighted):
+    """Pearson's chi-square of the picked positions of one row over 2e5 walk
+    steps against t_lj = |a_lj| / sum_k |a_lk| (Definition 1): the statistic
+    stays below the 0.999 quantile for its degrees of freedom (fixed seeds,
+    so the outcome is deterministic)."""
+    from scipy import stats
+
+    g = I.star(41)                          # row 0 has 40 entries
+    w = None
+    p = np.full(40, 1 / 40)
+    if weighted:
+        w = I.symmetric_weights(g, seed=6, signed=True, low=0.1, high=3.0)
+        a = np.abs(w[g.row_ptr[0]:g.row_ptr[1]]).astype(np.float64)
+        p = a / a.sum()
+    n = 200_000
+    for seed in (1, 2):
+        counts = E.sample_counts(g, 0, n, seed=seed, values=w)
+        assert counts.sum() == n
+        chi2 = float(np.sum((counts - n * p) ** 2 / (n * p)))
+        assert chi2 < stats.chi2.ppf(0.999, df=39), chi2
+    # a plausible mistake: sampling uniformly on the weighted row fails the test
+    if weighted:
+        counts = E.sample_counts(g, 0, n, seed=1)
+        assert float(np.sum((counts - n * p) ** 2 / (n * p))) > stats.chi2.ppf(0.999, df=39)
