@@ -788,6 +788,8 @@ def main():
                          "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                          "kernel": KERNEL[w["query"]], "kernel_ms": kernel_ms,
                          "algorithmic_bytes_per_step": ALGO_BYTES_PER_STEP[w["query"]],
+                         "useful_bytes_fraction": None if traffic is None else
+                         ALGO_BYTES_PER_STEP[w["query"]] * steps_per_launch / traffic,
                          "traffic_note": None if traffic is None else
                          "DRAM bytes per launch: ncu dram__bytes_read.sum + dram__bytes_write.sum per walk step on "
                          "the R-MAT scale 21 case (one 32-B sector per random step) x the walk steps of a launch"},
