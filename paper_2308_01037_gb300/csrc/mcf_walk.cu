@@ -307,9 +307,10 @@ __global__ void degree_table(int64_t max_deg, double gamma, float* __restrict__ 
         rm[d] = __double2float_rn(__dmul_rn(gamma, (double)d));
 }
 
-// Same walk schedule, Philox streams, float32 arithmetic and accumulation as
-// walk_action_kernel<false, false, MINB> (so the same result up to float64
-// summation order), with the per-step state reduced to {offset, degree}.
+// The same walks (ids, Philox streams), float32 arithmetic and accumulation
+// as walk_action_kernel<false, false, MINB> (so the same result up to float64
+// summation order), with the per-step state reduced to {offset, degree} and
+// a warp's idle lanes refilled refill_min or more at a time.
 template <int MINB, bool PREFETCH, bool VIA_COL>
 __global__ void __launch_bounds__(256, MINB) walk_tc_kernel(
     const uint2* __restrict__ nod, const uint2* __restrict__ eod, const int32_t* __restrict__ col,
