@@ -40,7 +40,9 @@ def _lib_():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
+            # MCF_ORACLE_LIB names another build of mcf_oracle.c: the tests
+            # that plant mistakes in a copy of the oracle load it this way
+            lib = ctypes.CDLL(os.environ.get("MCF_ORACLE_LIB") or build())
             P, i64, u64, u32, dbl, i32 = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32,
                                           ctypes.c_double, ctypes.c_int)
             lib.orc_philox4x32_10.argtypes = [P, P, P]

@@ -48,6 +48,9 @@ def test_allocation_rounding_floor_and_isolated():
     _, _, nw, off = E.allocation(g, gamma=1.0, n_walks=3)
     # p_0 = 2/6, p_leaf = 1/6: 3*2/6 = 1.0 -> 1, 3/6 = 0.5 -> llround 1 (half away from zero)
     assert nw.tolist() == [1, 1, 1, 1, 1, 0, 0]
+    # N_s = 2: 2/6 = 0.33 rounds to 0, and the floor of one walk lifts every leaf to 1
+    _, _, nw, off = E.allocation(g, gamma=1.0, n_walks=2)
+    assert nw.tolist() == [1, 1, 1, 1, 1, 0, 0] and off[-1] == 5
     _, _, nw, _ = E.allocation(g, gamma=1.0, n_walks=0, walks_per_node=4)
     assert nw.tolist() == [4, 4, 4, 4, 4, 0, 0]
 
@@ -85,6 +88,38 @@ def test_degree_two_polynomial_is_exact(ba12):
     assert np.allclose(y, exact, rtol=1e-13, atol=1e-13)
     d = E.diag(g, c, gamma=gam, walks_per_node=1, seed=9)["d"]
     assert np.allclose(d, c[0] + c[2] * np.diag(A @ A), rtol=1e-13, atol=1e-13)
+
+
+def test_degree_two_polynomial_with_loops_is_exact():
+    """A symmetric signed A with loops: a'_ii enters d_i through zeta_1 (the
+    zeta_1 A' term of Eq. rand_funm_formula_diag) and F = zeta_0 I + zeta_1 A'
+    + zeta_2 A'^2 for Algorithm 2; with zeta_k = 0 for k > 2 one walk per
+    node is exact for all three estimators."""
+    n = 8
+    und = np.array([(0, 1), (1, 2), (2, 3), (3, 0), (1, 5), (4, 5), (5, 6), (6, 7), (2, 6)])
+    loops = np.array([1, 4, 6])
+    src = np.concatenate([und[:, 0], und[:, 1], loops])
+    dst = np.concatenate([und[:, 1], und[:, 0], loops])
+    g = I.directed_from_edges(n, src, dst)
+    A0 = g.dense()
+    assert np.array_equal(A0, A0.T) and np.count_nonzero(np.diag(A0)) == 3
+    # symmetric signed values: the value of (i, j) is that of (min, max)
+    rows = np.repeat(np.arange(n), np.diff(g.row_ptr))
+    cols = g.col_idx.astype(np.int64)
+    rng = np.random.default_rng(11)
+    table = rng.uniform(0.5, 1.5, (n, n)) * rng.choice([-1.0, 1.0], (n, n))
+    w = table[np.minimum(rows, cols), np.maximum(rows, cols)].astype(np.float32)
+    gam = 0.4
+    A = gam * R.csr_matrix(g, w).toarray()
+    c = np.array([0.6, -1.1, 0.35])
+    exact_F = c[0] * np.eye(n) + c[1] * A + c[2] * A @ A
+    v = rng.standard_normal(n)
+    y = E.action(g, c, v=v, gamma=gam, walks_per_node=1, seed=2, values=w)["y"]
+    assert np.allclose(y, exact_F @ v, rtol=1e-13, atol=1e-13)
+    d = E.diag(g, c, gamma=gam, walks_per_node=1, seed=2, values=w)["d"]
+    assert np.allclose(d, np.diag(exact_F), rtol=1e-13, atol=1e-13)
+    F = E.funm_full(g, c, gamma=gam, walks_per_node=1, seed=2, values=w)
+    assert np.allclose(F, exact_F, rtol=1e-13, atol=1e-13)
 
 
 @pytest.mark.parametrize("G", [lambda: I.complete(7), lambda: I.cycle(9)])

@@ -122,6 +122,33 @@ def test_directed_cycle_is_exact(n):
     assert np.allclose(F, F_ex, rtol=1e-14, atol=1e-15)
     yc = E.mc_classic_action(g, c, np.arange(n), 1, seed=1)
     assert np.allclose(yc, c.sum(), rtol=1e-14)
+    # a general v: (P^k v)_i = v_{(i + k) mod n}, so y_i = sum_k zeta_k v_{(i+k) mod n}
+    v = np.random.default_rng(n + 1).standard_normal(n)
+    y_ex = np.array([sum(c[k] * v[(i + k) % n] for k in range(len(c))) for i in range(n)])
+    assert np.allclose(F_ex @ v, y_ex, rtol=1e-14)
+    assert np.allclose(E.action(g, c, v=v, walks_per_node=1, seed=1)["y"], y_ex, rtol=1e-13, atol=1e-14)
+    assert np.allclose(E.mc_classic_action(g, c, np.arange(n), 1, v=v, seed=1), y_ex, rtol=1e-13, atol=1e-14)
+
+
+def test_signed_weighted_directed_cycle_is_exact():
+    """Arc i -> i+1 carries a signed weight s_i: a row has one entry, so its
+    row sum |s_i| and sign fix the weight ratio of Eq. weights and every walk
+    is deterministic, (A'^k v)_i = gamma^k s_i s_(i+1) ... s_(i+k-1) v_(i+k).
+    One walk per node is exact for all four estimators; a dropped sign fails."""
+    n = 5
+    g = I.directed_cycle(n)
+    s = np.array([0.8, -1.25, 1.5, -0.6, 1.1], np.float32)   # row i's single value
+    gam = 0.7
+    A = gam * R.csr_matrix(g, s).toarray()
+    c = np.random.default_rng(2).uniform(0.1, 1.0, 11)
+    F_ex = R.dense_powers_series(A, c)
+    v = np.random.default_rng(3).standard_normal(n)
+    kw = dict(gamma=gam, walks_per_node=1, seed=4, values=s)
+    assert np.allclose(E.action(g, c, v=v, **kw)["y"], F_ex @ v, rtol=1e-13, atol=1e-14)
+    assert np.allclose(E.diag(g, c, **kw)["d"], np.diag(F_ex), rtol=1e-13, atol=1e-14)
+    assert np.allclose(E.funm_full(g, c, **kw), F_ex, rtol=1e-13, atol=1e-14)
+    yc = E.mc_classic_action(g, c, np.arange(n), 1, v=v, gamma=gam, seed=4, values=s)
+    assert np.allclose(yc, F_ex @ v, rtol=1e-13, atol=1e-14)
 
 
 def test_nilpotent_dag_is_polynomial():
