@@ -375,6 +375,56 @@ def test_standard_error_vanishes_without_variance():
     assert np.all(se <= 1e-7 * y)
 
 
+def test_enumerated_variances_match_repeated_runs():
+    """The enumerated variances that every sigma-bound above divides by, checked
+    against the spread of the C estimator itself: 3000 independent runs
+    (seeds) with the N_s allocation of Definition 1, so N_i differs between
+    nodes (Var(y_j) = sum_i a'_ji^2 Var(X_i) / N_i, and for the diagonal
+    sum_k a'_ik^2 Var(Y_k,i) / N_k).  The sample variance of a near-Gaussian
+    mean over 3000 runs is within a few percent of the true one."""
+    g = I.barabasi_albert(10, 2, 5)
+    w = I.symmetric_weights(g, seed=4, signed=True, low=0.1, high=5.0)
+    gam = 0.8 / np.abs(np.linalg.eigvalsh(R.csr_matrix(g, w).toarray())).max()
+    c = R.exp_coeffs(6)
+    ns = 150 * g.n
+    _, _, nw, _ = E.allocation(g, gamma=gam, n_walks=ns, values=w)
+    assert nw.max() > 2 * nw.min()
+    ex = R.enumerate_action(g, c, gamma=gam, values=w)
+    var_y = R.action_variance(ex, nw)
+    ed = R.enumerate_diag(g, c, gamma=gam, values=w, nw=nw)
+    runs = 3000
+    ys = np.array([E.action(g, c, gamma=gam, n_walks=ns, seed=s, values=w)["y"] for s in range(runs)])
+    ds = np.array([E.diag(g, c, gamma=gam, n_walks=ns, seed=s, values=w)["d"] for s in range(runs)])
+    assert np.all(var_y > 0) and np.all(ed["var_d"] > 0)
+    assert np.all(np.abs(ys.var(0, ddof=1) / var_y - 1.0) < 0.12)
+    assert np.all(np.abs(ds.var(0, ddof=1) / ed["var_d"] - 1.0) < 0.12)
+    assert _zscore(ys.mean(0), ex["mean_y"], var_y / runs) < Z_MAX
+    assert _zscore(ds.mean(0), ed["mean_d"], ed["var_d"] / runs) < Z_MAX
+
+
+def test_enumeration_with_loops_reproduces_series():
+    """Lemma 2 on a signed symmetric A with loops: a walk may stay on its node,
+    and the diagonal adds zeta_1 a'_ii."""
+    n = 7
+    und = np.array([(0, 1), (1, 2), (2, 3), (3, 4), (4, 0), (1, 5), (5, 6), (2, 6)])
+    loops = np.array([0, 2, 5])
+    g = I.directed_from_edges(n, np.concatenate([und[:, 0], und[:, 1], loops]),
+                              np.concatenate([und[:, 1], und[:, 0], loops]))
+    rows = np.repeat(np.arange(n), np.diff(g.row_ptr))
+    cols = g.col_idx.astype(np.int64)
+    rng = np.random.default_rng(6)
+    table = rng.uniform(0.5, 1.5, (n, n)) * rng.choice([-1.0, 1.0], (n, n))
+    w = table[np.minimum(rows, cols), np.maximum(rows, cols)].astype(np.float32)
+    A = R.csr_matrix(g, w).toarray()
+    assert np.array_equal(A, A.T) and np.count_nonzero(np.diag(A)) == 3
+    gam = 0.9 / np.abs(np.linalg.eigvalsh(A)).max()
+    c = np.random.default_rng(7).uniform(0.1, 1.0, 6)
+    F = R.dense_powers_series(gam * A, c)
+    v = rng.standard_normal(n)
+    assert np.allclose(R.enumerate_action(g, c, gamma=gam, v=v, values=w)["mean_y"], F @ v, rtol=1e-13, atol=1e-13)
+    assert np.allclose(R.enumerate_diag(g, c, gamma=gam, values=w)["mean_d"], np.diag(F), rtol=1e-13, atol=1e-13)
+
+
 # ------------------------------------------------------------ SelectNextState frequencies
 @pytest.mark.parametrize("weighted", [False, True])
 def test_sampler_frequencies_chi_square(weighted):

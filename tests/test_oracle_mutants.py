@@ -1,18 +1,25 @@
-"""Planted mistakes in a copy of the C oracle (oracle part 1): each one must
-fail at least one pin of tests/test_oracle_{estimator,general,philox}.py.
+"""Planted mistakes in copies of the oracle: each one must fail at least one
+pin of tests/test_oracle_*.py.
 
 The pins are meant to be chosen so that a plausible mistake anywhere in the
-estimator (a dropped term, a wrong sign or index, a transposed operand, a
-wrong normalisation) shows.  This test makes that claim checkable: it writes
-a copy of ``oracle/mcf_oracle.c`` with one textual change, compiles it with
-the oracle's own flags into a temporary directory, and runs the pin modules
-against it (``MCF_ORACLE_LIB`` makes ``oracle.estimator`` load that build).
+oracle (a dropped term, a wrong sign or index, a transposed operand, a wrong
+normalisation) shows.  This test makes that claim checkable.
+
+* The C estimator (part 1): a copy of ``oracle/mcf_oracle.c`` with one
+  textual change is compiled with the oracle's own flags into a temporary
+  directory, and the pin modules run against it (``MCF_ORACLE_LIB`` makes
+  ``oracle.estimator`` load that build).
+* The float64 reference (part 2): a temporary tree holds a copy of
+  ``oracle/`` whose ``reference.py`` carries one change, and a copy of
+  ``tests/``; the pin modules run from there.
+
 An unchanged copy must pass every pin, and every changed copy must fail one.
 The oracle in the tree is never modified.  Each mistake names the passage of
-the paper (or the reading of it) that it violates.
+the paper (or the reading, or the mathematics) that it violates.
 """
 import concurrent.futures as cf
 import os
+import shutil
 import subprocess
 import sys
 import tempfile
@@ -24,7 +31,9 @@ from paper_2308_01037_gb300 import inputs as I
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "mcf_oracle.c")
+REF = os.path.join(ROOT, "oracle", "reference.py")
 PINS = ["tests/test_oracle_estimator.py", "tests/test_oracle_general.py", "tests/test_oracle_philox.py"]
+REF_PINS = ["tests/test_oracle_reference.py", "tests/test_oracle_estimator.py", "tests/test_oracle_general.py"]
 
 # (name, what it violates, text in mcf_oracle.c, planted replacement)
 MUTANTS = [
@@ -117,6 +126,85 @@ MUTANTS = [
 ]
 
 
+# (name, what it violates, text in reference.py, planted replacement)
+REFERENCE_MUTANTS = [
+    ("exp_factorial", "zeta_k = 1/k! of the exponential",
+     "beta ** k / math.factorial(k)", "beta ** k / math.factorial(k + 1)"),
+    ("katz_tail_one_short", "geometric tail rho^(K+1) / (1 - rho) of the Neumann series",
+     "/ math.log(rho) - 1.0)))", "/ math.log(rho))))"),
+    ("mittag_leffler_beta", "zeta_k = 1 / Gamma(alpha k + beta)",
+     "math.exp(-math.lgamma(alpha * k + beta))", "math.exp(-math.lgamma(alpha * k + 1.0))"),
+    ("csr_without_gamma", "A' = gamma A (Section 2.2)",
+     "return sp.csr_matrix((gamma * data,", "return sp.csr_matrix((data,"),
+    ("lambda_second_largest", "scale 1/lambda_max",
+     "return float(np.linalg.eigvalsh(csr_matrix(g, values).toarray())[-1])",
+     "return float(np.linalg.eigvalsh(csr_matrix(g, values).toarray())[-2])"),
+    ("arpack_smallest", "scale 1/lambda_max (large graphs)", 'which="LA"', 'which="SA"'),
+    ("gershgorin_signed_sum", "Gershgorin bound max_i sum_k |a_ik| (Section 4.5)",
+     "np.abs(A).sum(axis=1).max()", "A.sum(axis=1).max()"),
+    ("eigen_reconstruction", "f(A) = V f(Lambda) V^T",
+     "return (V * f) @ V.T", "return (V * f) @ V"),
+    ("powers_not_accumulated", "Eq. power_series: A^k by repeated products",
+     "            P = P @ A\n", "            P = A\n"),
+    ("series_zeta0_dropped", "Eq. power_series: the zeta_0 v term",
+     "y = coeffs[0] * t\n", "y = 0.0 * t\n"),
+    ("series_diag_entries", "diagonal entries (e_i^T f(A') e_i)",
+     "out[b0:b0 + block] = D[idx, np.arange(len(idx))]",
+     "out[b0:b0 + block] = D[np.arange(len(idx)), np.arange(len(idx))]"),
+    ("walk_zeta_index", "Lemma 2: W^(k) carries zeta_(k+2)",
+     "X = X + coeffs[k + 2] * W * contrib(l)", "X = X + coeffs[k + 1] * W * contrib(l)"),
+    ("walk_truncation", "truncation at zeta_K",
+     "leaf = (k + 2 >= K) or len(nbr[l]) == 0", "leaf = (k + 3 >= K) or len(nbr[l]) == 0"),
+    ("walk_weight_without_t", "Eq. weights: W multiplied by a_ij / t_ij",
+     "stack.append((j, k + 1, W * (a / t), P * t, X))", "stack.append((j, k + 1, W * a, P * t, X))"),
+    ("walk_probability_without_t", "Definition 1: a path has probability prod t",
+     "stack.append((j, k + 1, W * (a / t), P * t, X))", "stack.append((j, k + 1, W * (a / t), P, X))"),
+    ("walk_cutoff_after_add", "Eq. weight_cutoff: the test precedes the visit",
+     "        if not (abs(W) > w_cutoff):\n            leaf = True\n        else:\n"
+     "            X = X + coeffs[k + 2] * W * contrib(l)\n            leaf = (k + 2 >= K) or len(nbr[l]) == 0\n",
+     "        X = X + coeffs[k + 2] * W * contrib(l)\n        if not (abs(W) > w_cutoff):\n"
+     "            leaf = True\n        else:\n            leaf = (k + 2 >= K) or len(nbr[l]) == 0\n"),
+    ("enum_action_zeta1_dropped", "Algorithm 3: y = zeta_0 v + zeta_1 r + A'q",
+     "y = coeffs[0] * v + (coeffs[1] * r if K >= 1 else 0.0)", "y = coeffs[0] * v"),
+    ("action_variance_not_squared", "Var(y_j) = sum_i a'_ji^2 Var(X_i) / N_i",
+     'var[j] += a * a * ex["var_walk"][i] / nw[i]', 'var[j] += a * ex["var_walk"][i] / nw[i]'),
+    ("action_variance_N_of_j", "Var(y_j) = sum_i a'_ji^2 Var(X_i) / N_i",
+     'var[j] += a * a * ex["var_walk"][i] / nw[i]', 'var[j] += a * a * ex["var_walk"][i] / nw[j]'),
+    ("enum_diag_row_k", "Eq. rand_funm_formula_diag: the rows i of column k",
+     "for i in np.nonzero(Arow[:, k])[0]:", "for i in np.nonzero(Arow[k, :])[0]:"),
+    ("enum_diag_aik_missing", "Eq. rand_funm_formula_diag: a'_ik <Q_k, C_i>",
+     "mean[i] += a * e1[i]", "mean[i] += e1[i]"),
+    ("enum_diag_aii_dropped", "Eq. rand_funm_formula_diag: the zeta_1 a'_ii term",
+     "coeffs[1] * Arow[i, i] if K >= 1 else 0.0", "0.0 * Arow[i, i] if K >= 1 else 0.0"),
+    ("enum_diag_variance_N_of_i", "Var(d_i) = sum_k a'_ik^2 Var(Y_k,i) / N_k",
+     "var[i] += a * a * max(e2[i] - e1[i] ** 2, 0.0) / nw[k]",
+     "var[i] += a * a * max(e2[i] - e1[i] ** 2, 0.0) / nw[i]"),
+    ("enum_rows_transposed", "a visit of l adds row l of A'",
+     "Arow[i, j] += a\n", "Arow[j, i] += a\n"),
+]
+
+
+def _pytest(pins, cwd, env):
+    r = subprocess.run([sys.executable, "-m", "pytest", *pins, "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu"],
+                       cwd=cwd, env=env, capture_output=True, text=True, timeout=900)
+    lines = r.stdout.splitlines()
+    failed = [ln for ln in lines if ln.startswith(("FAILED", "ERROR"))]
+    return r.returncode, failed[0] if failed else (lines[-1] if lines else r.stderr[-300:])
+
+
+def _run_reference_pins(text, lib):
+    """Runs the pin modules from a temporary tree whose oracle/reference.py is ``text``."""
+    with tempfile.TemporaryDirectory(prefix="reference_mutant_") as d:
+        skip = shutil.ignore_patterns("__pycache__", "_build")
+        shutil.copytree(os.path.join(ROOT, "oracle"), os.path.join(d, "oracle"), ignore=skip)
+        shutil.copytree(os.path.join(ROOT, "tests"), os.path.join(d, "tests"), ignore=skip)
+        os.symlink(os.path.join(ROOT, "paper_2308_01037_gb300"), os.path.join(d, "paper_2308_01037_gb300"))
+        with open(os.path.join(d, "oracle", "reference.py"), "w") as f:
+            f.write(text)
+        env = dict(os.environ, MCF_ORACLE_LIB=lib, OMP_NUM_THREADS="1", PYTHONDONTWRITEBYTECODE="1")
+        return _pytest(REF_PINS, d, env)
+
+
 def _run_pins(text):
     """Compiles ``text`` as the oracle and runs the pin modules against it;
     returns (pytest exit code, first failing test or last line)."""
@@ -128,32 +216,41 @@ def _run_pins(text):
         subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math", src,
                         "-o", so, "-lm"], check=True, capture_output=True)
         env = dict(os.environ, MCF_ORACLE_LIB=so, OMP_NUM_THREADS="1")
-        r = subprocess.run([sys.executable, "-m", "pytest", *PINS, "-x", "-q", "-p", "no:cacheprovider",
-                            "-m", "not gpu"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
-    lines = r.stdout.splitlines()
-    failed = [ln for ln in lines if ln.startswith(("FAILED", "ERROR"))]
-    return r.returncode, failed[0] if failed else (lines[-1] if lines else r.stderr[-300:])
+        return _pytest(PINS, ROOT, env)
+
+
+def _jobs(path, mutants, what):
+    with open(path) as f:
+        text = f.read()
+    for name, _, old, _ in mutants:
+        assert text.count(old) == 1, f"{name}: the text to change must occur exactly once in {what}"
+    return [("unchanged", text)] + [(name, text.replace(old, new)) for name, _, old, new in mutants]
 
 
 @pytest.fixture(scope="module")
 def outcomes():
     I.build()
-    E.build()
-    with open(SRC) as f:
-        text = f.read()
-    for name, _, old, _ in MUTANTS:
-        assert text.count(old) == 1, f"{name}: the text to change must occur exactly once in mcf_oracle.c"
-    jobs = [("unchanged", text)] + [(name, text.replace(old, new)) for name, _, old, new in MUTANTS]
+    lib = E.build()
+    jobs = [("c", name, text) for name, text in _jobs(SRC, MUTANTS, "mcf_oracle.c")]
+    jobs += [("py", name, text) for name, text in _jobs(REF, REFERENCE_MUTANTS, "reference.py")]
+
+    def run(job):
+        kind, _, text = job
+        return _run_pins(text) if kind == "c" else _run_reference_pins(text, lib)
+
     with cf.ThreadPoolExecutor(max(1, min(8, os.cpu_count() or 1))) as ex:
-        res = list(ex.map(lambda j: _run_pins(j[1]), jobs))
-    return dict(zip([j[0] for j in jobs], res))
+        res = list(ex.map(run, jobs))
+    return {(kind, name): r for (kind, name, _), r in zip(jobs, res)}
 
 
-def test_unchanged_copy_passes_every_pin(outcomes):
-    rc, info = outcomes["unchanged"]
+@pytest.mark.parametrize("kind", ["c", "py"])
+def test_unchanged_copy_passes_every_pin(outcomes, kind):
+    rc, info = outcomes[(kind, "unchanged")]
     assert rc == 0, info
 
 
-def test_every_planted_mistake_fails_a_pin(outcomes):
-    survived = {name: info for name, (rc, info) in outcomes.items() if name != "unchanged" and rc != 1}
+@pytest.mark.parametrize("kind", ["c", "py"])
+def test_every_planted_mistake_fails_a_pin(outcomes, kind):
+    survived = {name: info for (k, name), (rc, info) in outcomes.items()
+                if k == kind and name != "unchanged" and rc != 1}
     assert not survived, f"planted mistakes that no pin caught (or that broke the run): {survived}"

@@ -29,6 +29,14 @@ def test_gershgorin_is_max_degree():
     assert R.gershgorin(g) == g.degree.max()
 
 
+def test_gershgorin_signed_weights_by_hand():
+    """P_3 with a01 = 2, a12 = -3: absolute row sums 2, 5, 3 (a signed sum would give -1 for row 1)."""
+    g = I.path(3)
+    w = np.array([2.0, 2.0, -3.0, -3.0], np.float32)
+    assert R.gershgorin(g, w) == 5.0
+    assert R.gershgorin(g, -w) == 5.0
+
+
 @pytest.mark.parametrize("n", [3, 6, 11])
 def test_complete_graph_closed_form(n):
     """K_n = J - I has eigenvalues n-1 (eigenvector 1) and -1 (multiplicity n-1)."""
