@@ -122,7 +122,9 @@ typedef struct {
  * tables of the transition probabilities t_ij = |a_ij| / sum_k |a_ik|
  * (Eq. definition1).  Loops (a_ii != 0) are accepted.  n may be 0.
  * On success *out owns device memory until mcf_destroy_graph.
- * Errors: MCF_ERR_INVALID_ARG, MCF_ERR_INVALID_GRAPH, MCF_ERR_OOM, MCF_ERR_CUDA. */
+ * Errors: MCF_ERR_INVALID_ARG, MCF_ERR_INVALID_GRAPH, MCF_ERR_OOM, MCF_ERR_CUDA
+ * (also when no usable CUDA device or driver is present: nothing runs on
+ * the host instead). */
 mcf_status mcf_create_graph(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const float* values,
                             uint32_t flags, mcf_graph_t* out);
 

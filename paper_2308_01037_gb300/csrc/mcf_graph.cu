@@ -460,7 +460,10 @@ mcf_status mcf_create_graph(int64_t n, const int64_t* row_ptr, const int32_t* co
     if (graph_alloc(&g->row_ptr, (size_t)(n + 1) * sizeof(int64_t)) != cudaSuccess ||
         graph_alloc(&g->col_idx, (size_t)std::max<int64_t>(nnz, 1) * sizeof(int32_t)) != cudaSuccess ||
         graph_alloc(&g->diag, (size_t)std::max<int64_t>(n, 1) * sizeof(double)) != cudaSuccess) {
-        cudaGetLastError();
+        // the first device call of a graph: tell a missing device or driver from a full one
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaErrorMemoryAllocation)
+            return cleanup(fail(MCF_ERR_CUDA, std::string("no usable CUDA device: ") + cudaGetErrorString(e)));
         return cleanup(fail(MCF_ERR_OOM, "device allocation of the CSR failed"));
     }
     if (cudaMemcpy(g->row_ptr, row_ptr, (size_t)(n + 1) * sizeof(int64_t), kind) != cudaSuccess ||

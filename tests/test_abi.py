@@ -82,3 +82,19 @@ def test_struct_layouts_match_the_header(tmp_path):
         for f in cls._fields_:
             assert got[(name, f[0])] == getattr(cls, f[0]).offset, (name, f[0])
 
+
+
+def test_no_device_means_an_error_not_a_fallback(lib):
+    """On a host without a usable CUDA device the first device call of the
+    product path returns MCF_ERR_CUDA and the binding raises: nothing is
+    computed on the CPU instead."""
+    import numpy as np
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    rp = np.array([0, 1, 2], np.int64)
+    ci = np.array([1, 0], np.int32)
+    with pytest.raises(M.McfError) as ei:
+        M.mcf_create_graph(2, rp, ci)
+    assert ei.value.status == 4 and "CUDA" in str(ei.value)
