@@ -402,6 +402,38 @@ def test_enumerated_variances_match_repeated_runs():
     assert _zscore(ds.mean(0), ed["mean_d"], ed["var_d"] / runs) < Z_MAX
 
 
+@pytest.mark.parametrize("k", [0, 1, 2, 3, 4])
+def test_enumerated_second_moments_closed_form(k):
+    """With one non-zero coefficient zeta_(k+2) = 1 a walk's sum is X = W^(k) r_(l_k)
+    (the graph has no sinks), so E[X] = (A'^k r)_i and, because every step
+    multiplies E[W^2 g] by t_lj (a'_lj / t_lj)^2 = rowabs_l |a'_lj|,
+    E[X^2] = (M^k (r o r))_i with M = diag(rowabs) |A'| (Eq. weights, Definition 1).
+    For the diagonal, Y_(k,i) = W^(k) a'_(l_k, i): E[Y] = (A'^(k+1))_(ki) and
+    E[Y^2] = (M^k (A' o A'))_(ki)."""
+    g = I.barabasi_albert(12, 2, 3)
+    w = I.symmetric_weights(g, seed=5, signed=True)
+    A = R.csr_matrix(g, w).toarray()
+    gam = 0.7 / np.abs(np.linalg.eigvalsh(A)).max()
+    Ap = gam * A
+    M = np.abs(Ap).sum(1)[:, None] * np.abs(Ap)
+    Mk = np.linalg.matrix_power(M, k)
+    v = np.random.default_rng(1).standard_normal(g.n)
+    r = Ap @ v
+    c = np.zeros(k + 3)
+    c[k + 2] = 1.0
+    ex = R.enumerate_action(g, c, gamma=gam, v=v, values=w)
+    m1 = np.linalg.matrix_power(Ap, k) @ r
+    m2 = Mk @ (r * r)
+    assert np.allclose(ex["Eq"], m1, rtol=1e-12, atol=1e-15)
+    assert np.allclose(ex["var_walk"], m2 - m1 ** 2, rtol=1e-10, atol=1e-14 * m2.max())
+    ed = R.enumerate_diag(g, c, gamma=gam, values=w, nw=np.ones(g.n, np.int64))
+    EY = np.linalg.matrix_power(Ap, k + 1)
+    EY2 = Mk @ (Ap * Ap)
+    assert np.allclose(ed["mean_d"], (Ap * EY).sum(0), rtol=1e-12, atol=1e-15)   # zeta_0 = zeta_1 = 0
+    var_d = ((Ap * Ap) * (EY2 - EY ** 2)).sum(0)
+    assert np.allclose(ed["var_d"], var_d, rtol=1e-10, atol=1e-14 * max(EY2.max(), 1e-300))
+
+
 def test_enumeration_with_loops_reproduces_series():
     """Lemma 2 on a signed symmetric A with loops: a walk may stay on its node,
     and the diagonal adds zeta_1 a'_ii."""
