@@ -67,3 +67,13 @@ def test_clock_summary_parses_nvidia_smi_samples():
     assert c.summary()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
     c.lines = []
     assert c.summary()["samples"] == 0
+
+
+def test_reference_arm_other_ranks_exit_without_work():
+    """Under torchrun only rank 0 times the oracle and prints; another rank exits 0 silently."""
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", "ba1000_tc",
+           "--steps", "1", "--warmup", "0", "--ref-seconds", "1"]
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    out = subprocess.run(cmd, capture_output=True, text=True, timeout=120, cwd=ROOT, env=env)
+    assert out.returncode == 0, out.stderr[-2000:]
+    assert not [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
