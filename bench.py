@@ -790,6 +790,10 @@ def main():
                          "algorithmic_bytes_per_step": ALGO_BYTES_PER_STEP[w["query"]],
                          "useful_bytes_fraction": None if traffic is None else
                          ALGO_BYTES_PER_STEP[w["query"]] * steps_per_launch / traffic,
+                         # DRAM bytes actually moved per second (traffic / live launch time) and their share
+                         # of the measured copy peak
+                         "dram_gbs": None if traffic is None else traffic / (kernel_ms / 1000.0) / 1e9,
+                         "dram_frac": None if traffic is None else traffic / (kernel_ms / 1000.0) / 1e9 / peak,
                          "traffic_note": None if traffic is None else
                          "DRAM bytes per launch: ncu dram__bytes_read.sum + dram__bytes_write.sum per walk step on "
                          "the R-MAT scale 21 case (one 32-B sector per random step) x the walk steps of a launch"},
