@@ -162,6 +162,21 @@ def _ptr(x, dtype):
     return a.ctypes.data, a
 
 
+def _out_ptr(x):
+    """Pointer of an output buffer the library writes in place: it must already be
+    float64 and contiguous (a converted copy would take the results instead)."""
+    if _is_torch(x):
+        import torch
+
+        if x.dtype != torch.float64 or not x.is_contiguous():
+            raise TypeError(f"output must be a contiguous float64 tensor, got {x.dtype}"
+                            f"{'' if x.is_contiguous() else ' (not contiguous)'}")
+        return x.data_ptr(), x
+    if not (isinstance(x, np.ndarray) and x.dtype == np.float64 and x.flags.c_contiguous and x.flags.writeable):
+        raise TypeError("output must be a writeable C-contiguous float64 numpy array or torch tensor")
+    return x.ctypes.data, x
+
+
 def _stream_of(*arrays):
     for a in arrays:
         if a is not None and _is_torch(a) and a.is_cuda:
@@ -252,7 +267,7 @@ def mcf_action(g: GraphHandle, v, coeffs, out=None, device_out=None, stats=False
     """f(A')v by RandFunmAction; keyword arguments fill mcf_params."""
     y = _output(out, g.n, device_out if device_out is not None else v)
     vp, kv = _ptr(v, np.float64)
-    yp, ky = _ptr(y, np.float64)
+    yp, ky = _out_ptr(y)
     st = mcf_stats()
     p, kc = _params(coeffs, stream=kw.pop("stream", None) or _stream_of(v, y), **kw)
     _check(load().mcf_action(g.handle, ctypes.byref(p), vp, yp, ctypes.byref(st) if stats else None))
@@ -264,7 +279,7 @@ def mcf_action_nodes(g: GraphHandle, nodes, coeffs, v=None, out=None, device_out
     y = _output(out, len(nodes), device_out if device_out is not None else nodes)
     vp, kv = _ptr(v, np.float64)
     npt, kn = _ptr(nodes, np.int64)
-    yp, ky = _ptr(y, np.float64)
+    yp, ky = _out_ptr(y)
     st = mcf_stats()
     p, kc = _params(coeffs, stream=kw.pop("stream", None) or _stream_of(nodes, y), **kw)
     _check(load().mcf_action_nodes(g.handle, ctypes.byref(p), vp, npt, int(len(nodes)), yp,
@@ -275,7 +290,7 @@ def mcf_action_nodes(g: GraphHandle, nodes, coeffs, v=None, out=None, device_out
 def mcf_total_communicability(g: GraphHandle, coeffs, out=None, device_out=None, stats=False, **kw):
     """f(A')1 (total communicability)."""
     y = _output(out, g.n, device_out)
-    yp, ky = _ptr(y, np.float64)
+    yp, ky = _out_ptr(y)
     st = mcf_stats()
     p, kc = _params(coeffs, stream=kw.pop("stream", None) or _stream_of(y), **kw)
     _check(load().mcf_total_communicability(g.handle, ctypes.byref(p), yp, ctypes.byref(st) if stats else None))
@@ -287,7 +302,7 @@ def mcf_subgraph_centrality(g: GraphHandle, coeffs, nodes=None, out=None, device
     m = g.n if nodes is None else len(nodes)
     d = _output(out, m, device_out if device_out is not None else nodes)
     npt, kn = _ptr(nodes, np.int64)
-    dp, kd = _ptr(d, np.float64)
+    dp, kd = _out_ptr(d)
     st = mcf_stats()
     p, kc = _params(coeffs, stream=kw.pop("stream", None) or _stream_of(nodes, d), **kw)
     _check(load().mcf_subgraph_centrality(g.handle, ctypes.byref(p), npt, int(m), dp,
@@ -298,7 +313,7 @@ def mcf_subgraph_centrality(g: GraphHandle, coeffs, nodes=None, out=None, device
 def mcf_katz(g: GraphHandle, gamma, K=0, out=None, device_out=None, stats=False, **kw):
     """(I - gamma A)^{-1} 1 as the truncated Neumann series (K = 0: from the tail bound)."""
     y = _output(out, g.n, device_out)
-    yp, ky = _ptr(y, np.float64)
+    yp, ky = _out_ptr(y)
     st = mcf_stats()
     p, kc = _params([1.0], stream=kw.pop("stream", None) or _stream_of(y), **kw)
     _check(load().mcf_katz(g.handle, float(gamma), int(K), ctypes.byref(p), yp,
@@ -312,7 +327,7 @@ MCF_FULL_MAX_NODES = 16384
 def mcf_funm_full(g: GraphHandle, coeffs, out=None, device_out=None, stats=False, **kw):
     """Dense estimate F (n x n, row-major) of f(A') by RandFunm (Algorithm 2)."""
     F = _output(out, g.n * g.n, device_out)
-    Fp, kf = _ptr(F, np.float64)
+    Fp, kf = _out_ptr(F)
     st = mcf_stats()
     p, kc = _params(coeffs, stream=kw.pop("stream", None) or _stream_of(F), **kw)
     _check(load().mcf_funm_full(g.handle, ctypes.byref(p), Fp, ctypes.byref(st) if stats else None))
@@ -327,7 +342,7 @@ def mcf_mc_classic(g: GraphHandle, coeffs, walks_per_row, v=None, nodes=None, ou
     y = _output(out, m, device_out if device_out is not None else (nodes if nodes is not None else v))
     vp, kv = _ptr(v, np.float64)
     npt, kn = _ptr(nodes, np.int64)
-    yp, ky = _ptr(y, np.float64)
+    yp, ky = _out_ptr(y)
     st = mcf_stats()
     kw.setdefault("precision", MCF_F64)
     p, kc = _params(coeffs, walks_per_node=int(walks_per_row), stream=kw.pop("stream", None) or _stream_of(v, nodes, y),
@@ -346,7 +361,7 @@ def _query_struct(q):
     out = q.get("out")
     if out is None:
         out = _output(None, m, q.get("device_out"))
-    op, ko = _ptr(out, np.float64)
+    op, ko = _out_ptr(out)
     vp, kv = _ptr(q.get("v"), np.float64)
     npt, kn = _ptr(nodes, np.int64)
     pkw = {k: q[k] for k in ("scale", "n_walks", "walks_per_node", "w_cutoff", "seed", "request_id", "precision")
@@ -468,7 +483,7 @@ def mcf_total_communicability_noalloc(n, row_ptr, col_idx, coeffs, out, **kw):
     """f(A')1 with no device allocation by the library; CSR and ``out`` must be CUDA tensors."""
     rp, krp = _ptr(row_ptr, np.int64)
     ci, kci = _ptr(col_idx, np.int32)
-    yp, ky = _ptr(out, np.float64)
+    yp, ky = _out_ptr(out)
     nnz = int(col_idx.numel()) if _is_torch(col_idx) else len(col_idx)
     p, kc = _params(coeffs, stream=kw.pop("stream", None) or _stream_of(out), **kw)
     _check(load().mcf_total_communicability_noalloc(int(n), nnz, rp, ci, ctypes.byref(p), yp))

@@ -98,3 +98,22 @@ def test_no_device_means_an_error_not_a_fallback(lib):
     with pytest.raises(M.McfError) as ei:
         M.mcf_create_graph(2, rp, ci)
     assert ei.value.status == 4 and "CUDA" in str(ei.value)
+
+
+def test_outputs_must_be_float64_contiguous():
+    """The library writes results in place: an output of another dtype or a
+    strided view is refused (a converted copy would silently take the results)."""
+    import types
+
+    import numpy as np
+    import torch
+
+    g = types.SimpleNamespace(n=4, handle=None)
+    for bad in (np.zeros(4, np.float32), np.zeros(8)[::2], torch.zeros(4, dtype=torch.float32),
+                torch.zeros(8, dtype=torch.float64)[::2]):
+        with pytest.raises(TypeError):
+            M.mcf_total_communicability(g, [1.0, 1.0, 0.5], out=bad, n_walks=10)
+    ro = np.zeros(4)
+    ro.flags.writeable = False
+    with pytest.raises(TypeError):
+        M.mcf_subgraph_centrality(g, [1.0, 1.0, 0.5], out=ro, n_walks=10)
