@@ -30,10 +30,16 @@
  *   - Every call returns an mcf_status; nothing aborts or throws across the
  *     ABI.  mcf_last_error() returns a thread-local message for the last
  *     failing call of this thread.
- *   - Random numbers: one Philox4x32-10 block (Salmon et al., SC'11) per walk
- *     transition, key = (seed low, seed high), counter = (step, walk id low,
- *     walk id high, request_id).  The same seed gives the same walks on every
- *     run and every launch configuration.
+ *   - Random numbers: Philox4x32-10 (Salmon et al., SC'11) with key =
+ *     (seed low, seed high) and counter = (b, walk id low, walk id high,
+ *     request_id), where b numbers the blocks of one walk.  A transition out
+ *     of a row of a binary matrix uses one 32-bit word: transition k takes
+ *     word k mod 4 of block b = floor(k / 4).  A transition out of a row of a
+ *     weighted matrix uses two words (alias bucket and acceptance test):
+ *     transition k takes words 2 (k mod 2) and 2 (k mod 2) + 1 of block
+ *     b = floor(k / 2).  Walk ids are the exclusive prefix of N_i over the
+ *     nodes (the classical method of Algorithm 1: i * N + s).  The same seed
+ *     gives the same walks on every run and every launch configuration.
  */
 #ifndef MCF_H
 #define MCF_H
@@ -284,6 +290,12 @@ typedef struct {
     int64_t walk_steps;        /* over completed requests                          */
     double p50_ms, p99_ms, max_ms, mean_ms;  /* latency submit -> result ready      */
     double busy_s;             /* wall time from the first submit to the last completion */
+    /* Device windows of the completed batches (the GPU's global timer read by
+     * a kernel before a batch's first kernel and after its last one): the
+     * time during which two or more batches' work was on the device, and the
+     * largest number of batches whose windows overlapped at once. */
+    double device_overlap_ms;
+    int64_t max_concurrent_batches;
 } mcf_server_stats;
 
 /* Starts a request server on the current device: a scheduler thread that
@@ -297,12 +309,29 @@ typedef struct {
  * Errors: MCF_ERR_INVALID_ARG (zero budget, max_inflight < 1), MCF_ERR_CUDA. */
 mcf_status mcf_server_create(const mcf_server_config* config, mcf_server_t* out);
 
+/* Device memory a request may take: the buffers mcf_batch_create allocates
+ * for a batch holding only *query (for queries that batches run through the
+ * single-query path, a bound on that path's scratch).  The server admits
+ * requests while the sum of these over the requests in flight fits its
+ * budget.  Errors: MCF_ERR_INVALID_ARG (as mcf_batch_create would refuse the
+ * query), MCF_ERR_CUDA. */
+mcf_status mcf_query_footprint(const mcf_query* query, size_t* bytes);
+
+/* Device memory a batch plan holds (every buffer mcf_batch_create allocated). */
+mcf_status mcf_batch_device_bytes(mcf_batch_t batch, size_t* bytes);
+
 /* Queues a copy of *query (its arrays must stay valid until the request
  * completes) and returns a ticket.  A request whose footprint alone exceeds
- * the budget completes immediately with MCF_ERR_ADMISSION.  Completed
- * requests stay listed, so every ticket can be polled or waited on again,
- * until mcf_server_destroy releases them. */
+ * the budget completes immediately with MCF_ERR_ADMISSION; a query the batch
+ * planner would refuse returns MCF_ERR_INVALID_ARG and gets no ticket.
+ * Completed requests stay listed, so every ticket can be polled or waited on
+ * again, until mcf_server_release or mcf_server_destroy releases them. */
 mcf_status mcf_server_submit(mcf_server_t s, const mcf_query* query, uint64_t* ticket);
+
+/* Forgets a completed request (its ticket becomes unknown), so a long-running
+ * server does not keep every request it ever served.
+ * Errors: MCF_ERR_INVALID_ARG (unknown ticket, or not completed yet). */
+mcf_status mcf_server_release(mcf_server_t s, uint64_t ticket);
 
 /* *done = 1 once the ticket's result is in query->out; *result is its status. */
 mcf_status mcf_server_poll(mcf_server_t s, uint64_t ticket, int32_t* done, mcf_status* result);
@@ -326,29 +355,52 @@ mcf_status mcf_server_destroy(mcf_server_t s);
 #define MCF_NOALLOC_MAX_WALKS (1LL << 25)
 
 /* Total communicability f(A')1 for callers that cannot allocate device
- * memory -- for example code running inside a memory pool or a framework that
- * owns every device allocation, a pre-captured CUDA graph, or a process whose
- * allocator is already exhausted.  The paper has no counterpart: this is the
- * same computation as mcf_total_communicability (same walks, same result),
- * but the library allocates nothing.  Its scratch is one file-scope device
- * array of about 17 MB that every GPU loading libmcf holds until the process
- * exits; the caller passes inputs and output:
+ * memory -- for example code running inside a framework that owns every
+ * device allocation, or a process whose allocator is already exhausted.  The
+ * paper has no counterpart: this is the same computation as
+ * mcf_total_communicability (same walks, same result), but the library
+ * allocates nothing.  Its scratch is one file-scope device array of about
+ * 17 MB that every GPU loading libmcf holds until the process exits; the
+ * caller passes inputs and output:
  *   n, nnz           matrix size, n <= MCF_NOALLOC_MAX_NODES, nnz < 2^32;
  *   row_ptr, col_idx device pointers to a binary symmetric CSR (int64[n+1],
  *                    int32[nnz]); range and order are checked on the device
- *                    (MCF_ERR_INVALID_GRAPH), symmetry is the caller's duty;
+ *                    (MCF_ERR_INVALID_GRAPH, y left unchanged), symmetry is
+ *                    the caller's duty;
  *   params           as for mcf_total_communicability; the walk count (N_s + n,
  *                    or walks_per_node * n) must not exceed MCF_NOALLOC_MAX_WALKS;
  *   y                device pointer to float64[n].
  * Sizes beyond the limits return MCF_ERR_INVALID_ARG with the limit in
- * mcf_last_error().  The first call on a device looks up the array's device
- * address (with that device current), so make it before any stream capture.
- * Every call uses the same array and clears what must start at zero; calls
- * that overlap on the GPU (other streams, other threads) race on it and must
- * be serialised by the caller.  The call returns after its work is enqueued
- * on params->stream (after one short synchronisation for the CSR check). */
+ * mcf_last_error(), before any device work.  The first call on a device looks
+ * up the array's device address (with that device current) and keeps it for
+ * the life of the process, so make that first call before any stream capture,
+ * and do not use the library across a cudaDeviceReset.  Every call uses the
+ * same array and clears what must start at zero; calls that overlap on the
+ * GPU (other streams, other threads) race on it and must be serialised by the
+ * caller.  The call returns after its work is enqueued on params->stream
+ * (after one short synchronisation for the CSR check). */
 mcf_status mcf_total_communicability_noalloc(int64_t n, int64_t nnz, const int64_t* row_ptr, const int32_t* col_idx,
                                              const mcf_params* params, double* y);
+
+/* ------------------------------------------------------------ measurement */
+
+/* Measurement helpers; the paper has no counterpart.  A walk step reads one
+ * record at a random position of an array of per-entry records, so the rate
+ * at which this GPU serves random 8-byte reads bounds the walk kernels.
+ * mcf_gather_probe allocates a device array of array_bytes (< 32 GiB), makes
+ * about `reads` independent 8-byte reads at uniform random positions of it
+ * (256-thread blocks, 2048 threads per SM, 16 reads in flight per thread,
+ * L2 fetch granularity as the walk kernels use), times the launch with CUDA
+ * events on `stream` after one warm-up launch, frees the array and returns
+ * the reads per second.
+ * Errors: MCF_ERR_INVALID_ARG, MCF_ERR_OOM, MCF_ERR_CUDA. */
+mcf_status mcf_gather_probe(int64_t array_bytes, int64_t reads, void* stream, double* reads_per_s);
+
+/* Number of kernel executions of this library on the current device since
+ * the library was loaded: every kernel's first thread of block (0, 0, 0)
+ * counts its own execution, so a replayed CUDA graph counts again.
+ * Synchronises with the device (the counters are read back). */
+mcf_status mcf_kernel_launches(uint64_t* count);
 
 /* Thread-local description of the last error of this thread ("" if none). */
 const char* mcf_last_error(void);

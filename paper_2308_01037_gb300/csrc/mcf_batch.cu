@@ -59,6 +59,8 @@ struct BQuery {
     const uint2* eod;
     const double* diag;
     const int64_t* nodes;  // SC subset (device) or null
+    const int64_t* sub_ptr;   // SC subset: per-column lists of the requested rows (SubList)
+    const int32_t* sub_row;
     double* out;           // device output
     const double* zeta;    // K + 1 coefficients (device)
     const float* zf;       // the same, rounded to float32 (the walk kernels' precision)
@@ -87,6 +89,7 @@ __device__ __forceinline__ int find_le(const int64_t* __restrict__ a, int m, int
 // ||C'_i|| and per-query partial sums with exactly the partition and order of
 // the single-query colnorm kernel (block b of query q = blockIdx.x of that grid).
 __global__ void bq_colnorm(const BQuery* __restrict__ desc, double* __restrict__ colnorm, double* __restrict__ part) {
+    MCF_KERNEL_ENTRY();
     const BQuery& d = desc[blockIdx.y];
     double s = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < d.n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -99,6 +102,7 @@ __global__ void bq_colnorm(const BQuery* __restrict__ desc, double* __restrict__
 }
 
 __global__ void bq_sum(const double* __restrict__ part, int nb, double* __restrict__ tot) {
+    MCF_KERNEL_ENTRY();
     double s = 0.0;
     const double* p = part + (int64_t)blockIdx.x * nb;
     for (int b = threadIdx.x; b < nb; b += blockDim.x) s += p[b];
@@ -109,6 +113,7 @@ __global__ void bq_sum(const double* __restrict__ part, int nb, double* __restri
 __global__ void bq_alloc(const BQuery* __restrict__ desc, const int64_t* __restrict__ qoff, int Q, int64_t NT,
                          const double* __restrict__ colnorm, const double* __restrict__ tot,
                          const uint8_t* __restrict__ need, int64_t* __restrict__ nw, int64_t* __restrict__ flag) {
+    MCF_KERNEL_ENTRY();
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < NT; u += (int64_t)gridDim.x * blockDim.x) {
         const int q = find_le(qoff, Q, u);
         const BQuery& d = desc[q];
@@ -130,6 +135,7 @@ __global__ void bq_alloc(const BQuery* __restrict__ desc, const int64_t* __restr
 // whole 32-walk chunks, so no chunk mixes two queries.
 __global__ void bq_bases(BQuery* __restrict__ desc, int Q, int Q_tc, int64_t NT, const int64_t* __restrict__ gw,
                          int64_t* __restrict__ wbase, unsigned long long* __restrict__ counters) {
+    MCF_KERNEL_ENTRY();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const int64_t total = (int64_t)counters[BC_TOTAL];
     int64_t base = 0;
@@ -154,6 +160,7 @@ __global__ void bq_bases(BQuery* __restrict__ desc, int Q, int Q_tc, int64_t NT,
 
 __global__ void bq_starts_tc(const int64_t* __restrict__ flag, const int64_t* __restrict__ spos, int64_t NT_tc,
                              unsigned long long* __restrict__ counters) {
+    MCF_KERNEL_ENTRY();
     if (threadIdx.x == 0 && blockIdx.x == 0)
         counters[BC_STARTS_TC] = NT_tc > 0 ? (unsigned long long)(spos[NT_tc - 1] + flag[NT_tc - 1]) : 0ull;
 }
@@ -161,6 +168,7 @@ __global__ void bq_starts_tc(const int64_t* __restrict__ flag, const int64_t* __
 __global__ void bq_compact(const BQuery* __restrict__ desc, const int64_t* __restrict__ qoff, int Q, int Q_tc,
                            int64_t NT, const int64_t* __restrict__ flag, const int64_t* __restrict__ spos,
                            const int64_t* __restrict__ gw, uint32_t* __restrict__ starts, int64_t* __restrict__ soff) {
+    MCF_KERNEL_ENTRY();
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < NT; u += (int64_t)gridDim.x * blockDim.x) {
         if (!flag[u]) continue;
         const int q = find_le(qoff, Q, u);
@@ -174,6 +182,7 @@ __global__ void bq_compact(const BQuery* __restrict__ desc, const int64_t* __res
 __global__ void bq_chunks(const uint32_t* __restrict__ starts, const int64_t* __restrict__ soff,
                           const int64_t* __restrict__ nw, const unsigned long long* __restrict__ counters,
                           uint32_t* __restrict__ chunk_s0) {
+    MCF_KERNEL_ENTRY();
     const int64_t S = (int64_t)counters[BC_STARTS_TC];
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < S; s += (int64_t)gridDim.x * blockDim.x) {
         const int64_t c0 = (soff[s] + B_CHUNK - 1) / B_CHUNK;
@@ -185,6 +194,7 @@ __global__ void bq_chunks(const uint32_t* __restrict__ starts, const int64_t* __
 // rm_q[d] = float(gamma_q * d): r_l and the weight multiplier of a state of degree d.
 __global__ void bq_degree_tables(const BQuery* __restrict__ desc, const int64_t* __restrict__ rmoff, int Q_tc,
                                  int64_t total, float* __restrict__ rm) {
+    MCF_KERNEL_ENTRY();
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
         const int q = find_le(rmoff, Q_tc, t);
         rm[t] = __double2float_rn(__dmul_rn(desc[q].gamma, (double)(t - rmoff[q])));
@@ -194,6 +204,7 @@ __global__ void bq_degree_tables(const BQuery* __restrict__ desc, const int64_t*
 // Node records of the SC queries' nodes (float32 multiplier gamma * deg).
 __global__ void bq_records(const BQuery* __restrict__ desc, const int64_t* __restrict__ qoff, int Q, int64_t u0,
                            int64_t NT, Rec<false>* __restrict__ rec) {
+    MCF_KERNEL_ENTRY();
     for (int64_t u = u0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < NT; u += (int64_t)gridDim.x * blockDim.x) {
         const int q = find_le(qoff, Q, u);
         const BQuery& d = desc[q];
@@ -208,13 +219,12 @@ __global__ void bq_records(const BQuery* __restrict__ desc, const int64_t* __res
     }
 }
 
-__global__ void bq_mark(const BQuery* __restrict__ desc, int q0, int Q, uint8_t* __restrict__ need,
-                        uint8_t* __restrict__ want) {
+__global__ void bq_mark(const BQuery* __restrict__ desc, int q0, int Q, uint8_t* __restrict__ need) {
+    MCF_KERNEL_ENTRY();
     const BQuery& d = desc[q0 + blockIdx.y];
     if (!d.subset) return;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < d.n_out; t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = d.nodes[t];
-        want[d.node_off + i] = 1;
         for (int64_t p = d.rp[i]; p < d.rp[i + 1]; ++p) need[d.node_off + d.col[p]] = 1;
     }
 }
@@ -243,6 +253,7 @@ __global__ void __launch_bounds__(256, MINB) bwalk_tc_kernel(
     const BQuery* __restrict__ desc, int Q_tc, const float* __restrict__ rm_all, const int64_t* __restrict__ rmoff,
     const uint32_t* __restrict__ starts, const int64_t* __restrict__ soff, const uint32_t* __restrict__ chunk_s0,
     const int64_t* __restrict__ wbase, int grab, double* __restrict__ acc, unsigned long long* __restrict__ counters) {
+    MCF_KERNEL_ENTRY();
     double* const acc2 = nullptr;   // batches estimate no standard errors
     __shared__ WarpQuery wq[256 / 32];
     __shared__ WalkResults<float2> rbuf[256 / 32];
@@ -399,7 +410,7 @@ struct CtaQuery {
     const int32_t* col;
     const int64_t* cp;
     const int32_t* ri;
-    const uint8_t* want;
+    SubList sub;
     const Rec<false>* rec;
     double* dacc;
     int64_t n;
@@ -440,7 +451,7 @@ __device__ void bdiag_start(const CtaQuery& cq, DiagTable& t, uint32_t k0, int64
         }
         if (!__syncthreads_or(stopped)) break;
         __threadfence_block();
-        diag_apply<DENSE>(t, k0, Nk, cq.cp, cq.ri, nullptr, cq.want, cq.gamma, cq.dacc);
+        diag_apply<DENSE>(t, k0, Nk, cq.cp, cq.ri, nullptr, cq.sub, cq.gamma, cq.dacc);
         __syncthreads();
         diag_clear<DENSE>(t, cq.n);
         __syncthreads();
@@ -448,7 +459,7 @@ __device__ void bdiag_start(const CtaQuery& cq, DiagTable& t, uint32_t k0, int64
         __syncthreads();
     }
     __threadfence_block();
-    diag_apply<DENSE>(t, k0, Nk, cq.cp, cq.ri, nullptr, cq.want, cq.gamma, cq.dacc);
+    diag_apply<DENSE>(t, k0, Nk, cq.cp, cq.ri, nullptr, cq.sub, cq.gamma, cq.dacc);
     __syncthreads();
     diag_clear<DENSE>(t, cq.n);
     __syncthreads();
@@ -458,8 +469,9 @@ __device__ void bdiag_start(const CtaQuery& cq, DiagTable& t, uint32_t k0, int64
 __global__ void __launch_bounds__(256) bwalk_diag_kernel(
     const BQuery* __restrict__ desc, const int64_t* __restrict__ qoff, int Q, const uint32_t* __restrict__ starts,
     const int64_t* __restrict__ soff, const int64_t* __restrict__ nw, const Rec<false>* __restrict__ rec_sc,
-    int64_t sc_node0, uint8_t* __restrict__ want_sc, int cap_log2, int64_t region, double* __restrict__ qval,
+    int64_t sc_node0, int cap_log2, int64_t region, double* __restrict__ qval,
     double* __restrict__ dacc, unsigned long long* __restrict__ counters) {
+    MCF_KERNEL_ENTRY();
     extern __shared__ int32_t smem_i[];
     __shared__ CtaQuery cq;
     __shared__ int64_t cur;
@@ -486,7 +498,7 @@ __global__ void __launch_bounds__(256) bwalk_diag_kernel(
             cq.col = d.col;
             cq.cp = d.cp;
             cq.ri = d.ri;
-            cq.want = d.subset ? want_sc + (d.node_off - sc_node0) : nullptr;
+            cq.sub = SubList{d.subset ? d.sub_ptr : nullptr, d.sub_row, nullptr};
             cq.rec = rec_sc + (d.node_off - sc_node0);
             cq.dacc = dacc + d.node_off;
             cq.n = d.n;
@@ -525,8 +537,19 @@ __global__ void __launch_bounds__(256) bwalk_diag_kernel(
     }
 }
 
+// Device time (the global nanosecond timer) when this kernel runs: one
+// at the start and one at the end of a batch's device work bound the window
+// in which that work ran.
+__global__ void stamp_kernel(unsigned long long* __restrict__ slot) {
+    MCF_KERNEL_ENTRY();
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    *slot = t;
+}
+
 // ---------------------------------------------------------------- epilogues
 __global__ void bq_finalize(int64_t NT_tc, double* __restrict__ acc, const int64_t* __restrict__ nw) {
+    MCF_KERNEL_ENTRY();
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < NT_tc; u += (int64_t)gridDim.x * blockDim.x)
         acc[u] = nw[u] > 0 ? acc[u] / (double)nw[u] : 0.0;
 }
@@ -536,6 +559,7 @@ __global__ void bq_finalize(int64_t NT_tc, double* __restrict__ acc, const int64
 // d = zeta_0 + zeta_1 gamma a_ii + sum_k a'_ik <Q_k, C'_i>.
 __global__ void bq_epilogue(const BQuery* __restrict__ desc, const int64_t* __restrict__ boff, int Q,
                             int64_t n_blocks, const double* __restrict__ acc) {
+    MCF_KERNEL_ENTRY();
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -565,6 +589,8 @@ __global__ void bq_epilogue(const BQuery* __restrict__ desc, const int64_t* __re
 }  // namespace mcf
 
 using namespace mcf;
+
+uint64_t mcf::kernel_runs_batch() { return this_unit_kernel_runs(); }
 
 // ====================================================================== host
 struct BatchTuning {
@@ -600,7 +626,7 @@ struct mcf_batch {
     uint32_t *starts = nullptr, *chunk_s0 = nullptr;
     float* rm = nullptr;
     Rec<false>* rec_sc = nullptr;
-    uint8_t *need = nullptr, *want = nullptr;
+    uint8_t* need = nullptr;
     unsigned long long* counters = nullptr;
     void* scan_tmp = nullptr;
     size_t scan_bytes = 0;
@@ -610,6 +636,9 @@ struct mcf_batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int device = 0;
+    size_t bytes = 0;                         // device memory the plan holds
+    unsigned long long* stamps = nullptr;     // device: global-timer ns at the start and end of the last run
+    unsigned long long window[2] = {0, 0};    // host copy of the last run's stamps
 };
 
 template <class T>
@@ -620,8 +649,89 @@ static mcf_status balloc(mcf_batch* b, T** p, size_t count) {
         return fail(MCF_ERR_OOM, "device allocation for the batch failed");
     }
     b->bufs.push_back(q);
+    b->bytes += std::max<size_t>(count, 1) * sizeof(T);
     *p = static_cast<T*>(q);
     return MCF_OK;
+}
+
+// Launch shape of the fused diag kernel: threads per CTA follow the walks
+// per start, the hashed row holds about 16 visits per walk (2^10 .. 2^12
+// slots), and the per-CTA region of Q_k values spans the largest dense row
+// (graphs up to B_DENSE_MAX nodes) or the hash.
+struct DiagShape {
+    int cap_log2 = 10;
+    int threads = 256;
+    size_t smem = 0;
+    int64_t region = 0;
+    int grid = 0;
+};
+
+static mcf_status diag_shape(int64_t nk_hint, bool any_hash, int64_t dense_max, DiagShape* sh) {
+    sh->cap_log2 = 10;
+    if (any_hash) {
+        const int64_t want_slots = std::max<int64_t>(16 * nk_hint, 1024);
+        while (sh->cap_log2 < 12 && ((int64_t)1 << sh->cap_log2) < want_slots) ++sh->cap_log2;
+    }
+    sh->region = std::max<int64_t>(dense_max, (int64_t)1 << sh->cap_log2);
+    sh->smem = ((size_t)1 << sh->cap_log2) * 2 * sizeof(int32_t);
+    sh->threads = nk_hint <= 64 ? 64 : (nk_hint <= 128 ? 128 : 256);
+    if (cudaFuncSetAttribute(bwalk_diag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh->smem) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return fail(MCF_ERR_CUDA, "diag kernel shared memory");
+    }
+    sh->grid = persistent_grid(bwalk_diag_kernel, sh->threads, sh->smem);
+    return MCF_OK;
+}
+
+// Walks per start of a subgraph-centrality query, the hint that sizes its
+// CTAs and hashed rows.
+static int64_t sc_walk_hint(const mcf_params& p, int64_t n) {
+    return p.walks_per_node > 0 ? p.walks_per_node : std::max<int64_t>(1, p.n_walks / std::max<int64_t>(n, 1));
+}
+
+// Device memory a batch holding only query q allocates (mcf_batch_create's
+// buffers for one fused query, or a bound on the single-query path's
+// stream-ordered scratch for the other kinds); the request server admits by
+// the sum of these over the requests in flight.
+static int64_t query_footprint(const mcf_query& q, int64_t* out) {
+    const mcf_graph* g = q.graph;
+    const mcf_params& p = q.params;
+    const int64_t n = g->n, nnz = g->nnz, md = g->max_degree;
+    const int64_t walks = p.walks_per_node > 0 ? p.walks_per_node * n : p.n_walks + n;
+    const bool binary32 = !g->weighted && p.precision == MCF_F32W_F64ACC && nnz < ((int64_t)1 << 32);
+    const bool tc_kind = q.kind == MCF_QUERY_TOTAL_COMMUNICABILITY || q.kind == MCF_QUERY_KATZ;
+    const bool sc_kind = q.kind == MCF_QUERY_SUBGRAPH_CENTRALITY;
+    const int64_t tc_walks = p.walks_per_node > 0 ? p.walks_per_node * n : p.n_walks;
+    const bool host_out = !is_device_ptr(q.out);
+    const int64_t m = (sc_kind && q.nodes) ? q.n_nodes : n;
+    // subset lists: claim, count and pointer arrays, their scan, one row index per pair
+    const int64_t pairs = (sc_kind && q.nodes) ? std::min<int64_t>(nnz, m * md) : 0;
+    const int64_t lists = (sc_kind && q.nodes) ? 24 * n + 8 + (int64_t)scan_tmp_bytes(n) + 4 * std::max<int64_t>(pairs, 1)
+                                                     + (!is_device_ptr(q.nodes) ? 8 * m : 0)
+                                               : 0;
+    int64_t b = 16 + 4096;   // stamps, descriptor and offsets
+    if ((tc_kind && binary32 && tc_walks < B_FUSED_MAX_WALKS) || (sc_kind && binary32)) {
+        b += 60 * n + 8 + 8 * B_RED_BLOCKS + 8 + BC_N * 8 + 12 * MCF_MAX_COEFFS + (int64_t)scan_tmp_bytes(n);
+        if (tc_kind) {
+            b += 4 * (walks / B_CHUNK + 3) + 4 * (md + 1) + 4;
+        } else {
+            DiagShape sh;
+            if (diag_shape(sc_walk_hint(p, n), n > B_DENSE_MAX, n <= B_DENSE_MAX ? n : 0, &sh) != MCF_OK) return -1;
+            b += 17 * n + 8 + (int64_t)sh.grid * sh.region * 8 + lists;
+        }
+        if (host_out) b += 8 * m;
+    } else {
+        // the single-query path: per-node preparation (about 130 bytes per
+        // node with both precisions' records), chunk table, degree table,
+        // outputs and inputs staged from the host, and for subgraph
+        // centrality its accumulators and hashed or dense rows Q_k (at most
+        // 4864 CTAs x 16384 float64 values)
+        b += 200 * n + 4 * (walks / 32 + 3) + 4 * (md + 1) + (int64_t)scan_tmp_bytes(n) + 8 * MCF_MAX_COEFFS;
+        if (sc_kind) b += 9 * n + lists + (int64_t)4864 * 16384 * 8;
+    }
+    *out = b;
+    return b;
 }
 
 static mcf_status check_query(const mcf_query& q, int idx) {
@@ -633,6 +743,10 @@ static mcf_status check_query(const mcf_query& q, int idx) {
     if (q.kind != MCF_QUERY_KATZ && (!p.coeffs || p.n_coeffs < 1 || p.n_coeffs > MCF_MAX_COEFFS))
         return fail(MCF_ERR_INVALID_ARG, where + "coeffs must hold 1.." + std::to_string(MCF_MAX_COEFFS) + " values");
     if (p.n_walks < 0 || p.walks_per_node < 0) return fail(MCF_ERR_INVALID_ARG, where + "walk counts must be >= 0");
+    // as the single calls: fewer than 2^36 walks, compared without overflow
+    const int64_t n = q.graph->n, lim = (int64_t)1 << 36;
+    if (p.walks_per_node > 0 ? (n > 0 && p.walks_per_node > lim / n) : p.n_walks > lim - n)
+        return fail(MCF_ERR_INVALID_ARG, where + "more than 2^36 walks per query");
     if (!(p.w_cutoff >= 0.0)) return fail(MCF_ERR_INVALID_ARG, where + "w_cutoff must be >= 0");
     if (p.precision != MCF_F64 && p.precision != MCF_F32W_F64ACC)
         return fail(MCF_ERR_INVALID_ARG, where + "unknown precision");
@@ -649,12 +763,11 @@ static mcf_status record(mcf_batch* b, cudaStream_t st) {
     MCF_CUDA_TRY(cudaMemsetAsync(b->acc, 0, (size_t)std::max<int64_t>(b->NT, 1) * sizeof(double), st));
     if (b->sc_nodes > 0) {
         MCF_CUDA_TRY(cudaMemsetAsync(b->need, 0, (size_t)b->sc_nodes, st));
-        MCF_CUDA_TRY(cudaMemsetAsync(b->want, 0, (size_t)b->sc_nodes, st));
     }
     if (b->NT == 0) return MCF_OK;
     const int Q = b->Q;
     if (Q > b->Q_tc)
-        bq_mark<<<dim3(64, Q - b->Q_tc), 256, 0, st>>>(b->desc, b->Q_tc, Q, b->need - b->NT_tc, b->want - b->NT_tc);
+        bq_mark<<<dim3(64, Q - b->Q_tc), 256, 0, st>>>(b->desc, b->Q_tc, Q, b->need - b->NT_tc);
     bq_colnorm<<<dim3(B_RED_BLOCKS, Q), B_RED_THREADS, 0, st>>>(b->desc, b->colnorm, b->part);
     bq_sum<<<Q, B_RED_THREADS, 0, st>>>(b->part, B_RED_BLOCKS, b->tot);
     bq_alloc<<<grid_for(b->NT, 256), 256, 0, st>>>(b->desc, b->qoff, Q, b->NT, b->colnorm, b->tot,
@@ -683,7 +796,7 @@ static mcf_status record(mcf_batch* b, cudaStream_t st) {
     if (Q > b->Q_tc) {
         bq_records<<<grid_for(b->sc_nodes, 256), 256, 0, st>>>(b->desc, b->qoff, Q, b->NT_tc, b->NT, b->rec_sc);
         bwalk_diag_kernel<<<b->diag_grid, b->diag_threads, b->diag_smem, st>>>(
-            b->desc, b->qoff, Q, b->starts, b->soff, b->nw, b->rec_sc, b->NT_tc, b->want, b->cap_log2, b->region,
+            b->desc, b->qoff, Q, b->starts, b->soff, b->nw, b->rec_sc, b->NT_tc, b->cap_log2, b->region,
             b->qval, b->acc, b->counters);
         MCF_CUDA_TRY(cudaGetLastError());
     }
@@ -746,7 +859,7 @@ static mcf_status autotune(mcf_batch* b, cudaStream_t st) {
     cudaEventCreate(&e1);
     float best = 1e30f;
     BatchTuning pick = b->tune;
-    ScopedL2Fetch fetch(walk_tuning().l2_fetch);
+    ScopedL2Fetch fetch(L2_FETCH_BYTES);
     for (const BatchTuning& c : cands) {
         b->tune = c;
         MCF_TRY(record(b, st));   // warm
@@ -768,7 +881,29 @@ static mcf_status autotune(mcf_batch* b, cudaStream_t st) {
     return MCF_OK;
 }
 
+void mcf::batch_window(const mcf_batch* b, uint64_t* begin_ns, uint64_t* end_ns) {
+    *begin_ns = b->window[0];
+    *end_ns = b->window[1];
+}
+
 extern "C" {
+
+mcf_status mcf_query_footprint(const mcf_query* q, size_t* bytes) {
+    set_error("");
+    if (!q || !bytes) return fail(MCF_ERR_INVALID_ARG, "NULL argument");
+    MCF_TRY(check_query(*q, 0));
+    int64_t b = 0;
+    if (query_footprint(*q, &b) < 0) return MCF_ERR_CUDA;
+    *bytes = (size_t)b;
+    return MCF_OK;
+}
+
+mcf_status mcf_batch_device_bytes(mcf_batch_t b, size_t* bytes) {
+    set_error("");
+    if (!b || !bytes) return fail(MCF_ERR_INVALID_ARG, "NULL argument");
+    *bytes = b->bytes;
+    return MCF_OK;
+}
 
 mcf_status mcf_batch_destroy(mcf_batch_t b) {
     if (!b) return MCF_OK;
@@ -795,6 +930,10 @@ mcf_status mcf_batch_create(const mcf_query* queries, int32_t n_queries, uint32_
         return s;
     };
     cudaGetDevice(&b->device);
+    {
+        mcf_status rs = balloc(b, &b->stamps, 2);
+        if (rs != MCF_OK) return bail(rs);
+    }
     b->queries.assign(queries, queries + n_queries);
     b->params.resize(n_queries);
     b->coeffs.resize(n_queries);
@@ -893,9 +1032,7 @@ mcf_status mcf_batch_create(const mcf_query* queries, int32_t n_queries, uint32_
                 const int64_t mw = p.walks_per_node > 0 ? p.walks_per_node * g->n : p.n_walks + g->n;
                 max_chunks += mw / B_CHUNK + 2;
             } else {
-                const int64_t hint = p.walks_per_node > 0 ? p.walks_per_node
-                                                          : std::max<int64_t>(1, p.n_walks / std::max<int64_t>(g->n, 1));
-                nk_hint = std::max(nk_hint, hint);
+                nk_hint = std::max(nk_hint, sc_walk_hint(p, g->n));
                 if (x.dense) dense_max = std::max(dense_max, g->n);
                 else any_hash = true;
             }
@@ -913,18 +1050,14 @@ mcf_status mcf_batch_create(const mcf_query* queries, int32_t n_queries, uint32_
         if (b->NT >= ((int64_t)1 << 32)) return bail(fail(MCF_ERR_INVALID_ARG, "a batch spans at most 2^32 nodes"));
         // diag launch shape
         if (b->Q > b->Q_tc) {
-            b->cap_log2 = 10;
-            if (any_hash) {
-                const int64_t want_slots = std::max<int64_t>(16 * nk_hint, 1024);
-                while (b->cap_log2 < 12 && ((int64_t)1 << b->cap_log2) < want_slots) ++b->cap_log2;
-            }
-            b->region = std::max<int64_t>(dense_max, (int64_t)1 << b->cap_log2);
-            b->diag_smem = ((size_t)1 << b->cap_log2) * 2 * sizeof(int32_t);
-            b->diag_threads = nk_hint <= 64 ? 64 : (nk_hint <= 128 ? 128 : 256);
-            if (cudaFuncSetAttribute(bwalk_diag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)b->diag_smem) != cudaSuccess)
-                return bail(fail(MCF_ERR_CUDA, "diag kernel shared memory"));
-            b->diag_grid = persistent_grid(bwalk_diag_kernel, b->diag_threads, b->diag_smem);
+            DiagShape sh;
+            mcf_status rs = diag_shape(nk_hint, any_hash, dense_max, &sh);
+            if (rs != MCF_OK) return bail(rs);
+            b->cap_log2 = sh.cap_log2;
+            b->region = sh.region;
+            b->diag_smem = sh.smem;
+            b->diag_threads = sh.threads;
+            b->diag_grid = sh.grid;
         }
         b->tc_grid[0] = persistent_grid(bwalk_tc_kernel<5>, 256, 0);
         b->tc_grid[1] = persistent_grid(bwalk_tc_kernel<6>, 256, 0);
@@ -957,7 +1090,6 @@ mcf_status mcf_batch_create(const mcf_query* queries, int32_t n_queries, uint32_
         A(&b->zf, (size_t)b->Q * MCF_MAX_COEFFS);
         A(&b->rec_sc, b->sc_nodes);
         A(&b->need, b->sc_nodes);
-        A(&b->want, b->sc_nodes);
         b->scan_bytes = scan_tmp_bytes(b->NT);
         A((char**)&b->scan_tmp, b->scan_bytes);
         if (b->Q > b->Q_tc) A(&b->qval, (size_t)b->diag_grid * (size_t)b->region);
@@ -983,6 +1115,8 @@ mcf_status mcf_batch_create(const mcf_query* queries, int32_t n_queries, uint32_
                     if (q.nodes[t] < 0 || q.nodes[t] >= q.graph->n)
                         return bail(fail(MCF_ERR_INVALID_ARG, "query " + std::to_string(i) + ": node out of range"));
                 if (is_device_ptr(q.nodes)) {
+                    if ((rc = check_nodes_on_device(q.nodes, q.n_nodes, q.graph->n, st)) != MCF_OK)
+                        return bail(fail(rc, "query " + std::to_string(i) + ": " + get_error()));
                     d[f].nodes = q.nodes;
                 } else {
                     int64_t* nd;
@@ -990,6 +1124,15 @@ mcf_status mcf_batch_create(const mcf_query* queries, int32_t n_queries, uint32_
                     cudaMemcpyAsync(nd, q.nodes, q.n_nodes * sizeof(int64_t), cudaMemcpyHostToDevice, st);
                     d[f].nodes = nd;
                 }
+                // per-column lists of the requested rows, built once: the
+                // subset's indices are read when the batch is planned
+                SubList sl{};
+                rc = build_subset_lists(q.graph, d[f].nodes, q.n_nodes, st, [&](void** p, size_t bytes) {
+                    return balloc(b, (char**)p, bytes);
+                }, &sl);
+                if (rc != MCF_OK) return bail(rc);
+                d[f].sub_ptr = sl.ptr;
+                d[f].sub_row = sl.row;
             }
             if (is_device_ptr(q.out)) {
                 d[f].out = q.out;
@@ -1010,8 +1153,8 @@ mcf_status mcf_batch_create(const mcf_query* queries, int32_t n_queries, uint32_
         if (flags & MCF_BATCH_AUTOTUNE) {
             if ((rc = autotune(b, st)) != MCF_OK) return bail(rc);
         } else {
-            b->tune.minb = walk_tuning().minb;
-            b->tune.grab = walk_tuning().grab;
+            b->tune.minb = WALK_MINB;
+            b->tune.grab = WALK_GRAB;
         }
         if (flags & MCF_BATCH_CUDA_GRAPH) {
             cudaStream_t cs;
@@ -1043,8 +1186,9 @@ mcf_status mcf_batch_run(mcf_batch_t b, void* stream, mcf_stats* stats) {
         cudaEventCreate(&e1);
         cudaEventRecord(e0, st);
     }
+    stamp_kernel<<<1, 1, 0, st>>>(b->stamps);
     if (b->Q > 0) {
-        ScopedL2Fetch fetch(walk_tuning().l2_fetch);
+        ScopedL2Fetch fetch(L2_FETCH_BYTES);
         if (b->exec) MCF_CUDA_TRY(cudaGraphLaunch(b->exec, st));
         else MCF_TRY(record(b, st));
     }
@@ -1086,6 +1230,9 @@ mcf_status mcf_batch_run(mcf_batch_t b, void* stream, mcf_stats* stats) {
         ms += (float)s1.kernel_ms;
         fl |= s1.flags;
     }
+    stamp_kernel<<<1, 1, 0, st>>>(b->stamps + 1);
+    MCF_CUDA_TRY(cudaGetLastError());
+    MCF_CUDA_TRY(cudaMemcpyAsync(b->window, b->stamps, sizeof(b->window), cudaMemcpyDeviceToHost, st));
     MCF_CUDA_TRY(cudaStreamSynchronize(st));
     if (stats) {
         stats->walks = walks;

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
 #include <type_traits>
 
 #include "mcf_internal.cuh"
@@ -439,36 +440,70 @@ __device__ int diag_walk_edge(const DiagTable& t, uint32_t k0, uint2 od0, int64_
     return -1;
 }
 
-// d_i += a'_ik <Q_k, C'_i> / N_k for the rows i of column k (warp per row),
-// read from the column-major copy of A (rp/col/val: column pointers, row
-// indices and values; for a symmetric A the row arrays themselves).
+// The requested rows of each column for a RandFunmDiag node subset S:
+// column k lists the nodes i in S with a_ik != 0 (row[ptr[k] .. ptr[k+1]))
+// and, for a weighted A, the entries a_ik (val).  Built from the rows of the
+// requested nodes, so the dot phase of a column costs sum over its listed
+// rows instead of a pass over the whole column.
+struct SubList {
+    const int64_t* ptr;   // n + 1, or null: no subset (every row of column k)
+    const int32_t* row;
+    const float* val;     // null for a binary A
+};
+
+// MCF_ERR_INVALID_ARG unless every nodes_dev[t] (device memory) lies in [0, n);
+// waits for the stream.
+mcf_status check_nodes_on_device(const int64_t* nodes_dev, int64_t m, int64_t n, cudaStream_t st);
+
+// Builds the SubList of the node subset nodes_dev[0..m) (device indices, in
+// range) of graph g on stream st; device memory comes from alloc.  Waits for
+// the stream once (the number of pairs sizes the lists).
+mcf_status build_subset_lists(const mcf_graph* g, const int64_t* nodes_dev, int64_t m, cudaStream_t st,
+                              const std::function<mcf_status(void**, size_t)>& alloc, SubList* out);
+
+// <Q_k, C'_i> / gamma summed over column i of A (rp/col/val: the
+// column-major copy; for a symmetric A the row arrays themselves), reduced
+// over the warp (every lane returns the sum).
+template <bool DENSE>
+__device__ __forceinline__ double diag_dot(const DiagTable& t, int32_t i, const int64_t* __restrict__ rp,
+                                           const int32_t* __restrict__ col, const float* __restrict__ val) {
+    const int lane = threadIdx.x & 31;
+    // Q_k is sparse: most lookups find nothing, and adding an exact zero
+    // changes no sum, so only nonzero entries reach the (narrow) float64
+    // pipe; the test is on the bit pattern, an integer operation
+    double dot = 0.0;
+    if (val) {
+        for (int64_t q = rp[i] + lane; q < rp[i + 1]; q += 32) {
+            const double qv = q_get<DENSE>(t, (uint32_t)col[q]);
+            if (__double_as_longlong(qv) != 0) dot += (double)val[q] * qv;
+        }
+    } else {
+        for (int64_t q = rp[i] + lane; q < rp[i + 1]; q += 32) {
+            const double qv = q_get<DENSE>(t, (uint32_t)col[q]);
+            if (__double_as_longlong(qv) != 0) dot += qv;
+        }
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, d);
+    return dot;
+}
+
+// d_i += a'_ik <Q_k, C'_i> / N_k for the rows i of column k (warp per row):
+// every row of the column (sub.ptr null; read from the column-major copy)
+// or only the rows the subset lists for column k.
 template <bool DENSE>
 __device__ __forceinline__ void diag_apply(const DiagTable& t, uint32_t k0, int64_t Nk, const int64_t* __restrict__ rp,
                                            const int32_t* __restrict__ col, const float* __restrict__ val,
-                                           const uint8_t* __restrict__ want, double gamma, double* __restrict__ dacc) {
+                                           const SubList& sub, double gamma, double* __restrict__ dacc) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    for (int64_t p = rp[k0] + wid; p < rp[k0 + 1]; p += nwarp) {
-        const int32_t i = col[p];
-        if (want && !want[i]) continue;
-        // Q_k is sparse: most lookups find nothing, and adding an exact zero
-        // changes no sum, so only nonzero entries reach the (narrow) float64
-        // pipe; the test is on the bit pattern, an integer operation
-        double dot = 0.0;
-        if (val) {
-            for (int64_t q = rp[i] + lane; q < rp[i + 1]; q += 32) {
-                const double qv = q_get<DENSE>(t, (uint32_t)col[q]);
-                if (__double_as_longlong(qv) != 0) dot += (double)val[q] * qv;
-            }
-        } else {
-            for (int64_t q = rp[i] + lane; q < rp[i + 1]; q += 32) {
-                const double qv = q_get<DENSE>(t, (uint32_t)col[q]);
-                if (__double_as_longlong(qv) != 0) dot += qv;
-            }
-        }
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) dot += __shfl_down_sync(0xffffffffu, dot, d);
+    const int64_t* lp = sub.ptr ? sub.ptr : rp;
+    const int32_t* lrow = sub.ptr ? sub.row : col;
+    const float* lval = sub.ptr ? sub.val : val;
+    for (int64_t p = lp[k0] + wid; p < lp[k0 + 1]; p += nwarp) {
+        const int32_t i = lrow[p];
+        const double dot = diag_dot<DENSE>(t, i, rp, col, val);
         if (lane == 0) {
-            const double aik = gamma * (val ? (double)val[p] : 1.0);
+            const double aik = gamma * (lval ? (double)lval[p] : 1.0);
             atomicAdd(&dacc[i], (aik * (gamma * dot)) / (double)Nk);
         }
     }

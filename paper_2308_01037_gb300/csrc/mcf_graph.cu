@@ -50,9 +50,7 @@ int num_sms() {
 // Three-phase exclusive scan: per-block totals, a single-block scan of the
 // totals, then per-block scans offset by the scanned totals.  The partition
 // is fixed, so the result does not depend on timing.
-constexpr int SCAN_THREADS = 512;
-constexpr int SCAN_ITEMS = 8;
-constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+// SCAN_THREADS, SCAN_ITEMS and SCAN_TILE are declared in mcf_internal.cuh.
 
 __device__ __forceinline__ int64_t warp_incl_scan(int64_t v) {
     const int lane = threadIdx.x & 31;
@@ -85,6 +83,7 @@ __device__ int64_t block_excl_scan(int64_t v, int64_t* total) {
 }
 
 __global__ void scan_block_totals(const int64_t* __restrict__ in, int64_t n, int64_t* __restrict__ tot) {
+    MCF_KERNEL_ENTRY();
     int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
     int64_t s = 0;
 #pragma unroll
@@ -96,6 +95,7 @@ __global__ void scan_block_totals(const int64_t* __restrict__ in, int64_t n, int
 }
 
 __global__ void scan_totals_single(int64_t* __restrict__ tot, int64_t nb, int64_t* __restrict__ total_out) {
+    MCF_KERNEL_ENTRY();
     int64_t carry = 0;
     for (int64_t b0 = 0; b0 < nb; b0 += SCAN_THREADS) {
         int64_t i = b0 + threadIdx.x;
@@ -110,6 +110,7 @@ __global__ void scan_totals_single(int64_t* __restrict__ tot, int64_t nb, int64_
 
 __global__ void scan_apply(const int64_t* __restrict__ in, int64_t* __restrict__ out, int64_t n,
                            const int64_t* __restrict__ tot) {
+    MCF_KERNEL_ENTRY();
     int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
     int64_t v[SCAN_ITEMS];
     int64_t s = 0;
@@ -127,7 +128,7 @@ __global__ void scan_apply(const int64_t* __restrict__ in, int64_t* __restrict__
     }
 }
 
-size_t scan_tmp_bytes(int64_t n) { return (size_t)((n + SCAN_TILE - 1) / SCAN_TILE + 1) * sizeof(int64_t); }
+size_t scan_tmp_bytes(int64_t n) { return scan_tmp_bytes_for(n); }
 
 mcf_status scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* total_dev, void* tmp, size_t tmp_bytes,
                     cudaStream_t st) {
@@ -168,6 +169,7 @@ __global__ void validate_rows(int64_t n, int64_t nnz, const int64_t* __restrict_
                               const float* __restrict__ val, uint32_t* __restrict__ bad,
                               unsigned long long* __restrict__ maxdeg, unsigned long long* __restrict__ loops,
                               double* __restrict__ diag, unsigned long long* __restrict__ sums) {
+    MCF_KERNEL_ENTRY();
     const int lane = threadIdx.x & 31;
     int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -221,6 +223,7 @@ __global__ void weighted_rows(int64_t n, const int64_t* __restrict__ rp, const i
                               const float* __restrict__ val, double* __restrict__ row_abs,
                               double* __restrict__ row_sq, WEntry* __restrict__ went, double* __restrict__ s_buf,
                               int32_t* __restrict__ small_buf, int32_t* __restrict__ large_buf) {
+    MCF_KERNEL_ENTRY();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int64_t b = rp[i], e = rp[i + 1];
@@ -265,6 +268,7 @@ __global__ void weighted_rows(int64_t n, const int64_t* __restrict__ rp, const i
 __global__ void spmv_f64_kernel(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                                 const float* __restrict__ val, const double* __restrict__ x, double* __restrict__ y,
                                 double beta) {
+    MCF_KERNEL_ENTRY();
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t base = warp * 32; base < n; base += nwarps * 32) {
@@ -302,6 +306,7 @@ __device__ double block_sum(double v) {
 // part[b] = (x . y, (x + y) . (x + y)) over block b's grid-stride share
 __global__ void power_partials(int64_t n, const double* __restrict__ x, const double* __restrict__ y,
                                double* __restrict__ part) {
+    MCF_KERNEL_ENTRY();
     double d = 0.0, q = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         double xi = x[i], yi = y[i];
@@ -315,6 +320,7 @@ __global__ void power_partials(int64_t n, const double* __restrict__ x, const do
 }
 
 __global__ void power_finish(const double* __restrict__ part, int nb, double* __restrict__ out) {
+    MCF_KERNEL_ENTRY();
     double d = 0.0, q = 0.0;
     for (int b = threadIdx.x; b < nb; b += blockDim.x) { d += part[2 * b]; q += part[2 * b + 1]; }
     d = block_sum(d);
@@ -325,17 +331,20 @@ __global__ void power_finish(const double* __restrict__ part, int nb, double* __
 // x <- (x + y) / norm
 __global__ void power_update(int64_t n, double* __restrict__ x, const double* __restrict__ y,
                              const double* __restrict__ stats) {
+    MCF_KERNEL_ENTRY();
     double inv = 1.0 / sqrt(stats[1]);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         x[i] = (x[i] + y[i]) * inv;
 }
 
 __global__ void fill_f64(int64_t n, double* __restrict__ x, double v) {
+    MCF_KERNEL_ENTRY();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         x[i] = v;
 }
 
 __global__ void max_f64(int64_t n, const double* __restrict__ x, unsigned long long* __restrict__ out) {
+    MCF_KERNEL_ENTRY();
     double m = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         m = fmax(m, x[i]);
@@ -348,6 +357,8 @@ __global__ void max_f64(int64_t n, const double* __restrict__ x, unsigned long l
 using namespace mcf;
 
 // ====================================================================== C ABI
+uint64_t mcf::kernel_runs_graph() { return this_unit_kernel_runs(); }
+
 extern "C" {
 
 const char* mcf_last_error(void) { return get_error(); }
@@ -357,6 +368,7 @@ const char* mcf_version(void) { return "mcf 0.1 (sm_103a)"; }
 // row order, each product and sum rounded on its own.
 __global__ void column_sq(int64_t n, const int64_t* __restrict__ cp, const float* __restrict__ cv,
                           double* __restrict__ out) {
+    MCF_KERNEL_ENTRY();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         double sq = 0.0;
         for (int64_t q = cp[i]; q < cp[i + 1]; ++q) {

@@ -161,11 +161,41 @@ __device__ __forceinline__ double warp_listed_row_sums(int64_t base, int64_t m, 
     return s;
 }
 
+// ---------------------------------------------------------------- kernel execution count
+// Every kernel of the library counts its own executions: its first thread
+// of block (0, 0, 0) adds one to a per-translation-unit device counter (a
+// CUDA graph replay counts again).  kernel_runs_<unit>() read the counters
+// of the current device; mcf_kernel_launches() returns their sum.
+static __device__ unsigned long long g_kernel_runs;
+#define MCF_KERNEL_ENTRY()                                                                              \
+    do {                                                                                                \
+        if ((blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x | threadIdx.y | threadIdx.z) == 0)     \
+            atomicAdd(&g_kernel_runs, 1ull);                                                            \
+    } while (0)
+static inline uint64_t this_unit_kernel_runs() {
+    unsigned long long v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_kernel_runs, sizeof(v)) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return v;
+}
+uint64_t kernel_runs_walk();
+uint64_t kernel_runs_batch();
+uint64_t kernel_runs_graph();
+uint64_t kernel_runs_probe();
+
 // ---------------------------------------------------------------- helpers (host)
 bool is_device_ptr(const void* p);
 int num_sms();
 
 // Exclusive scan of int64 values (in place allowed: out may equal in), n >= 0.
+// Its partition: tiles of SCAN_TILE values, one block of SCAN_THREADS each;
+// the scratch holds one total per tile plus one.
+constexpr int SCAN_THREADS = 512;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+constexpr size_t scan_tmp_bytes_for(int64_t n) { return (size_t)((n + SCAN_TILE - 1) / SCAN_TILE + 1) * sizeof(int64_t); }
 // Writes the total to *total_dev (device pointer) when non-null.  Deterministic.
 mcf_status scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* total_dev, void* tmp, size_t tmp_bytes,
                     cudaStream_t st);
@@ -177,7 +207,7 @@ mcf_status spmv_f64(const mcf_graph* g, const double* x, double* y, double beta,
 // Stream-ordered scratch allocation helpers.
 struct Scratch {
     cudaStream_t st;
-    void* ptrs[32];
+    void* ptrs[48];
     int n = 0;
     explicit Scratch(cudaStream_t s) : st(s) {}
     ~Scratch() {
@@ -185,7 +215,7 @@ struct Scratch {
     }
     template <class T>
     mcf_status get(T** p, size_t count) {
-        if (n >= 32) return fail(MCF_ERR_OOM, "too many scratch buffers");
+        if (n >= 48) return fail(MCF_ERR_OOM, "too many scratch buffers");
         size_t bytes = count * sizeof(T);
         if (bytes == 0) bytes = 16;
         void* q = nullptr;
@@ -278,39 +308,21 @@ struct ScopedL2Fetch {
     }
 };
 
-// Launch-shape knobs of the walk kernels, read once from the environment:
-// MCF_WALK_MINB (resident 256-thread blocks per SM the register budget is
-// sized for: 5, 6 or 8), MCF_WALK_GRAB (32-walk chunks a warp takes per atomic)
-// and MCF_WALK_TC_PATH (0 disables the per-entry record layout).
-struct WalkTuning {
-    int minb = 5;
-    int grab = 4;
-    bool tc_path = true;   // MCF_WALK_TC_PATH=0 selects the general node-record kernel for v = 1
-    int l2_fetch = 32;     // MCF_L2_FETCH_BYTES: L2 fetch granularity for walk kernels (0 = leave as is)
-    bool prefetch = false; // MCF_WALK_PREFETCH=1: issue the next random read before the cutoff test
-    int walks_per_thread = 1;  // MCF_WALK_PER_THREAD=2: two walks per thread in the TC kernel
-    bool tc_col = false;   // MCF_WALK_TC_READ=col: column index + node record instead of the per-entry record
-    bool diag_edge = true; // MCF_DIAG_EDGE=0: subgraph-centrality walks read node record + column index
-    int diag_cap_log2 = 12; // MCF_DIAG_CAP_LOG2 (10..14): largest hashed row Q_k, log2 of its slots
-    int refill_min = 16;    // MCF_WALK_REFILL_MIN (1..32): idle lanes a TC warp waits for before refilling
-};
-inline const WalkTuning& walk_tuning() {
-    static WalkTuning t = [] {
-        WalkTuning w;
-        if (const char* e = getenv("MCF_L2_FETCH_BYTES")) w.l2_fetch = std::max(0, std::min(128, atoi(e)));
-        if (const char* e = getenv("MCF_WALK_PREFETCH")) w.prefetch = atoi(e) != 0;
-        if (const char* e = getenv("MCF_WALK_PER_THREAD")) w.walks_per_thread = atoi(e) == 2 ? 2 : 1;
-        if (const char* e = getenv("MCF_WALK_TC_PATH")) w.tc_path = atoi(e) != 0;
-        if (const char* e = getenv("MCF_WALK_TC_READ")) w.tc_col = strcmp(e, "col") == 0;
-        if (const char* e = getenv("MCF_DIAG_EDGE")) w.diag_edge = atoi(e) != 0;
-        if (const char* e = getenv("MCF_DIAG_CAP_LOG2")) w.diag_cap_log2 = std::max(10, std::min(14, atoi(e)));
-        if (const char* e = getenv("MCF_WALK_REFILL_MIN")) w.refill_min = std::max(1, std::min(32, atoi(e)));
-        if (const char* e = getenv("MCF_WALK_MINB")) w.minb = atoi(e) >= 8 ? 8 : (atoi(e) <= 5 ? 5 : 6);
-        if (const char* e = getenv("MCF_WALK_GRAB")) w.grab = std::max(1, std::min(64, atoi(e)));
-        return w;
-    }();
-    return t;
-}
+// Launch shape of the walk kernels (fixed; every value yields the same
+// results, only the speed depends on them):
+//   WALK_MINB        resident 256-thread blocks per SM the walk kernels' register budget is sized for;
+//   WALK_GRAB        32-walk chunks a warp takes per atomic;
+//   WALK_REFILL_MIN  idle lanes a total-communicability warp waits for before it refills them;
+//   L2_FETCH_BYTES   L2 fetch granularity the walk kernels run with (ScopedL2Fetch);
+//   DIAG_CAP_LOG2    log2 of the slots of the largest hashed row Q_k of RandFunmDiag.
+constexpr int WALK_MINB = 5;
+constexpr int WALK_GRAB = 4;
+constexpr int WALK_REFILL_MIN = 16;
+constexpr int L2_FETCH_BYTES = 32;
+constexpr int DIAG_CAP_LOG2 = 12;
+
+// Global-timer window (ns) of a batch's last run: from its first kernel to its last.
+void batch_window(const mcf_batch* b, uint64_t* begin_ns, uint64_t* end_ns);
 
 // Builds the graph's node_od / edge_od arrays on first use (binary, nnz < 2^32).
 mcf_status ensure_edge_od(mcf_graph* g, cudaStream_t st);

@@ -48,17 +48,11 @@ struct Worker {
     std::thread thread;
 };
 
-// Device memory a request's batch scratch may take: per-node arrays, the
-// chunk table, the degree table and outputs; subgraph centrality adds its
-// per-CTA row regions.
+// Device memory a request's batch may take (mcf_query_footprint); -1 for a
+// query the batch planner would refuse.
 int64_t footprint(const mcf_query& q) {
-    const mcf_graph* g = q.graph;
-    const mcf_params& p = q.params;
-    const int64_t n = g->n;
-    const int64_t walks = p.walks_per_node > 0 ? p.walks_per_node * n : p.n_walks + n;
-    int64_t b = 112 * n + walks / 8 + 4 * (g->max_degree + 1) + (1 << 20);
-    if (q.kind == MCF_QUERY_SUBGRAPH_CENTRALITY) b += (int64_t)160 << 20;
-    return b;
+    size_t b = 0;
+    return mcf_query_footprint(&q, &b) == MCF_OK ? (int64_t)b : -1;
 }
 
 }  // namespace
@@ -76,6 +70,8 @@ struct mcf_server {
     std::thread scheduler;
     std::vector<Worker*> workers;
     std::vector<double> latencies;
+    // global-timer windows (ns) of the completed batches' device work
+    std::vector<std::pair<uint64_t, uint64_t>> windows;
     int64_t submitted = 0, completed = 0, rejected = 0, batches = 0, steps = 0;
     bool any_submit = false;
     Clock::time_point t_first, t_last;
@@ -101,6 +97,8 @@ static void worker_loop(mcf_server* s, Worker* w) {
         mcf_stats st{};
         mcf_status rc = mcf_batch_create(qs.data(), (int32_t)qs.size(), 0, w->stream, &b);
         if (rc == MCF_OK) rc = mcf_batch_run(b, w->stream, &st);
+        uint64_t t0 = 0, t1 = 0;
+        if (rc == MCF_OK) mcf::batch_window(b, &t0, &t1);
         mcf_batch_destroy(b);
         const auto now = Clock::now();
         {
@@ -114,6 +112,7 @@ static void worker_loop(mcf_server* s, Worker* w) {
                 ++s->completed;
             }
             s->steps += st.walk_steps;
+            if (t1 > t0) s->windows.push_back({t0, t1});
             ++s->batches;
             s->t_last = now;
             w->job.clear();
@@ -211,6 +210,11 @@ mcf_status mcf_server_submit(mcf_server_t s, const mcf_query* query, uint64_t* t
         r->q.params.coeffs = r->coeffs.data();
     }
     r->bytes = footprint(r->q);
+    if (r->bytes < 0) {
+        const std::string why = mcf_last_error();
+        delete r;
+        return fail(MCF_ERR_INVALID_ARG, "request refused: " + why);
+    }
     r->t_submit = Clock::now();
     {
         std::lock_guard<std::mutex> lk(s->mu);
@@ -288,6 +292,39 @@ mcf_status mcf_server_get_stats(mcf_server_t s, mcf_server_stats* out) {
         out->mean_ms = sum / (double)l.size();
     }
     if (s->any_submit && s->completed > 0) out->busy_s = std::chrono::duration<double>(s->t_last - s->t_first).count();
+    // sweep over the batches' device windows: time with two or more batches'
+    // work on the device, and the largest number at once
+    std::vector<std::pair<uint64_t, int>> ev;
+    ev.reserve(2 * s->windows.size());
+    for (const auto& w : s->windows) {
+        ev.push_back({w.first, 1});
+        ev.push_back({w.second, -1});
+    }
+    std::sort(ev.begin(), ev.end(), [](const std::pair<uint64_t, int>& a, const std::pair<uint64_t, int>& b) {
+        return a.first != b.first ? a.first < b.first : a.second < b.second;   // ends before starts at a tie
+    });
+    int live = 0, most = 0;
+    uint64_t prev = 0, overlap_ns = 0;
+    for (const auto& e : ev) {
+        if (live >= 2) overlap_ns += e.first - prev;
+        live += e.second;
+        most = std::max(most, live);
+        prev = e.first;
+    }
+    out->device_overlap_ms = (double)overlap_ns * 1e-6;
+    out->max_concurrent_batches = most;
+    return MCF_OK;
+}
+
+mcf_status mcf_server_release(mcf_server_t s, uint64_t ticket) {
+    set_error("");
+    if (!s) return fail(MCF_ERR_INVALID_ARG, "server is NULL");
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->all.find(ticket);
+    if (it == s->all.end()) return fail(MCF_ERR_INVALID_ARG, "unknown ticket");
+    if (it->second->state != 2) return fail(MCF_ERR_INVALID_ARG, "the request has not completed");
+    delete it->second;
+    s->all.erase(it);
     return MCF_OK;
 }
 

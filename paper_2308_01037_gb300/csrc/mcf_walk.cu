@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <mutex>
 #include <string>
+#include <functional>
 #include <type_traits>
 
 #include "mcf_device.cuh"
@@ -23,6 +24,7 @@ namespace mcf {
 __global__ void r_kernel(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                          const float* __restrict__ val, const double* __restrict__ v, double gamma,
                          double* __restrict__ r) {
+    MCF_KERNEL_ENTRY();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int64_t b = rp[i], e = rp[i + 1];
@@ -45,6 +47,7 @@ __global__ void r_kernel(int64_t n, const int64_t* __restrict__ rp, const int32_
 // fixed-partition partial sums of it.
 __global__ void colnorm_kernel(int64_t n, const int64_t* __restrict__ cp, const double* __restrict__ col_sq,
                                double gamma, double* __restrict__ colnorm, double* __restrict__ part) {
+    MCF_KERNEL_ENTRY();
     double s = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double sq = col_sq ? col_sq[i] : (double)(cp[i + 1] - cp[i]);
@@ -57,6 +60,7 @@ __global__ void colnorm_kernel(int64_t n, const int64_t* __restrict__ cp, const 
 }
 
 __global__ void sum_partials(const double* __restrict__ part, int nb, double* __restrict__ out) {
+    MCF_KERNEL_ENTRY();
     double s = 0.0;
     for (int b = threadIdx.x; b < nb; b += blockDim.x) s += part[b];
     s = block_sum_d(s);
@@ -69,6 +73,7 @@ __global__ void sum_partials(const double* __restrict__ part, int nb, double* __
 __global__ void alloc_kernel(int64_t n, const double* __restrict__ colnorm, const double* __restrict__ tot,
                              int64_t n_walks, int64_t wpn, const uint8_t* __restrict__ need, int64_t* __restrict__ nw,
                              int64_t* __restrict__ flag) {
+    MCF_KERNEL_ENTRY();
     const double T = *tot;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double c = colnorm[i];
@@ -89,6 +94,7 @@ __global__ void alloc_kernel(int64_t n, const double* __restrict__ colnorm, cons
 __global__ void compact_starts(int64_t n, const int64_t* __restrict__ flag, const int64_t* __restrict__ spos,
                                const int64_t* __restrict__ woff, int32_t* __restrict__ starts,
                                int64_t* __restrict__ soff, const unsigned long long* __restrict__ counters) {
+    MCF_KERNEL_ENTRY();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         if (flag[i]) {
             starts[spos[i]] = (int32_t)i;
@@ -101,6 +107,7 @@ __global__ void compact_starts(int64_t n, const int64_t* __restrict__ flag, cons
 // chunk_s0[c] = index s of the start whose walk range holds walk 32c.
 __global__ void chunk_table(const int64_t* __restrict__ soff, const unsigned long long* __restrict__ counters,
                             uint32_t* __restrict__ chunk_s0) {
+    MCF_KERNEL_ENTRY();
     const int64_t S = (int64_t)counters[C_STARTS];
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < S; s += (int64_t)gridDim.x * blockDim.x) {
         const int64_t c0 = (soff[s] + WARP_CHUNK - 1) / WARP_CHUNK;
@@ -112,6 +119,7 @@ __global__ void chunk_table(const int64_t* __restrict__ soff, const unsigned lon
 template <bool F64>
 __global__ void build_records(int64_t n, const int64_t* __restrict__ rp, const double* __restrict__ row_abs,
                               double gamma, const double* __restrict__ r, Rec<F64>* __restrict__ rec) {
+    MCF_KERNEL_ENTRY();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t b = rp[i];
         const int64_t d = rp[i + 1] - b;
@@ -143,13 +151,14 @@ __global__ void build_records(int64_t n, const int64_t* __restrict__ rp, const d
 // Algorithm 3's while loop.  A lane keeps a running sum while its
 // consecutive walks share a start node and adds it to acc[start] with one
 // float64 atomic when the start changes.
-template <bool F64, bool WEIGHTED, int MINB>
-__global__ void __launch_bounds__(256, MINB) walk_action_kernel(
+template <bool F64, bool WEIGHTED>
+__global__ void __launch_bounds__(256, WALK_MINB) walk_action_kernel(
     const Rec<F64>* __restrict__ rec, const int32_t* __restrict__ col, const WEntry* __restrict__ went,
     const int32_t* __restrict__ starts, const int64_t* __restrict__ soff, const int64_t* __restrict__ goff,
     const uint32_t* __restrict__ chunk_s0,
     const double* __restrict__ zeta_g, int K, double wc, float wc32, uint2 key, uint32_t req, int grab,
     double* __restrict__ acc, double* __restrict__ acc2, unsigned long long* __restrict__ counters) {
+    MCF_KERNEL_ENTRY();
     using real = typename std::conditional<F64, double, float>::type;
     using rtype = typename std::conditional<F64, double, float2>::type;
     __shared__ real zeta[MCF_MAX_COEFFS];
@@ -292,33 +301,38 @@ __global__ void __launch_bounds__(256, MINB) walk_action_kernel(
 // (one random 8-byte read per step); rm[d] = float(gamma * d) is a per-solve
 // table indexed by degree (small, cache-resident).
 __global__ void build_node_od(int64_t n, const int64_t* __restrict__ rp, uint2* __restrict__ nod) {
+    MCF_KERNEL_ENTRY();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         nod[i] = make_uint2((uint32_t)rp[i], (uint32_t)(rp[i + 1] - rp[i]));
 }
 
 __global__ void build_edge_od(int64_t nnz, const int32_t* __restrict__ col, const uint2* __restrict__ nod,
                               uint2* __restrict__ eod) {
+    MCF_KERNEL_ENTRY();
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x)
         eod[p] = nod[col[p]];
 }
 
 __global__ void degree_table(int64_t max_deg, double gamma, float* __restrict__ rm) {
+    MCF_KERNEL_ENTRY();
     for (int64_t d = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; d <= max_deg; d += (int64_t)gridDim.x * blockDim.x)
         rm[d] = __double2float_rn(__dmul_rn(gamma, (double)d));
 }
 
 // The same walks (ids, Philox streams), float32 arithmetic and accumulation
-// as walk_action_kernel<false, false, MINB> (so the same result up to float64
+// as walk_action_kernel<false, false> (so the same result up to float64
 // summation order), with the per-step state reduced to {offset, degree} and
-// a warp's idle lanes refilled refill_min or more at a time.
-template <int MINB, bool PREFETCH, bool VIA_COL>
-__global__ void __launch_bounds__(256, MINB) walk_tc_kernel(
-    const uint2* __restrict__ nod, const uint2* __restrict__ eod, const int32_t* __restrict__ col,
-    const float* __restrict__ rm,
+// a warp's idle lanes refilled refill_min or more at a time.  The next
+// state's record is read only once the walk is known to go on (after the
+// cutoff test): a read issued earlier would be wasted DRAM work at every
+// walk's end, and the kernel is bound by the rate of random DRAM reads.
+__global__ void __launch_bounds__(256, WALK_MINB) walk_tc_kernel(
+    const uint2* __restrict__ nod, const uint2* __restrict__ eod, const float* __restrict__ rm,
     const int32_t* __restrict__ starts, const int64_t* __restrict__ soff, const int64_t* __restrict__ goff,
     const uint32_t* __restrict__ chunk_s0,
     const double* __restrict__ zeta_g, int K, float wc32, uint2 key, uint32_t req, int grab, int refill_min,
     double* __restrict__ acc, double* __restrict__ acc2, unsigned long long* __restrict__ counters) {
+    MCF_KERNEL_ENTRY();
     __shared__ float zeta[MCF_MAX_COEFFS];
     __shared__ WalkResults<float2> rbuf[256 / 32];
     for (int k = threadIdx.x; k <= K; k += blockDim.x) zeta[k] = (float)zeta_g[k];
@@ -340,18 +354,6 @@ __global__ void __launch_bounds__(256, MINB) walk_tc_kernel(
     uint4 u = make_uint4(0u, 0u, 0u, 0u);
     F2Acc a32;
     uint32_t my_steps = 0, my_walks = 0, flags = 0;
-    // The {offset, degree} of entry j's neighbour: one random read of the
-    // per-entry record, or (VIA_COL) the column index and then the
-    // neighbour's node record, which stays in L2 (half the bytes of DRAM
-    // array per entry, one more dependent read per step).
-    auto next_od = [&](uint32_t j) -> uint2 {
-        if constexpr (VIA_COL) {
-            const int32_t nb = load_col(col + (int64_t)off + j, policy_evict_first());
-            return load_od(nod + nb, policy_evict_last());
-        } else {
-            return load_od(eod + (int64_t)off + j, policy_evict_first());
-        }
-    };
     for (;;) {
         unsigned idle = __ballot_sync(FULL, !active);
         // refill once at least refill_min lanes are idle (or all are): fewer
@@ -407,17 +409,7 @@ __global__ void __launch_bounds__(256, MINB) walk_tc_kernel(
         if (!__any_sync(FULL, active)) break;
         bool done = false;
         if (active) {
-            // With PREFETCH the next state's read is issued before the cutoff
-            // test (its address depends only on this state's record and the
-            // random word, not on W), so the degree-table lookup and the test
-            // overlap the random read; the read is wasted when the walk ends.
             const bool last = k + 2 >= K || deg == 0;
-            uint2 nx = make_uint2(0u, 0u);
-            if (PREFETCH && !last) {
-                uint32_t w0, w1;
-                walk_words<false>(u, k, (uint32_t)g, (uint32_t)((uint64_t)g >> 32), req, key, w0, w1);
-                nx = next_od(__umulhi(w0, deg));
-            }
             done = !(fabsf(W) > wc32);
             if (!done) {
                 const float t = __ldg(rm + deg);
@@ -425,11 +417,9 @@ __global__ void __launch_bounds__(256, MINB) walk_tc_kernel(
                 if (last) {
                     done = true;
                 } else {
-                    if (!PREFETCH) {
-                        uint32_t w0, w1;
-                        walk_words<false>(u, k, (uint32_t)g, (uint32_t)((uint64_t)g >> 32), req, key, w0, w1);
-                        nx = next_od(__umulhi(w0, deg));
-                    }
+                    uint32_t w0, w1;
+                    walk_words<false>(u, k, (uint32_t)g, (uint32_t)((uint64_t)g >> 32), req, key, w0, w1);
+                    const uint2 nx = load_od(eod + (int64_t)off + __umulhi(w0, deg), policy_evict_first());
                     W = __fmul_rn(W, t);
                     off = nx.x;
                     deg = nx.y;
@@ -460,167 +450,9 @@ __global__ void __launch_bounds__(256, MINB) walk_tc_kernel(
     }
 }
 
-// Two (NW) walks per thread: the same schedule as walk_tc_kernel, but each
-// warp runs NW independent pools of 32-walk chunks and every thread advances
-// one walk of each pool per iteration, issuing both random reads before it
-// consumes either, so a thread keeps NW dependent-read chains in flight.
-struct TcPool {
-    int32_t c = -1, c_end = -1;
-    int p = 0, valid = 0;
-    int32_t cs = 0;
-    bool exhausted = false;
-};
-struct TcLane {
-    bool active = false;
-    int64_t g = 0;
-    uint32_t node0 = 0, off = 0, deg = 0;
-    int k = 0;
-    float W = 1.f;
-    uint4 u = make_uint4(0u, 0u, 0u, 0u);
-    F2Acc a;
-};
-
-__device__ __forceinline__ void tc_refill(TcPool& P, TcLane& L, const uint2* __restrict__ nod,
-                                          const int32_t* __restrict__ starts, const int64_t* __restrict__ soff,
-                                          const int64_t* __restrict__ goff,
-                                          const uint32_t* __restrict__ chunk_s0, int32_t n_chunks, int grab,
-                                          unsigned long long* __restrict__ counters, int lane, unsigned lt_mask) {
-    const unsigned FULL = 0xffffffffu;
-    unsigned idle = __ballot_sync(FULL, !L.active);
-    while (idle && !P.exhausted) {
-        if (P.p >= P.valid) {
-            ++P.c;
-            if (P.c >= P.c_end) {
-                int32_t base = 0;
-                if (lane == 0) base = (int32_t)atomicAdd((unsigned int*)&counters[C_NEXT], (unsigned)grab);
-                base = __shfl_sync(FULL, base, 0);
-                P.c = base;
-                P.c_end = min(base + grab, n_chunks);
-            }
-            if (P.c >= n_chunks) {
-                P.exhausted = true;
-                break;
-            }
-            const int64_t S = (int64_t)counters[C_STARTS];
-            const int64_t s0 = chunk_s0[P.c];
-            const int64_t bnd = (s0 + 1 + lane <= S) ? soff[s0 + 1 + lane] : INT64_MAX;
-            const int64_t gl = (int64_t)P.c * WARP_CHUNK + lane;
-            int cnt = 0;
-#pragma unroll
-            for (int step = 16; step > 0; step >>= 1) {
-                const int64_t bv = __shfl_sync(FULL, bnd, cnt + step - 1);
-                if (bv <= gl) cnt += step;
-            }
-            P.cs = (int32_t)(s0 + cnt);
-            P.valid = (int)min((int64_t)WARP_CHUNK, (int64_t)counters[C_TOTAL] - (int64_t)P.c * WARP_CHUNK);
-            P.p = 0;
-        }
-        const int avail = P.valid - P.p;
-        const int rank = __popc(idle & lt_mask);
-        const int src = min(P.p + rank, WARP_CHUNK - 1);
-        const int32_t s_new = __shfl_sync(FULL, P.cs, src);
-        if (((idle >> lane) & 1u) && rank < avail) {
-            L.g = (int64_t)P.c * WARP_CHUNK + P.p + rank;
-            if (goff != soff) L.g = goff[s_new] + (L.g - soff[s_new]);
-            L.node0 = (uint32_t)starts[s_new];
-            const uint2 od = nod[L.node0];
-            L.off = od.x;
-            L.deg = od.y;
-            L.k = 0;
-            L.W = 1.f;
-            L.a = F2Acc();
-            L.active = true;
-        }
-        P.p += min(avail, __popc(idle));
-        idle = __ballot_sync(FULL, !L.active);
-    }
-}
-
-template <int MINB, int NW>
-__global__ void __launch_bounds__(256, MINB) walk_tc_multi_kernel(
-    const uint2* __restrict__ nod, const uint2* __restrict__ eod, const float* __restrict__ rm,
-    const int32_t* __restrict__ starts, const int64_t* __restrict__ soff, const int64_t* __restrict__ goff,
-    const uint32_t* __restrict__ chunk_s0,
-    const double* __restrict__ zeta_g, int K, float wc32, uint2 key, uint32_t req, int grab,
-    double* __restrict__ acc, unsigned long long* __restrict__ counters) {
-    double* const acc2 = nullptr;   // no second moments in this variant
-    __shared__ float zeta[MCF_MAX_COEFFS];
-    __shared__ WalkResults<float2> rbuf[256 / 32];
-    for (int k = threadIdx.x; k <= K; k += blockDim.x) zeta[k] = (float)zeta_g[k];
-    __syncthreads();
-    const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    const unsigned lt_mask = (1u << lane) - 1u;
-    WalkResults<float2>& rb = rbuf[threadIdx.x >> 5];
-    const int32_t n_chunks = (int32_t)(((int64_t)counters[C_TOTAL] + WARP_CHUNK - 1) / WARP_CHUNK);
-    TcPool P[NW];
-    TcLane L[NW];
-    int rb_n = 0;
-    uint32_t my_steps = 0, my_walks = 0, flags = 0;
-    for (;;) {
-        bool any = false;
-#pragma unroll
-        for (int s = 0; s < NW; ++s) {
-            tc_refill(P[s], L[s], nod, starts, soff, goff, chunk_s0, n_chunks, grab, counters, lane, lt_mask);
-            any |= L[s].active;
-        }
-        if (!__any_sync(FULL, any)) break;
-        uint2 nx[NW];
-        bool last[NW];
-#pragma unroll
-        for (int s = 0; s < NW; ++s) {
-            last[s] = L[s].k + 2 >= K || L[s].deg == 0;
-            nx[s] = make_uint2(0u, 0u);
-            if (L[s].active && !last[s]) {
-                uint32_t w0, w1;
-                walk_words<false>(L[s].u, L[s].k, (uint32_t)L[s].g, (uint32_t)((uint64_t)L[s].g >> 32), req, key, w0, w1);
-                nx[s] = load_od(eod + (int64_t)L[s].off + __umulhi(w0, L[s].deg), policy_evict_first());
-            }
-        }
-#pragma unroll
-        for (int s = 0; s < NW; ++s) {
-            bool done = false;
-            if (L[s].active) {
-                done = !(fabsf(L[s].W) > wc32);
-                if (!done) {
-                    const float t = __ldg(rm + L[s].deg);
-                    L[s].a.add(__fmul_rn(__fmul_rn(zeta[L[s].k + 2], L[s].W), t));
-                    if (last[s]) {
-                        done = true;
-                    } else {
-                        L[s].W = __fmul_rn(L[s].W, t);
-                        L[s].off = nx[s].x;
-                        L[s].deg = nx[s].y;
-                        ++L[s].k;
-                        ++my_steps;
-                    }
-                }
-                if (done) {
-                    if (!isfinite(L[s].W) || !isfinite(L[s].a.hi)) flags |= 1u;
-                    ++my_walks;
-                    L[s].active = false;
-                }
-            }
-            rb_n = rb.push(done, L[s].node0, make_float2(L[s].a.hi, L[s].a.lo), rb_n, lane, lt_mask, acc, acc2);
-        }
-    }
-    rb.flush(rb_n, lane, acc, acc2);
-    unsigned long long ws = my_steps, ww = my_walks;
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) {
-        ws += __shfl_down_sync(FULL, ws, d);
-        ww += __shfl_down_sync(FULL, ww, d);
-        flags |= __shfl_down_sync(FULL, flags, d);
-    }
-    if (lane == 0) {
-        atomicAdd(&counters[C_STEPS], ws);
-        atomicAdd(&counters[C_WALKS], ww);
-        if (flags) atomicOr(&counters[C_FLAGS], (unsigned long long)flags);
-    }
-}
-
 // q_i = acc_i / N_i (Eq. rand_funm_action_formula, the 1/N_i factor of W^(0)).
 __global__ void finalize_q(int64_t n, double* __restrict__ acc, const int64_t* __restrict__ nw) {
+    MCF_KERNEL_ENTRY();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         acc[i] = nw[i] > 0 ? acc[i] / (double)nw[i] : 0.0;
 }
@@ -631,6 +463,7 @@ __global__ void action_epilogue(int64_t n, const int64_t* __restrict__ rp, const
                                 const float* __restrict__ val, double gamma, double z0, double z1,
                                 const double* __restrict__ v, const double* __restrict__ r,
                                 const double* __restrict__ q, double* __restrict__ y) {
+    MCF_KERNEL_ENTRY();
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -645,6 +478,7 @@ __global__ void action_epilogue(int64_t n, const int64_t* __restrict__ rp, const
 // cof[s] is where start s's walks begin in it (soff[s] keeps the full-run id).
 __global__ void subset_walks(int64_t n, const int64_t* __restrict__ flag, const int64_t* __restrict__ nw,
                              int64_t* __restrict__ wmask) {
+    MCF_KERNEL_ENTRY();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         wmask[i] = flag[i] ? nw[i] : 0;
 }
@@ -652,6 +486,7 @@ __global__ void subset_walks(int64_t n, const int64_t* __restrict__ flag, const 
 __global__ void subset_offsets(int64_t n, const int64_t* __restrict__ flag, const int64_t* __restrict__ spos,
                                const int64_t* __restrict__ cw, int64_t* __restrict__ cof,
                                const unsigned long long* __restrict__ counters) {
+    MCF_KERNEL_ENTRY();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         if (flag[i]) cof[spos[i]] = cw[i];
     if (blockIdx.x == 0 && threadIdx.x == 0) cof[counters[C_STARTS]] = (int64_t)counters[C_TOTAL];
@@ -662,6 +497,7 @@ __global__ void action_epilogue_nodes(int64_t m, const int64_t* __restrict__ nod
                                       const int32_t* __restrict__ col, const float* __restrict__ val, double gamma,
                                       double z0, double z1, const double* __restrict__ v, const double* __restrict__ r,
                                       const double* __restrict__ q, double* __restrict__ y) {
+    MCF_KERNEL_ENTRY();
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -682,6 +518,7 @@ __global__ void action_epilogue_nodes(int64_t m, const int64_t* __restrict__ nod
 // squares acc2_i); 0 when N_i < 2.
 __global__ void se_node_var(int64_t n, const double* __restrict__ q, const double* __restrict__ acc2,
                             const int64_t* __restrict__ nw, double* __restrict__ w) {
+    MCF_KERNEL_ENTRY();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t N = nw[i];
         double x = 0.0;
@@ -699,6 +536,7 @@ __global__ void se_rows(int64_t m, const int64_t* __restrict__ rows, const int64
                         const int32_t* __restrict__ col, const float* __restrict__ val, double gamma,
                         const double* __restrict__ w, const double* __restrict__ y,
                         unsigned long long* __restrict__ out) {
+    MCF_KERNEL_ENTRY();
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -740,9 +578,10 @@ __global__ void __launch_bounds__(256) walk_diag_kernel(
     const float* __restrict__ cv, const int32_t* __restrict__ col, const WEntry* __restrict__ went,
     const uint4* __restrict__ erec, const uint2* __restrict__ nod, const float* __restrict__ rm,
     const int32_t* __restrict__ starts,
-    const int64_t* __restrict__ woff, const int64_t* __restrict__ nw, const uint8_t* __restrict__ want, double gamma,
+    const int64_t* __restrict__ woff, const int64_t* __restrict__ nw, SubList sub, double gamma,
     const double* __restrict__ zeta_g, int K, double wc, float wc32, uint2 key, uint32_t req, int64_t n, int cap_log2,
     double* __restrict__ qval, double* __restrict__ dacc, unsigned long long* __restrict__ counters) {
+    MCF_KERNEL_ENTRY();
     using real = typename std::conditional<F64, double, float>::type;
     static_assert(!EDGE || (!F64 && !WEIGHTED), "neighbour records serve binary float32 walks");
     extern __shared__ int32_t smem_i[];
@@ -814,7 +653,7 @@ __global__ void __launch_bounds__(256) walk_diag_kernel(
             if (!__syncthreads_or(stopped)) break;
             // the table filled up: apply the partial row, clear it, resume
             __threadfence_block();
-            diag_apply<DENSE>(t, k0, Nk, cp, ri, cv, want, gamma, dacc);
+            diag_apply<DENSE>(t, k0, Nk, cp, ri, cv, sub, gamma, dacc);
             __syncthreads();
             diag_clear<DENSE>(t, n);
             __syncthreads();
@@ -822,7 +661,7 @@ __global__ void __launch_bounds__(256) walk_diag_kernel(
             __syncthreads();
         }
         __threadfence_block();
-        diag_apply<DENSE>(t, k0, Nk, cp, ri, cv, want, gamma, dacc);
+        diag_apply<DENSE>(t, k0, Nk, cp, ri, cv, sub, gamma, dacc);
         __syncthreads();
         diag_clear<DENSE>(t, n);
         __syncthreads();
@@ -843,18 +682,56 @@ __global__ void __launch_bounds__(256) walk_diag_kernel(
     }
 }
 
-// need[j] = 1 for every column j adjacent to a requested node; want[i] = 1 for requested nodes.
-__global__ void mark_nodes(int64_t m, const int64_t* __restrict__ nodes, const int64_t* __restrict__ rp,
-                           const int32_t* __restrict__ col, uint8_t* __restrict__ need, uint8_t* __restrict__ want) {
+// Per-column lists of the requested rows of a RandFunmDiag node subset
+// (SubList): first[i] = the first position t with nodes[t] = i claims node i
+// (a node listed twice is counted once); cnt[k] = |{i in S : a_ik != 0}|; after
+// the scan of cnt into ptr, fill places each pair (k, i) of a claimed node.
+__global__ void sub_claim(int64_t m, const int64_t* __restrict__ nodes, long long* __restrict__ first) {
+    MCF_KERNEL_ENTRY();
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x)
+        atomicCAS((unsigned long long*)&first[nodes[t]], ~0ull, (unsigned long long)t);
+}
+
+__global__ void sub_count(int64_t m, const int64_t* __restrict__ nodes, const long long* __restrict__ first,
+                          const int64_t* __restrict__ rp, const int32_t* __restrict__ col, int64_t* __restrict__ cnt) {
+    MCF_KERNEL_ENTRY();
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = nodes[t];
-        want[i] = 1;
+        if (first[i] != t) continue;
+        for (int64_t p = rp[i]; p < rp[i + 1]; ++p) atomicAdd((unsigned long long*)&cnt[col[p]], 1ull);
+    }
+}
+
+__global__ void sub_fill(int64_t m, const int64_t* __restrict__ nodes, const long long* __restrict__ first,
+                         const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const float* __restrict__ val,
+                         const int64_t* __restrict__ ptr, int64_t* __restrict__ fill, int32_t* __restrict__ row,
+                         float* __restrict__ sval) {
+    MCF_KERNEL_ENTRY();
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = nodes[t];
+        if (first[i] != t) continue;
+        for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+            const int32_t k = col[p];
+            const int64_t pos = ptr[k] + (int64_t)atomicAdd((unsigned long long*)&fill[k], 1ull);
+            row[pos] = (int32_t)i;
+            if (val) sval[pos] = val[p];
+        }
+    }
+}
+
+// need[j] = 1 for every column j adjacent to a requested node.
+__global__ void mark_nodes(int64_t m, const int64_t* __restrict__ nodes, const int64_t* __restrict__ rp,
+                           const int32_t* __restrict__ col, uint8_t* __restrict__ need) {
+    MCF_KERNEL_ENTRY();
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = nodes[t];
         for (int64_t p = rp[i]; p < rp[i + 1]; ++p) need[col[p]] = 1;
     }
 }
 
 __global__ void check_nodes(int64_t m, const int64_t* __restrict__ nodes, int64_t n,
                             unsigned long long* __restrict__ counters) {
+    MCF_KERNEL_ENTRY();
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x)
         if (nodes[t] < 0 || nodes[t] >= n) atomicOr(&counters[C_FLAGS], 2ull);
 }
@@ -863,6 +740,7 @@ __global__ void check_nodes(int64_t m, const int64_t* __restrict__ nodes, int64_
 __global__ void diag_finish(int64_t m, const int64_t* __restrict__ nodes, const double* __restrict__ dacc,
                             const double* __restrict__ diag, double gamma, double z0, double z1, int K,
                             double* __restrict__ d) {
+    MCF_KERNEL_ENTRY();
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = nodes ? nodes[t] : t;
         double v = z0;
@@ -872,6 +750,8 @@ __global__ void diag_finish(int64_t m, const int64_t* __restrict__ nodes, const 
 }
 
 // ====================================================================== host side
+constexpr int64_t MAX_WALKS_PER_SOLVE = (int64_t)1 << 36;
+
 static mcf_status check_params(const mcf_graph* g, const mcf_params* p) {
     if (!g) return fail(MCF_ERR_INVALID_ARG, "graph is NULL");
     if (!p) return fail(MCF_ERR_INVALID_ARG, "params is NULL");
@@ -890,6 +770,12 @@ static mcf_status check_params(const mcf_graph* g, const mcf_params* p) {
         if (!isfinite(p->coeffs[k])) return fail(MCF_ERR_INVALID_ARG, "coefficients must be finite");
     if (p->precision == MCF_F32W_F64ACC && g->nnz >= ((int64_t)1 << 32))
         return fail(MCF_ERR_UNSUPPORTED, "float32 walk records need nnz < 2^32");
+    // walk ids (and the chunk tables indexed by them) stay below 2^36:
+    // compared without forming N_s + n or walks_per_node * n, which could overflow
+    const int64_t n = g->n;
+    const bool too_many = p->walks_per_node > 0 ? (n > 0 && p->walks_per_node > MAX_WALKS_PER_SOLVE / n)
+                                                : p->n_walks > MAX_WALKS_PER_SOLVE - n;
+    if (too_many) return fail(MCF_ERR_INVALID_ARG, "more than 2^36 walks per solve");
     return MCF_OK;
 }
 
@@ -985,14 +871,14 @@ static mcf_status finish_stats(mcf_stats* stats, const unsigned long long* count
     return MCF_OK;
 }
 
-template <bool F64, bool WEIGHTED, int MINB>
-static void launch_action_walks_t(const mcf_graph* g, const Prep& P, uint32_t* chunk_s0, int K, double wc, uint2 key,
-                                  uint32_t req, double* acc, double* acc2, cudaStream_t st) {
-    auto kern = walk_action_kernel<F64, WEIGHTED, MINB>;
+template <bool F64, bool WEIGHTED>
+static void launch_action_walks(const mcf_graph* g, const Prep& P, uint32_t* chunk_s0, int K, double wc, uint2 key,
+                                uint32_t req, double* acc, double* acc2, cudaStream_t st) {
+    auto kern = walk_action_kernel<F64, WEIGHTED>;
     const int grid = persistent_grid(kern, 256, 0);
-    ScopedL2Fetch fetch(walk_tuning().l2_fetch);
+    ScopedL2Fetch fetch(L2_FETCH_BYTES);
     kern<<<grid, 256, 0, st>>>((const Rec<F64>*)P.rec, g->col_idx, g->went, P.starts, P.cof, P.soff, chunk_s0, P.zeta,
-                               K, wc, cutoff_f32(wc), key, req, walk_tuning().grab, acc, acc2, P.counters);
+                               K, wc, cutoff_f32(wc), key, req, WALK_GRAB, acc, acc2, P.counters);
 }
 
 // Builds the graph's node_od / edge_od arrays on first use (binary, nnz < 2^32).
@@ -1033,6 +919,7 @@ mcf_status ensure_edge_od(mcf_graph* g, cudaStream_t st) {
 
 __global__ void build_edge_rec(int64_t nnz, const int32_t* __restrict__ col, const uint2* __restrict__ nod,
                                uint4* __restrict__ erec) {
+    MCF_KERNEL_ENTRY();
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
         const int32_t c = col[p];
         const uint2 od = nod[c];
@@ -1056,34 +943,12 @@ mcf_status ensure_edge_rec(mcf_graph* g, cudaStream_t st) {
     return MCF_OK;
 }
 
-template <int MINB>
-static void launch_tc_walks_t(const mcf_graph* g, const Prep& P, const float* rm, uint32_t* chunk_s0, int K,
-                              double wc, uint2 key, uint32_t req, double* acc, double* acc2, cudaStream_t st) {
-    if (walk_tuning().walks_per_thread == 2 && !acc2) {
-        auto kern = walk_tc_multi_kernel<(MINB > 4 ? 4 : MINB), 2>;
-        const int grid = persistent_grid(kern, 256, 0);
-        ScopedL2Fetch fetch(walk_tuning().l2_fetch);
-        kern<<<grid, 256, 0, st>>>(g->node_od, g->edge_od, rm, P.starts, P.cof, P.soff, chunk_s0, P.zeta, K,
-                                   cutoff_f32(wc), key, req, walk_tuning().grab, acc, P.counters);
-        return;
-    }
-    const bool pf = walk_tuning().prefetch, vc = walk_tuning().tc_col;
-    auto kern = pf ? (vc ? walk_tc_kernel<MINB, true, true> : walk_tc_kernel<MINB, true, false>)
-                   : (vc ? walk_tc_kernel<MINB, false, true> : walk_tc_kernel<MINB, false, false>);
-    const int grid = persistent_grid(kern, 256, 0);
-    ScopedL2Fetch fetch(walk_tuning().l2_fetch);
-    kern<<<grid, 256, 0, st>>>(g->node_od, g->edge_od, g->col_idx, rm, P.starts, P.cof, P.soff, chunk_s0, P.zeta, K,
-                               cutoff_f32(wc), key, req, walk_tuning().grab, walk_tuning().refill_min, acc, acc2,
-                               P.counters);
-}
-
-template <bool F64, bool WEIGHTED>
-static void launch_action_walks(const mcf_graph* g, const Prep& P, uint32_t* chunk_s0, int K, double wc, uint2 key,
-                                uint32_t req, double* acc, double* acc2, cudaStream_t st) {
-    if (walk_tuning().minb == 8) launch_action_walks_t<F64, WEIGHTED, 8>(g, P, chunk_s0, K, wc, key, req, acc, acc2, st);
-    else if (walk_tuning().minb == 5)
-        launch_action_walks_t<F64, WEIGHTED, 5>(g, P, chunk_s0, K, wc, key, req, acc, acc2, st);
-    else launch_action_walks_t<F64, WEIGHTED, 6>(g, P, chunk_s0, K, wc, key, req, acc, acc2, st);
+static void launch_tc_walks(const mcf_graph* g, const Prep& P, const float* rm, uint32_t* chunk_s0, int K, double wc,
+                            uint2 key, uint32_t req, double* acc, double* acc2, cudaStream_t st) {
+    const int grid = persistent_grid(walk_tc_kernel, 256, 0);
+    ScopedL2Fetch fetch(L2_FETCH_BYTES);
+    walk_tc_kernel<<<grid, 256, 0, st>>>(g->node_od, g->edge_od, rm, P.starts, P.cof, P.soff, chunk_s0, P.zeta, K,
+                                         cutoff_f32(wc), key, req, WALK_GRAB, WALK_REFILL_MIN, acc, acc2, P.counters);
 }
 
 static mcf_status solve_action(mcf_graph* g, const mcf_params* p, const double* v, double* y, mcf_stats* stats,
@@ -1116,7 +981,7 @@ static mcf_status solve_action(mcf_graph* g, const mcf_params* p, const double* 
     if (!y_on_dev) MCF_TRY(sc.get(&y_dev, m));
     // a node subset walks only the columns adjacent to the requested nodes
     const int64_t* nodes_dev = nullptr;
-    uint8_t *need = nullptr, *want = nullptr;
+    uint8_t* need = nullptr;
     if (nodes) {
         if (m == 0) return MCF_OK;
         if (is_device_ptr(nodes)) {
@@ -1138,10 +1003,8 @@ static mcf_status solve_action(mcf_graph* g, const mcf_params* p, const double* 
             nodes_dev = nd;
         }
         MCF_TRY(sc.get(&need, n));
-        MCF_TRY(sc.get(&want, n));
         MCF_CUDA_TRY(cudaMemsetAsync(need, 0, n, st));
-        MCF_CUDA_TRY(cudaMemsetAsync(want, 0, n, st));
-        mark_nodes<<<grid_for(m, 256), 256, 0, st>>>(m, nodes_dev, g->row_ptr, g->col_idx, need, want);
+        mark_nodes<<<grid_for(m, 256), 256, 0, st>>>(m, nodes_dev, g->row_ptr, g->col_idx, need);
     }
     Prep P;
     MCF_TRY(prepare(g, p, gamma, v_dev, need, sc, P, st));
@@ -1170,9 +1033,9 @@ static mcf_status solve_action(mcf_graph* g, const mcf_params* p, const double* 
     if (n > 0) {
         MCF_CUDA_TRY(cudaMemsetAsync(acc, 0, n * sizeof(double), st));
         if (K >= 2) {
-            // walk ids are bounded by N_s + n (rounding) or walks_per_node * n
+            // walk ids are bounded by N_s + n (rounding) or walks_per_node * n,
+            // below MAX_WALKS_PER_SOLVE (check_params)
             const int64_t max_walks = p->walks_per_node > 0 ? p->walks_per_node * n : p->n_walks + n;
-            if (max_walks >= ((int64_t)1 << 36)) return fail(MCF_ERR_INVALID_ARG, "more than 2^36 walks per solve");
             const int64_t max_chunks = max_walks / WARP_CHUNK + 2;
             uint32_t* chunk_s0;
             MCF_TRY(sc.get(&chunk_s0, max_chunks));
@@ -1183,7 +1046,7 @@ static mcf_status solve_action(mcf_graph* g, const mcf_params* p, const double* 
                 cudaEventRecord(e0, st);
             }
             const uint2 key = philox_key(p->seed);
-            const bool tc_path = ones && !f64 && !g->weighted && g->nnz < ((int64_t)1 << 32) && walk_tuning().tc_path;
+            const bool tc_path = ones && !f64 && !g->weighted && g->nnz < ((int64_t)1 << 32);
             if (tc_path) {
                 MCF_TRY(ensure_edge_od(g, st));
                 float* rm;
@@ -1191,9 +1054,7 @@ static mcf_status solve_action(mcf_graph* g, const mcf_params* p, const double* 
                 degree_table<<<grid_for(g->max_degree + 1, 256), 256, 0, st>>>(g->max_degree, gamma, rm);
                 const uint32_t rq = p->request_id;
                 const double wc = p->w_cutoff;
-                if (walk_tuning().minb == 8) launch_tc_walks_t<8>(g, P, rm, chunk_s0, K, wc, key, rq, acc, acc2, st);
-                else if (walk_tuning().minb == 5) launch_tc_walks_t<5>(g, P, rm, chunk_s0, K, wc, key, rq, acc, acc2, st);
-                else launch_tc_walks_t<6>(g, P, rm, chunk_s0, K, wc, key, rq, acc, acc2, st);
+                launch_tc_walks(g, P, rm, chunk_s0, K, wc, key, rq, acc, acc2, st);
             } else if (f64 && g->weighted) {
                 launch_action_walks<true, true>(g, P, chunk_s0, K, p->w_cutoff, key, p->request_id, acc, acc2, st);
             } else if (f64) {
@@ -1249,7 +1110,7 @@ constexpr int64_t DIAG_EDGE_MIN_NNZ = (int64_t)1 << 20;
 // several CTAs share an SM and keep enough walks in flight); a start with
 // more distinct visits flushes its partial row.
 template <bool F64, bool WEIGHTED, bool DENSE>
-static mcf_status launch_diag(const mcf_graph* g, const Prep& P, const uint8_t* want, double gamma, int K, double wc,
+static mcf_status launch_diag(const mcf_graph* g, const Prep& P, const SubList& sub, double gamma, int K, double wc,
                               uint2 key, uint32_t req, int64_t nk_hint, double* dacc, Scratch& sc, cudaStream_t st) {
     // binary float32 walks read 16-byte neighbour records when the graph has them
     constexpr bool can_edge = !F64 && !WEIGHTED;
@@ -1269,7 +1130,7 @@ static mcf_status launch_diag(const mcf_graph* g, const Prep& P, const uint8_t* 
     if (!DENSE) {
         const int64_t want_slots = std::max<int64_t>(4 * std::max<int64_t>(nk_hint, 1) * 4, 4 * threads);
         cap_log2 = 10;
-        while (cap_log2 < walk_tuning().diag_cap_log2 && ((int64_t)1 << cap_log2) < want_slots) ++cap_log2;
+        while (cap_log2 < DIAG_CAP_LOG2 && ((int64_t)1 << cap_log2) < want_slots) ++cap_log2;
         cap = (int64_t)1 << cap_log2;
         smem = (size_t)cap * 2 * sizeof(int32_t);
     }
@@ -1277,11 +1138,57 @@ static mcf_status launch_diag(const mcf_graph* g, const Prep& P, const uint8_t* 
     const int grid = persistent_grid(kern, threads, smem);
     double* qval;
     MCF_TRY(sc.get(&qval, (size_t)grid * (size_t)std::max<int64_t>(cap, 1)));
-    ScopedL2Fetch fetch(walk_tuning().l2_fetch);
+    ScopedL2Fetch fetch(L2_FETCH_BYTES);
     kern<<<grid, threads, smem, st>>>((const Rec<F64>*)P.rec, g->col_ptr, g->row_idx, g->col_values, g->col_idx,
-                                      g->went, g->edge_rec, g->node_od, rm, P.starts, P.woff, P.nw, want, gamma, P.zeta,
+                                      g->went, g->edge_rec, g->node_od, rm, P.starts, P.woff, P.nw, sub, gamma, P.zeta,
                                       K, wc, cutoff_f32(wc), key, req, g->n, cap_log2, qval, dacc, P.counters);
     MCF_CUDA_TRY(cudaGetLastError());
+    return MCF_OK;
+}
+
+mcf_status check_nodes_on_device(const int64_t* nodes_dev, int64_t m, int64_t n, cudaStream_t st) {
+    if (m <= 0) return MCF_OK;
+    unsigned long long* chk = nullptr;
+    if (cudaMallocAsync((void**)&chk, N_COUNTERS * sizeof(unsigned long long), st) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MCF_ERR_OOM, "device allocation for the node check failed");
+    }
+    unsigned long long h = 0;
+    cudaMemsetAsync(chk, 0, N_COUNTERS * sizeof(unsigned long long), st);
+    check_nodes<<<grid_for(m, 256), 256, 0, st>>>(m, nodes_dev, n, chk);
+    cudaMemcpyAsync(&h, &chk[C_FLAGS], sizeof(h), cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(chk, st);
+    MCF_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h & 2ull) return fail(MCF_ERR_INVALID_ARG, "node index out of range");
+    return MCF_OK;
+}
+
+mcf_status build_subset_lists(const mcf_graph* g, const int64_t* nodes_dev, int64_t m, cudaStream_t st,
+                              const std::function<mcf_status(void**, size_t)>& alloc, SubList* out) {
+    const int64_t n = g->n;
+    long long* first;
+    int64_t *cnt, *ptr;
+    void *stmp, *rowv, *svalv = nullptr;
+    const size_t sbytes = scan_tmp_bytes(n);
+    MCF_TRY(alloc((void**)&first, std::max<int64_t>(n, 1) * sizeof(long long)));
+    MCF_TRY(alloc((void**)&cnt, std::max<int64_t>(n, 1) * sizeof(int64_t)));
+    MCF_TRY(alloc((void**)&ptr, (n + 1) * sizeof(int64_t)));
+    MCF_TRY(alloc(&stmp, sbytes));
+    MCF_CUDA_TRY(cudaMemsetAsync(first, 0xff, n * sizeof(long long), st));
+    MCF_CUDA_TRY(cudaMemsetAsync(cnt, 0, n * sizeof(int64_t), st));
+    sub_claim<<<grid_for(m, 256), 256, 0, st>>>(m, nodes_dev, first);
+    sub_count<<<grid_for(m, 256), 256, 0, st>>>(m, nodes_dev, first, g->row_ptr, g->col_idx, cnt);
+    MCF_TRY(scan_i64(cnt, ptr, n, ptr + n, stmp, sbytes, st));
+    int64_t pairs = 0;
+    MCF_CUDA_TRY(cudaMemcpyAsync(&pairs, ptr + n, sizeof(pairs), cudaMemcpyDeviceToHost, st));
+    MCF_CUDA_TRY(cudaStreamSynchronize(st));
+    MCF_TRY(alloc(&rowv, std::max<int64_t>(pairs, 1) * sizeof(int32_t)));
+    if (g->values) MCF_TRY(alloc(&svalv, std::max<int64_t>(pairs, 1) * sizeof(float)));
+    MCF_CUDA_TRY(cudaMemsetAsync(cnt, 0, n * sizeof(int64_t), st));
+    sub_fill<<<grid_for(m, 256), 256, 0, st>>>(m, nodes_dev, first, g->row_ptr, g->col_idx, g->values, ptr, cnt,
+                                               (int32_t*)rowv, (float*)svalv);
+    MCF_CUDA_TRY(cudaGetLastError());
+    *out = SubList{ptr, (const int32_t*)rowv, (const float*)svalv};
     return MCF_OK;
 }
 
@@ -1300,7 +1207,7 @@ static mcf_status solve_diag(mcf_graph* g, const mcf_params* p, const int64_t* n
     keep_pool_memory();
     Scratch sc(st);
     const int64_t* nodes_dev = nullptr;
-    uint8_t *need = nullptr, *want = nullptr;
+    uint8_t* need = nullptr;
     if (nodes && m > 0) {
         if (is_device_ptr(nodes)) nodes_dev = nodes;
         else {
@@ -1312,9 +1219,7 @@ static mcf_status solve_diag(mcf_graph* g, const mcf_params* p, const int64_t* n
             nodes_dev = nd;
         }
         MCF_TRY(sc.get(&need, n));
-        MCF_TRY(sc.get(&want, n));
         MCF_CUDA_TRY(cudaMemsetAsync(need, 0, n, st));
-        MCF_CUDA_TRY(cudaMemsetAsync(want, 0, n, st));
     }
     const bool d_on_dev = is_device_ptr(d);
     double* d_dev = d;
@@ -1331,7 +1236,15 @@ static mcf_status solve_diag(mcf_graph* g, const mcf_params* p, const int64_t* n
         MCF_CUDA_TRY(cudaStreamSynchronize(st));
         if (h & 2ull) return fail(MCF_ERR_INVALID_ARG, "node index out of range");
     }
-    if (nodes_dev) mark_nodes<<<grid_for(m, 256), 256, 0, st>>>(m, nodes_dev, g->row_ptr, g->col_idx, need, want);
+    SubList sub{nullptr, nullptr, nullptr};
+    if (nodes_dev) {
+        mark_nodes<<<grid_for(m, 256), 256, 0, st>>>(m, nodes_dev, g->row_ptr, g->col_idx, need);
+        // per-column lists of the requested rows (Section 3.3: only the
+        // columns k with a_ik != 0 for a requested i, and of each only those i)
+        MCF_TRY(build_subset_lists(g, nodes_dev, m, st, [&](void** q, size_t bytes) {
+                    return sc.get((char**)q, bytes);
+                }, &sub));
+    }
     Prep P;
     MCF_TRY(prepare(g, p, gamma, nullptr, need, sc, P, st));
     double* dacc;
@@ -1350,12 +1263,11 @@ static mcf_status solve_diag(mcf_graph* g, const mcf_params* p, const int64_t* n
             const bool dense = n <= DIAG_DENSE_MAX;
             // larger graphs: one 16-byte neighbour record per step (on a small
             // graph the node records and column indices stay in L1 and L2)
-            if (!f64 && !g->weighted && g->nnz >= DIAG_EDGE_MIN_NNZ && g->nnz < ((int64_t)1 << 32) &&
-                walk_tuning().diag_edge)
+            if (!f64 && !g->weighted && g->nnz >= DIAG_EDGE_MIN_NNZ && g->nnz < ((int64_t)1 << 32))
                 MCF_TRY(ensure_edge_rec(g, st));
             mcf_status rc;
             const int64_t nk_hint = p->walks_per_node > 0 ? p->walks_per_node : std::max<int64_t>(1, p->n_walks / std::max<int64_t>(n, 1));
-#define MCF_DIAG(F, W, D) rc = launch_diag<F, W, D>(g, P, want, gamma, K, p->w_cutoff, key, p->request_id, nk_hint, dacc, sc, st)
+#define MCF_DIAG(F, W, D) rc = launch_diag<F, W, D>(g, P, sub, gamma, K, p->w_cutoff, key, p->request_id, nk_hint, dacc, sc, st)
             if (f64) {
                 if (g->weighted) { if (dense) MCF_DIAG(true, true, true); else MCF_DIAG(true, true, false); }
                 else { if (dense) MCF_DIAG(true, false, true); else MCF_DIAG(true, false, false); }
@@ -1389,6 +1301,7 @@ __global__ void __launch_bounds__(128) walk_full_kernel(
     const int32_t* __restrict__ starts, const int64_t* __restrict__ woff, const int64_t* __restrict__ nw,
     const double* __restrict__ zeta_g, int K, double wc, float wc32, uint2 key, uint32_t req, int64_t n,
     double* __restrict__ Q, unsigned long long* __restrict__ counters) {
+    MCF_KERNEL_ENTRY();
     using real = typename std::conditional<F64, double, float>::type;
     __shared__ real zeta[MCF_MAX_COEFFS];
     __shared__ int64_t cur;
@@ -1446,6 +1359,7 @@ __global__ void __launch_bounds__(128) walk_full_kernel(
 // of Q is zero).
 __global__ void full_edge_coeffs(int64_t nnz, const int32_t* __restrict__ col, const float* __restrict__ val,
                                  const int64_t* __restrict__ nw, double gamma, double* __restrict__ ce) {
+    MCF_KERNEL_ENTRY();
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
         const int64_t Nm = nw[col[p]];
         ce[p] = Nm == 0 ? 0.0 : (gamma * (val ? (double)val[p] : 1.0)) / (double)Nm;
@@ -1505,6 +1419,7 @@ __global__ void __launch_bounds__(FULL_THREADS) full_epilogue(
     const int64_t* __restrict__ cp, const int32_t* __restrict__ ri, const float* __restrict__ cv,
     const double* __restrict__ Q, const double* __restrict__ ce, double gamma, double z0, double z1, int K,
     double* __restrict__ F) {
+    MCF_KERNEL_ENTRY();
     extern __shared__ double aq[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     const int64_t B = blockDim.x;
@@ -1633,6 +1548,7 @@ __global__ void __launch_bounds__(256) mc_classic_kernel(
     const int32_t* __restrict__ col, const WEntry* __restrict__ went, const double* __restrict__ v,
     const double* __restrict__ zeta_g, int K, double wc, uint2 key, uint32_t req, double* __restrict__ acc,
     unsigned long long* __restrict__ counters) {
+    MCF_KERNEL_ENTRY();
     __shared__ double zeta[MCF_MAX_COEFFS];
     for (int k = threadIdx.x; k <= K; k += blockDim.x) zeta[k] = zeta_g[k];
     __syncthreads();
@@ -1691,6 +1607,7 @@ __global__ void __launch_bounds__(256) mc_classic_kernel(
 }
 
 __global__ void mc_classic_finish(int64_t m, const double* __restrict__ acc, int64_t N, double* __restrict__ y) {
+    MCF_KERNEL_ENTRY();
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x)
         y[t] = acc[t] / (double)N;
 }
@@ -1794,26 +1711,33 @@ constexpr int64_t NOALLOC_MAX_NODES = MCF_NOALLOC_MAX_NODES;
 constexpr int64_t NOALLOC_MAX_WALKS = MCF_NOALLOC_MAX_WALKS;
 
 constexpr size_t na_align(size_t b) { return (b + 255) & ~(size_t)255; }
+constexpr size_t NOALLOC_SCAN_BYTES = scan_tmp_bytes_for(NOALLOC_MAX_NODES);
+// The carved layout, in the order solve_tc_noalloc takes it.
 constexpr size_t NOALLOC_BYTES =
     na_align(8 * NOALLOC_MAX_NODES) * 7 +                      // r, colnorm, nw, flag, woff, spos, acc
     na_align(4 * NOALLOC_MAX_NODES) +                          // starts
     na_align(8 * (NOALLOC_MAX_NODES + 1)) +                    // soff
     na_align(sizeof(Rec<true>) * NOALLOC_MAX_NODES) +          // node records (largest variant)
     na_align(4 * (NOALLOC_MAX_WALKS / WARP_CHUNK + 2)) +       // chunk table
-    na_align(8 * ((NOALLOC_MAX_NODES + 4095) / 4096 + 1)) +    // scan block totals
+    na_align(NOALLOC_SCAN_BYTES) +                             // scan block totals
     na_align(8 * (RED_BLOCKS + 1)) + na_align(8 * N_COUNTERS) + na_align(8 * MCF_MAX_COEFFS) +
     na_align(8 * 4);                                           // partials, counters, coefficients, check flags
+static_assert(sizeof(Rec<true>) >= sizeof(Rec<false>), "the record slot holds either variant");
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 
-// Device address of g_noalloc_scratch, looked up once per device (the host
-// symbol is only a stand-in and must never be handed to a kernel).
+// Device address of g_noalloc_scratch, looked up once per device with that
+// device current (the host symbol is only a stand-in and must never be handed
+// to a kernel).  The cached address belongs to the context it was taken in,
+// so the library must not be used across a cudaDeviceReset.
 static void* g_noalloc_base[64] = {};
+static std::mutex g_noalloc_mu;
 
 static mcf_status noalloc_base(void** out) {
     int dev = 0;
     MCF_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return fail(MCF_ERR_UNSUPPORTED, "device ordinal above 63");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
     if (!g_noalloc_base[dev]) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
@@ -1840,6 +1764,7 @@ struct Carve {
 // [0, nnz], columns in [0, n) and strictly increasing within a row.
 __global__ void noalloc_check_csr(int64_t n, int64_t nnz, const int64_t* __restrict__ rp,
                                   const int32_t* __restrict__ col, unsigned long long* __restrict__ bad) {
+    MCF_KERNEL_ENTRY();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t b = rp[i], e = rp[i + 1];
         if ((i == 0 && b != 0) || (i == n - 1 && e != nnz) || b < 0 || b > e || e > nnz) {
@@ -1870,11 +1795,13 @@ static mcf_status solve_tc_noalloc(int64_t n, int64_t nnz, const int64_t* row_pt
     if (p->n_walks < 0 || p->walks_per_node < 0) return fail(MCF_ERR_INVALID_ARG, "walk counts must be >= 0");
     if (p->n_coeffs > 2 && p->n_walks == 0 && p->walks_per_node == 0)
         return fail(MCF_ERR_INVALID_ARG, "n_walks or walks_per_node must be > 0");
-    const int64_t bound = p->walks_per_node > 0 ? p->walks_per_node * n : p->n_walks + n;
-    if (p->walks_per_node > NOALLOC_MAX_WALKS || bound > NOALLOC_MAX_WALKS)
-        return fail(MCF_ERR_INVALID_ARG, "the walk count (up to " + std::to_string(bound) +
-                                             ") exceeds the allocation-free limit of " +
-                                             std::to_string(NOALLOC_MAX_WALKS) + " walks");
+    // walk ids run up to N_s + n (rounding) or walks_per_node * n; compared
+    // without forming the sums, which could overflow for huge requests
+    const bool too_many = p->walks_per_node > 0 ? (n > 0 && p->walks_per_node > NOALLOC_MAX_WALKS / n)
+                                                : p->n_walks > NOALLOC_MAX_WALKS - n;
+    if (too_many)
+        return fail(MCF_ERR_INVALID_ARG, "the walk count (N_s + n, or walks_per_node * n) exceeds the allocation-free "
+                                         "limit of " + std::to_string(NOALLOC_MAX_WALKS) + " walks");
     if (!(p->w_cutoff >= 0.0)) return fail(MCF_ERR_INVALID_ARG, "w_cutoff must be >= 0");
     if (p->precision != MCF_F64 && p->precision != MCF_F32W_F64ACC)
         return fail(MCF_ERR_INVALID_ARG, "unknown precision");
@@ -1906,7 +1833,7 @@ static mcf_status solve_tc_noalloc(int64_t n, int64_t nnz, const int64_t* row_pt
     P.cof = P.soff;   // every start is walked: walk ids and walked space coincide
     P.rec = cv.take<Rec<true>>(NOALLOC_MAX_NODES);
     uint32_t* chunk_s0 = cv.take<uint32_t>(NOALLOC_MAX_WALKS / WARP_CHUNK + 2);
-    P.scan_bytes = 8 * ((NOALLOC_MAX_NODES + 4095) / 4096 + 1);
+    P.scan_bytes = NOALLOC_SCAN_BYTES;
     P.scan_tmp = cv.take<char>(P.scan_bytes);
     P.part = cv.take<double>(RED_BLOCKS + 1);
     P.counters = cv.take<unsigned long long>(N_COUNTERS);
@@ -1958,6 +1885,8 @@ static mcf_status solve_tc_noalloc(int64_t n, int64_t nnz, const int64_t* row_pt
 }  // namespace mcf
 
 using namespace mcf;
+
+uint64_t mcf::kernel_runs_walk() { return this_unit_kernel_runs(); }
 
 extern "C" {
 

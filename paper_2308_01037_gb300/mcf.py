@@ -67,7 +67,8 @@ class mcf_server_stats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("rejected", ctypes.c_int64),
                 ("batches", ctypes.c_int64), ("walk_steps", ctypes.c_int64), ("p50_ms", ctypes.c_double),
                 ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
-                ("busy_s", ctypes.c_double)]
+                ("busy_s", ctypes.c_double), ("device_overlap_ms", ctypes.c_double),
+                ("max_concurrent_batches", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -106,7 +107,12 @@ SIGNATURES = {
     "mcf_server_wait": ([_P, ctypes.c_uint64, _D, _P, _P], ctypes.c_int),
     "mcf_server_get_stats": ([_P, _P], ctypes.c_int),
     "mcf_server_destroy": ([_P], ctypes.c_int),
+    "mcf_server_release": ([_P, ctypes.c_uint64], ctypes.c_int),
+    "mcf_query_footprint": ([_P, _P], ctypes.c_int),
+    "mcf_batch_device_bytes": ([_P, _P], ctypes.c_int),
     "mcf_total_communicability_noalloc": ([_I64, _I64, _P, _P, _P, _P], ctypes.c_int),
+    "mcf_gather_probe": ([_I64, _I64, _P, _P], ctypes.c_int),
+    "mcf_kernel_launches": ([_P], ctypes.c_int),
     "mcf_last_error": ([], ctypes.c_char_p),
     "mcf_version": ([], ctypes.c_char_p),
 }
@@ -469,6 +475,26 @@ def mcf_server_wait(s: ServerHandle, ticket: int, timeout_s: float = -1.0):
     return out, lat.value
 
 
+def mcf_server_release(s: ServerHandle, ticket: int):
+    """Forgets a completed request."""
+    _check(load().mcf_server_release(s.handle, ctypes.c_uint64(ticket)))
+    s.pending.pop(ticket, None)
+
+
+def mcf_query_footprint(query: dict) -> int:
+    """Device bytes the server charges a request (see mcf_batch_create for the dict)."""
+    st, out, keep = _query_struct(query)
+    b = ctypes.c_size_t()
+    _check(load().mcf_query_footprint(ctypes.byref(st), ctypes.byref(b)))
+    return int(b.value)
+
+
+def mcf_batch_device_bytes(b: BatchHandle) -> int:
+    out = ctypes.c_size_t()
+    _check(load().mcf_batch_device_bytes(b.handle, ctypes.byref(out)))
+    return int(out.value)
+
+
 def mcf_server_get_stats(s: ServerHandle) -> dict:
     st = mcf_server_stats()
     _check(load().mcf_server_get_stats(s.handle, ctypes.byref(st)))
@@ -488,6 +514,20 @@ def mcf_total_communicability_noalloc(n, row_ptr, col_idx, coeffs, out, **kw):
     p, kc = _params(coeffs, stream=kw.pop("stream", None) or _stream_of(out), **kw)
     _check(load().mcf_total_communicability_noalloc(int(n), nnz, rp, ci, ctypes.byref(p), yp))
     return out
+
+
+def mcf_gather_probe(array_bytes, reads, stream=None) -> float:
+    """Random 8-byte reads per second over a device array of ``array_bytes``."""
+    out = ctypes.c_double()
+    _check(load().mcf_gather_probe(int(array_bytes), int(reads), stream, ctypes.byref(out)))
+    return out.value
+
+
+def mcf_kernel_launches() -> int:
+    """Kernel executions of the library on the current device since it was loaded."""
+    out = ctypes.c_uint64()
+    _check(load().mcf_kernel_launches(ctypes.byref(out)))
+    return int(out.value)
 
 
 def mcf_last_error() -> str:

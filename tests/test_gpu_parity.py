@@ -169,6 +169,50 @@ def test_subgraph_centrality_hashed_row_with_flushes(precision):
     assert_parity(d, ref["d"])
 
 
+@pytest.mark.timeout(600)
+def test_subgraph_centrality_subset_hashed_rows_neighbour_records():
+    """A node subset on a graph with >= 2^20 entries and n > 16384: hashed rows
+    Q_k, 16-byte neighbour records and the per-column lists of requested rows
+    together.  Nodes: the top hub, three of its neighbours, a low-degree node,
+    an isolated node if any, and a duplicate; only the columns adjacent to them
+    are walked, and the dot phase of a hub column touches only the listed rows."""
+    g = I.rmat(16, 16, seed=9)
+    assert g.nnz >= 1 << 20 and g.n > 16384
+    gam = 1.0 / R.lambda_max(g)
+    h = upload(g)
+    c = R.exp_coeffs(30)
+    hub = int(np.argmax(g.degree))
+    nbrs = g.col_idx[g.row_ptr[hub]:g.row_ptr[hub + 1]]
+    low = int(np.nonzero(g.degree == 1)[0][0]) if np.any(g.degree == 1) else 3
+    iso = np.nonzero(g.degree == 0)[0]
+    nodes = [hub, int(nbrs[0]), int(nbrs[len(nbrs) // 2]), int(nbrs[-1]), low, hub]
+    if iso.size:
+        nodes.append(int(iso[0]))
+    nodes = np.array(nodes, dtype=np.int64)
+    kw = dict(scale=gam, walks_per_node=16, w_cutoff=1e-6, seed=12, precision=M.MCF_F32W_F64ACC)
+    d, st = M.mcf_subgraph_centrality(h, c, nodes=nodes, stats=True, **kw)
+    ref = E.diag(g, c, gamma=gam, walks_per_node=16, w_cutoff=1e-6, seed=12, precision=1, nodes=nodes)
+    assert_parity(d, ref["d"])
+    assert st["walks"] == ref["walks"] and st["walk_steps"] == ref["steps"]
+    # the same entries from device-resident indices
+    d2 = M.mcf_subgraph_centrality(h, c, nodes=torch.from_numpy(nodes).cuda(), **kw)
+    assert_parity(d2.cpu().numpy(), ref["d"])
+
+
+def test_subgraph_centrality_subset_weighted_signed():
+    """The per-column lists carry the entries a_ik of a weighted, signed A."""
+    g = I.barabasi_albert(400, 3, 5)
+    vals = I.symmetric_weights(g, seed=6, signed=True)
+    h = upload(g, vals)
+    gam = 0.05
+    c = R.exp_coeffs(12)
+    nodes = np.array([0, 7, 399, 7, 123], dtype=np.int64)
+    for precision in (M.MCF_F64, M.MCF_F32W_F64ACC):
+        d = M.mcf_subgraph_centrality(h, c, nodes=nodes, scale=gam, walks_per_node=200, seed=8, precision=precision)
+        ref = E.diag(g, c, gamma=gam, walks_per_node=200, seed=8, precision=precision, nodes=nodes, values=vals)
+        assert_parity(d, ref["d"])
+
+
 def test_subgraph_centrality_subset_equals_full(ba1000):
     g, h, gam = ba1000
     c = R.exp_coeffs(30)

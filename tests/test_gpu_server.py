@@ -2,8 +2,10 @@
 
 Requests submitted concurrently are grouped into batches that run on several
 streams at once; each request keeps its own walk ids, so its result must equal
-the single call's (parity tolerance 1e-12 relative) whatever it was batched
-with.  Admission by device footprint and the latency counters are checked too.
+the oracle's same-seed estimate and the single call's (parity tolerance 1e-12
+relative) whatever it was batched with, and batches' device work must overlap
+in time.  Admission by device footprint (checked against what a batch really
+allocates), releasing tickets and the latency counters are checked too.
 """
 import threading
 
@@ -12,6 +14,7 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
+from oracle import estimator as E
 from oracle import reference as R
 from paper_2308_01037_gb300 import inputs as I
 from paper_2308_01037_gb300 import mcf as M
@@ -61,6 +64,21 @@ def single(q):
     return M.mcf_action(q["graph"], q["v"], q["coeffs"], **kw)
 
 
+def oracle_of(q, pool):
+    """The oracle's same-seed estimate of a served request (float32 walk weights)."""
+    g = next(gg for gg, hh, _ in pool if hh is q["graph"])
+    kw = dict(seed=q["seed"], request_id=q["request_id"], precision=1)
+    if q["kind"] == M.MCF_QUERY_TOTAL_COMMUNICABILITY:
+        return E.action(g, q["coeffs"], gamma=q["scale"], n_walks=q["n_walks"], w_cutoff=q["w_cutoff"], **kw)["y"]
+    if q["kind"] == M.MCF_QUERY_KATZ:
+        # K from the tail bound with the library's lambda_max (the value mcf_katz uses)
+        K = R.katz_terms_for_tail(q["katz_gamma"] * M.mcf_spectral_radius(q["graph"]), 1e-4)
+        return E.action(g, R.katz_coeffs(K), gamma=q["katz_gamma"], walks_per_node=q["walks_per_node"], **kw)["y"]
+    if q["kind"] == M.MCF_QUERY_SUBGRAPH_CENTRALITY:
+        return E.diag(g, q["coeffs"], gamma=q["scale"], walks_per_node=q["walks_per_node"], nodes=q["nodes"], **kw)["d"]
+    return E.action(g, q["coeffs"], v=q["v"], gamma=q["scale"], n_walks=q["n_walks"], **kw)["y"]
+
+
 def test_results_in_the_mix_equal_results_alone(pool):
     rng = np.random.default_rng(0)
     qs = [request(pool, i, rng) for i in range(48)]
@@ -82,17 +100,70 @@ def test_results_in_the_mix_equal_results_alone(pool):
     assert st["completed"] == len(qs) and st["rejected"] == 0
     assert st["batches"] >= 2 and 0 < st["p50_ms"] <= st["p99_ms"] <= st["max_ms"]
     for q, (out, lat) in zip(qs, outs):
-        ref = single(q)
-        err = np.abs(np.asarray(out) - ref)
-        assert np.all(err <= RTOL * np.abs(ref) + ATOL)
+        out = np.asarray(out)
+        for ref in (oracle_of(q, pool), single(q)):
+            assert np.all(np.abs(out - ref) <= RTOL * np.abs(ref) + ATOL), q["kind"]
         assert lat > 0
+
+
+def test_batches_overlap_on_the_device(pool):
+    """Two long requests handed to two workers at once: the second batch's
+    first kernel runs before the first batch's last kernel has finished (the
+    device windows from the GPU's global timer overlap), and both results
+    equal the oracle's."""
+    g, h, gam = pool[1]
+    c = R.exp_coeffs(30)
+    qs = [dict(graph=h, kind=M.MCF_QUERY_TOTAL_COMMUNICABILITY, coeffs=c, scale=gam, n_walks=400 * g.n,
+               w_cutoff=1e-6, seed=77 + i, request_id=900 + i, precision=M.MCF_F32W_F64ACC) for i in range(2)]
+    srv = M.mcf_server_create(hbm_budget_bytes=8 << 30, max_inflight=2, max_batch=1)
+    tickets = [M.mcf_server_submit(srv, q) for q in qs]
+    outs = [M.mcf_server_wait(srv, t, timeout_s=120.0)[0] for t in tickets]
+    st = M.mcf_server_get_stats(srv)
+    srv.close()
+    assert st["batches"] == 2
+    assert st["max_concurrent_batches"] == 2 and st["device_overlap_ms"] > 0.0, st
+    for q, out in zip(qs, outs):
+        ref = oracle_of(q, pool)
+        assert np.all(np.abs(np.asarray(out) - ref) <= RTOL * np.abs(ref) + ATOL)
+
+
+def test_footprint_covers_what_a_batch_allocates(pool):
+    """The admission estimate of a request is at least the device memory
+    mcf_batch_create allocates for a batch of that request alone (and not
+    more than twice that plus 64 MiB for the fused kinds)."""
+    rng = np.random.default_rng(3)
+    for i in range(8):
+        q = request(pool, i, rng)
+        q["out"] = torch.empty(len(q["nodes"]) if "nodes" in q else q["graph"].n, dtype=torch.float64,
+                               device="cuda")
+        est = M.mcf_query_footprint(q)
+        b = M.mcf_batch_create([q])
+        got = M.mcf_batch_device_bytes(b)
+        b.close()
+        assert est >= got, (i, est, got)
+        if q["kind"] != M.MCF_QUERY_ACTION:
+            assert est <= 2 * got + (64 << 20), (i, est, got)
+
+
+def test_released_tickets_are_forgotten(pool):
+    g, h, gam = pool[0]
+    srv = M.mcf_server_create(hbm_budget_bytes=1 << 30, max_inflight=1, max_batch=2)
+    t = M.mcf_server_submit(srv, dict(graph=h, kind=M.MCF_QUERY_TOTAL_COMMUNICABILITY, coeffs=R.exp_coeffs(10),
+                                      scale=gam, n_walks=1000, seed=1))
+    M.mcf_server_wait(srv, t, timeout_s=60.0)
+    M.mcf_server_release(srv, t)
+    with pytest.raises(M.McfError):
+        M.mcf_server_poll(srv, t)
+    with pytest.raises(M.McfError):
+        M.mcf_server_release(srv, t)
+    srv.close()
 
 
 def test_admission_by_memory_budget(pool):
     g, h, gam = pool[1]
-    srv = M.mcf_server_create(hbm_budget_bytes=1 << 20, max_inflight=1, max_batch=4)
-    t = M.mcf_server_submit(srv, dict(graph=h, kind=M.MCF_QUERY_TOTAL_COMMUNICABILITY, coeffs=R.exp_coeffs(10),
-                                      scale=gam, n_walks=1000))
+    q = dict(graph=h, kind=M.MCF_QUERY_TOTAL_COMMUNICABILITY, coeffs=R.exp_coeffs(10), scale=gam, n_walks=1000)
+    srv = M.mcf_server_create(hbm_budget_bytes=M.mcf_query_footprint(q) - 1, max_inflight=1, max_batch=4)
+    t = M.mcf_server_submit(srv, q)
     done, res = M.mcf_server_poll(srv, t)
     assert done and res == 5   # MCF_ERR_ADMISSION
     with pytest.raises(M.McfError):
@@ -107,9 +178,8 @@ def test_requests_queue_until_memory_frees(pool):
     c = R.exp_coeffs(20)
     qs = [dict(graph=h, kind=M.MCF_QUERY_TOTAL_COMMUNICABILITY, coeffs=c, scale=gam, n_walks=10 * g.n, seed=i,
                request_id=i) for i in range(6)]
-    # the server's device-footprint estimate of one such request (per-node
-    # scratch, chunk table, degree table, fixed part); 1.5 of it admits one at a time
-    one = 112 * g.n + (10 * g.n + g.n) // 8 + 4 * (int(g.degree.max()) + 1) + (1 << 20)
+    # the server's device-footprint estimate of one such request; 1.5 of it admits one at a time
+    one = M.mcf_query_footprint(qs[0])
     srv = M.mcf_server_create(hbm_budget_bytes=int(1.5 * one), max_inflight=2, max_batch=8)
     tickets = [M.mcf_server_submit(srv, q) for q in qs]
     outs = [M.mcf_server_wait(srv, t, timeout_s=60.0)[0] for t in tickets]
