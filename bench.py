@@ -62,11 +62,6 @@ WORKLOADS = {
 # subgraph centrality reads 12 B (no r_l) and reduces into the L2-resident row Q_k.
 ALGO_BYTES_PER_STEP = {"tc": 16, "sc": 12}
 KERNEL = {"tc": "walk_tc_kernel", "sc": "walk_diag_kernel"}
-# Kernels one solve launches: 12 of preparation (r, column norms and their
-# sum, allocation, two three-kernel scans, start compaction, node records),
-# then chunk table, degree table, walks, 1/N_i and the epilogue (total
-# communicability) or walks and the finishing pass (subgraph centrality).
-LAUNCHES_PER_SOLVE = {"tc": 17, "sc": 14}
 # DRAM bytes (read + write) per walk step of walk_tc_kernel from one ncu
 # capture of the R-MAT scale 21 profiling case (7.785e9 B over 264,240,439
 # steps of one launch); a launch of the larger case is scaled by its steps.
@@ -279,20 +274,47 @@ def aggregate(ms, steps, device="cpu"):
     return float(t.item()), float(s.item())
 
 
-def batch_queries(M, R, I, n_graphs, log_n_max, seed=3, katz_rule="gershgorin"):
+# ---------------------------------------------------------------- accuracy-targeted walk budgets
+# Every batched and served query runs with a walk budget calibrated once per
+# (graph, kind): one accuracy-targeted solve (params.target_rel_err) from a
+# small pilot budget returns how many replicas of it met the target; the
+# query's budget is that many times the pilot.  The target sits a factor 4
+# below the 1e-3 bar because the library's estimate is the spread of the
+# error, not a bound.
+CAL_TARGET = 2.5e-4
+KINDS = ("tc", "sc", "katz")
+
+
+def calibrate(M, solve, pilot, cap):
+    """(calibrated budget, budget met, estimated error, replicas) from one
+    accuracy-targeted solve with ``pilot`` walks per replica."""
+    _, st = solve(dict(pilot, target_rel_err=CAL_TARGET, max_walks=cap))
+    key = "walks_per_node" if pilot.get("walks_per_node", 0) > 0 else "n_walks"
+    return {key: int(pilot[key]) * int(st["replicas"])}, bool(st["budget_met"]), float(st["est_rel_err"]), \
+        int(st["replicas"])
+
+
+def query_solver(M, h, kind, coeffs=None, gamma=None, katz_gamma=None, nodes=None):
+    """A one-argument single-query solve (kwargs -> (result, stats)) for calibration."""
+    if kind == "tc":
+        return lambda kw: M.mcf_total_communicability(h, coeffs, scale=gamma, stats=True, **kw)
+    if kind == "katz":
+        return lambda kw: M.mcf_katz(h, katz_gamma, 0, stats=True, **kw)
+    return lambda kw: M.mcf_subgraph_centrality(h, coeffs, nodes=nodes, scale=gamma, stats=True, **kw)
+
+
+def batch_queries(M, R, I, n_graphs, log_n_max, seed=3):
     """The mixed multi-graph workload: n = round(10^U[3, log_n_max]); half
     Barabasi-Albert (m in 2..8), half Erdos-Renyi (mean degree U[8, 32]);
     queries cycle total communicability exp(A/lambda)1, subgraph centrality
-    diag exp(A/lambda) and Katz, float32 walk weights.  Walk budgets are set
-    for a relative l_inf error near 1e-3 (measured with the oracle on BA and ER
-    graphs: about 1000 walks per node for TC and Katz, 64 for SC).  Katz uses
-    gamma = 0.85 / max_i sum_k |a_ik| (the Gershgorin bound of Section 4.5, for
-    which Theorem 1's variance condition holds) or, with katz_rule="lambda",
-    gamma = 0.85 / lambda_max."""
+    diag exp(A/lambda) and Katz with gamma = 0.85 / lambda_max, float32 walk
+    weights, each with a walk budget calibrated to 1e-3 (CAL_TARGET)."""
     rng = np.random.default_rng(seed)
-    graphs, qs = [], []
+    graphs, qs, cal = [], [], []
     c = exp_coeffs(30)
+    t_gen = t_cal = 0.0
     for j in range(n_graphs):
+        t0 = time.perf_counter()
         n = int(round(10 ** rng.uniform(3, log_n_max)))
         if j % 2 == 0:
             g = I.barabasi_albert(n, int(rng.integers(2, 9)), seed + j)
@@ -301,18 +323,30 @@ def batch_queries(M, R, I, n_graphs, log_n_max, seed=3, katz_rule="gershgorin"):
         h = M.mcf_create_graph(g.n, g.row_ptr, g.col_idx)
         lam = M.mcf_spectral_radius(h, tol=1e-10, max_iter=10000)
         graphs.append((g, h, lam))
+        t1 = time.perf_counter()
+        t_gen += t1 - t0
         base = dict(graph=h, seed=seed * 1000 + j, request_id=j, precision=M.MCF_F32W_F64ACC)
-        kind = j % 3
-        if kind == 0:
-            qs.append(dict(base, kind=M.MCF_QUERY_TOTAL_COMMUNICABILITY, coeffs=c, scale=1.0 / lam,
-                           n_walks=1024 * g.n, w_cutoff=1e-6))
-        elif kind == 1:
-            qs.append(dict(base, kind=M.MCF_QUERY_SUBGRAPH_CENTRALITY, coeffs=c, scale=1.0 / lam, walks_per_node=64,
-                           w_cutoff=1e-6))
+        kind = KINDS[j % 3]
+        common = dict(seed=base["seed"], request_id=j, precision=M.MCF_F32W_F64ACC)
+        if kind == "tc":
+            pilot = dict(common, n_walks=g.n, w_cutoff=1e-6)
+            budget, met, est, reps = calibrate(M, query_solver(M, h, "tc", c, 1.0 / lam), pilot, 4096 * g.n)
+            qs.append(dict(base, kind=M.MCF_QUERY_TOTAL_COMMUNICABILITY, coeffs=c, scale=1.0 / lam, w_cutoff=1e-6,
+                           **budget))
+        elif kind == "sc":
+            pilot = dict(common, walks_per_node=4, w_cutoff=1e-6)
+            budget, met, est, reps = calibrate(M, query_solver(M, h, "sc", c, 1.0 / lam), pilot, 4096 * g.n)
+            qs.append(dict(base, kind=M.MCF_QUERY_SUBGRAPH_CENTRALITY, coeffs=c, scale=1.0 / lam, w_cutoff=1e-6,
+                           **budget))
         else:
-            kg = 0.85 / (lam if katz_rule == "lambda" else M.mcf_gershgorin(h))
-            qs.append(dict(base, kind=M.MCF_QUERY_KATZ, katz_gamma=kg, katz_terms=0, walks_per_node=1024))
-    return graphs, qs
+            kg = 0.85 / lam
+            pilot = dict(common, walks_per_node=4)
+            budget, met, est, reps = calibrate(M, query_solver(M, h, "katz", katz_gamma=kg), pilot, 256 * g.n)
+            qs.append(dict(base, kind=M.MCF_QUERY_KATZ, katz_gamma=kg, katz_terms=0, **budget))
+        cal.append({"kind": kind, "n": g.n, "budget_met": met, "est_rel_err": est, "replicas": reps})
+        t_cal += time.perf_counter() - t1
+    log(f"[bench] batch graphs generated and uploaded in {t_gen:.1f}s, budgets calibrated in {t_cal:.1f}s")
+    return graphs, qs, cal
 
 
 def solve_single(M, q):
@@ -325,66 +359,96 @@ def solve_single(M, q):
     return M.mcf_subgraph_centrality(q["graph"], q["coeffs"], nodes=q.get("nodes"), out=q.get("out"), **kw)
 
 
-def run_batched(M, R, I, n_graphs, log_n_max, reps=3):
+def _kind_of(M, q):
+    return {M.MCF_QUERY_TOTAL_COMMUNICABILITY: "tc", M.MCF_QUERY_KATZ: "katz",
+            M.MCF_QUERY_SUBGRAPH_CENTRALITY: "sc"}[q["kind"]]
+
+
+def run_batched(M, R, I, n_graphs, log_n_max, reps=2):
     """Solves/s of the batch (plain and CUDA-graph replay) against the same
-    queries solved one at a time, and the worst relative error of a sample of
-    queries against the float64 series."""
+    queries solved one at a time, for the whole mix and for each kind alone;
+    budgets calibrated to 1e-3; the worst relative error per kind against the
+    float64 series on the graphs up to 1e5 nodes (subgraph centrality on 32
+    sampled nodes of each); Katz at gamma = 0.85 /
+    lambda_max with the second-moment radius rho(diag(s')|A'|) per graph and
+    the queries whose calibration stopped at the walk cap."""
     import torch
 
     t = time.time()
-    graphs, qs = batch_queries(M, R, I, n_graphs, log_n_max)
-    log(f"[bench] batch workload: {len(qs)} graphs, sum n = {sum(g.n for g, _, _ in graphs)} ({time.time() - t:.1f}s)")
+    graphs, qs, cal = batch_queries(M, R, I, n_graphs, log_n_max)
+    log(f"[bench] batch workload: {len(qs)} graphs, sum n = {sum(g.n for g, _, _ in graphs)}, calibrated "
+        f"({time.time() - t:.1f}s)")
     for q, (g, _, _) in zip(qs, graphs):
         q["out"] = torch.empty(g.n, dtype=torch.float64, device="cuda")
-    for q in qs[:3]:
-        solve_single(M, q)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(reps):
-        for q in qs:
+    res = {"queries": len(qs), "sum_n": int(sum(g.n for g, _, _ in graphs))}
+
+    def time_single(sel):
+        for q in sel[:2]:
             solve_single(M, q)
-    torch.cuda.synchronize()
-    t_single = (time.perf_counter() - t0) / reps
-    res = {"queries": len(qs), "sum_n": int(sum(g.n for g, _, _ in graphs)),
-           "one_at_a_time_solves_per_s": len(qs) / t_single}
-    for name, flags in (("batched", M.MCF_BATCH_AUTOTUNE), ("batched_cuda_graph", M.MCF_BATCH_CUDA_GRAPH | M.MCF_BATCH_AUTOTUNE)):
-        b = M.mcf_batch_create(qs, flags=flags)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            for q in sel:
+                solve_single(M, q)
+        torch.cuda.synchronize()
+        return len(sel) / ((time.perf_counter() - t0) / reps)
+
+    def time_batch(sel, flags):
+        b = M.mcf_batch_create(sel, flags=flags)
         M.mcf_batch_run(b)
         t0 = time.perf_counter()
         for _ in range(reps):
             _, st = M.mcf_batch_run(b, stats=True)
         el = (time.perf_counter() - t0) / reps
-        res[name + "_solves_per_s"] = len(qs) / el
-        res[name + "_walk_steps_per_s"] = st["walk_steps"] / el
         b.close()
-    # accuracy of the batch results (last run) on the smaller graphs, per kind
-    errs = {"tc": [], "sc": [], "katz": []}
-    for q, (g, h, lam) in zip(qs, graphs):
-        if g.n > 200_000:
+        return len(sel) / el, st["walk_steps"] / el
+
+    per_kind = {}
+    for kind in ("all",) + KINDS:
+        t0 = time.perf_counter()
+        sel = qs if kind == "all" else [q for q in qs if _kind_of(M, q) == kind]
+        one = time_single(sel)
+        cg, steps = time_batch(sel, M.MCF_BATCH_CUDA_GRAPH | M.MCF_BATCH_AUTOTUNE)
+        per_kind[kind] = {"queries": len(sel), "one_at_a_time_solves_per_s": one,
+                          "batched_cuda_graph_solves_per_s": cg, "speedup": cg / one}
+        if kind == "all":
+            bat, _ = time_batch(sel, M.MCF_BATCH_AUTOTUNE)
+            per_kind[kind]["batched_solves_per_s"] = bat
+            res["batched_cuda_graph_walk_steps_per_s"] = steps
+        log(f"[bench] batch timing ({kind}): {time.perf_counter() - t0:.1f}s")
+    res["solves_per_s"] = per_kind
+    res["speedup_vs_one_at_a_time"] = per_kind["all"]["speedup"]
+    # accuracy of the batch results (last run) on the graphs up to 1e5 nodes, per kind
+    errs = {k: [] for k in KINDS}
+    miss = {k: [] for k in KINDS}
+    rho2 = []
+    for q, (g, h, lam), cl in zip(qs, graphs, cal):
+        kind = _kind_of(M, q)
+        if kind == "katz":
+            rho2.append(M.mcf_second_moment_radius(h, q["katz_gamma"], tol=1e-4, max_iter=500))
+        if g.n > 100_000:
             continue
         y = q["out"].cpu().numpy()
-        if q["kind"] == M.MCF_QUERY_TOTAL_COMMUNICABILITY:
-            ref, kind = R.series_action(g, exp_coeffs(30), 1.0 / lam), "tc"
-        elif q["kind"] == M.MCF_QUERY_KATZ:
-            rho = q["katz_gamma"] * lam
-            K = R.katz_terms_for_tail(rho, 1e-4)
-            ref, kind = R.series_action(g, R.katz_coeffs(K), q["katz_gamma"]), "katz"
+        if kind == "tc":
+            ref = R.series_action(g, exp_coeffs(30), 1.0 / lam)
+        elif kind == "katz":
+            K = R.katz_terms_for_tail(q["katz_gamma"] * lam, 1e-4)
+            ref = R.series_action(g, R.katz_coeffs(K), q["katz_gamma"])
         else:
-            nodes = np.arange(0, g.n, max(1, g.n // 256))
-            ref, kind = R.series_diag(g, exp_coeffs(30), nodes, 1.0 / lam), "sc"
-            y = y[nodes]
-        errs[kind].append(float(np.abs(y - ref).max() / np.abs(ref).max()))
+            nodes = np.arange(0, g.n, max(1, g.n // 32))
+            ref, y = R.series_diag(g, exp_coeffs(30), nodes, 1.0 / lam), y[nodes]
+        e = float(np.abs(y - ref).max() / np.abs(ref).max())
+        (errs if cl["budget_met"] else miss)[kind].append(e)
     res["max_rel_err_vs_fp64"] = {k: (max(v) if v else None) for k, v in errs.items()}
-    res["katz_gamma"] = "0.85 / max_i sum_k |a_ik| (Gershgorin, Section 4.5)"
-    # the same Katz query with gamma = 0.85 / lambda_max on the smallest BA graph:
-    # Theorem 1's condition fails there and the walk weights' variance explodes
-    j = min((k for k in range(len(qs)) if k % 2 == 0), key=lambda k: graphs[k][0].n)
-    g, h, lam = graphs[j]
-    y = M.mcf_katz(h, 0.85 / lam, 0, walks_per_node=64, seed=1, precision=M.MCF_F32W_F64ACC)
-    K = R.katz_terms_for_tail(0.85, 1e-4)
-    ref = R.series_action(g, R.katz_coeffs(K), 0.85 / lam)
-    res["katz_lambda_gamma_rel_err"] = float(np.abs(y - ref).max() / np.abs(ref).max())
-    res["speedup_vs_one_at_a_time"] = res["batched_cuda_graph_solves_per_s"] / res["one_at_a_time_solves_per_s"]
+    res["budget_misses_rel_err_vs_fp64"] = {k: (max(v) if v else None) for k, v in miss.items()}
+    res["calibration"] = {
+        "target_rel_err": CAL_TARGET,
+        "budget_met": {k: sum(1 for c_ in cal if c_["kind"] == k and c_["budget_met"]) for k in KINDS},
+        "budget_missed": {k: sum(1 for c_ in cal if c_["kind"] == k and not c_["budget_met"]) for k in KINDS},
+        "median_replicas": {k: float(np.median([c_["replicas"] for c_ in cal if c_["kind"] == k] or [0])) for k in KINDS}}
+    res["katz_gamma"] = "0.85 / lambda_max"
+    res["katz_second_moment_radius"] = {"min": float(min(rho2)), "median": float(np.median(rho2)),
+                                        "max": float(max(rho2)), "above_1": int(sum(r > 1 for r in rho2))} if rho2 else None
     for _, h, _ in graphs:
         h.close()
     return res
@@ -392,39 +456,47 @@ def run_batched(M, R, I, n_graphs, log_n_max, reps=3):
 
 def run_serving(M, R, I, scales, n_requests, rate=200.0, seed=5):
     """Poisson arrivals (rate req/s) over a resident R-MAT pool; query mix 50%
-    total communicability, 30% Katz, 20% subgraph centrality on 10^4 sampled
-    nodes; p50/p99 latency from the server's counters."""
+    total communicability, 30% Katz (gamma = 0.85 / max_i sum_k |a_ik|, the
+    paper's setting), 20% subgraph centrality on 10^4 sampled nodes; walk
+    budgets calibrated per graph and kind to 1e-3; p50/p99 latency from the
+    server's counters, device overlap of batches, errors on sampled graphs."""
     t = time.time()
     pool = []
+    c = exp_coeffs(30)
+    rng = np.random.default_rng(seed)
     for sc in scales:
         g = I.rmat(sc, 16, seed=sc)
         h = M.mcf_create_graph(g.n, g.row_ptr, g.col_idx)
         lam = M.mcf_spectral_radius(h, tol=1e-10, max_iter=10000)
-        pool.append((g, h, lam))
-    log(f"[bench] serving pool: R-MAT scales {scales[0]}..{scales[-1]} ({time.time() - t:.1f}s)")
-    rng = np.random.default_rng(seed)
-    c = exp_coeffs(30)
+        kg = 0.85 / M.mcf_gershgorin(h)
+        nodes = rng.choice(g.n, size=min(10_000, g.n), replace=False).astype(np.int64)
+        common = dict(seed=seed, request_id=0, precision=M.MCF_F32W_F64ACC)
+        budgets = {
+            "tc": calibrate(M, query_solver(M, h, "tc", c, 1.0 / lam), dict(common, n_walks=g.n // 4, w_cutoff=1e-6),
+                            1024 * g.n)[0],
+            "katz": calibrate(M, query_solver(M, h, "katz", katz_gamma=kg), dict(common, walks_per_node=1),
+                              1024 * g.n)[0],
+            "sc": calibrate(M, query_solver(M, h, "sc", c, 1.0 / lam, nodes=nodes),
+                            dict(common, walks_per_node=1, w_cutoff=1e-6), 1024 * g.n)[0]}
+        pool.append((g, h, lam, kg, nodes, budgets))
+        log(f"[bench] serving pool: R-MAT scale {sc} ready, budgets {budgets} ({time.time() - t:.1f}s)")
     qs, arrivals, tnow = [], [], 0.0
     for i in range(n_requests):
         tnow += rng.exponential(1.0 / rate)
         arrivals.append(tnow)
-        g, h, lam = pool[int(rng.integers(len(pool)))]
+        g, h, lam, kg, nodes, budgets = pool[int(rng.integers(len(pool)))]
         u = rng.random()
         base = dict(graph=h, seed=seed * 100000 + i, request_id=i, precision=M.MCF_F32W_F64ACC)
         if u < 0.5:
-            qs.append(dict(base, kind=M.MCF_QUERY_TOTAL_COMMUNICABILITY, coeffs=c, scale=1.0 / lam, n_walks=16 * g.n,
-                           w_cutoff=1e-6))
+            qs.append(dict(base, kind=M.MCF_QUERY_TOTAL_COMMUNICABILITY, coeffs=c, scale=1.0 / lam, w_cutoff=1e-6,
+                           **budgets["tc"]))
         elif u < 0.8:
-            qs.append(dict(base, kind=M.MCF_QUERY_KATZ, katz_gamma=0.85 / M.mcf_gershgorin(h), katz_terms=0,
-                           walks_per_node=16))
+            qs.append(dict(base, kind=M.MCF_QUERY_KATZ, katz_gamma=kg, katz_terms=0, **budgets["katz"]))
         else:
-            nodes = rng.choice(g.n, size=min(10_000, g.n), replace=False).astype(np.int64)
-            qs.append(dict(base, kind=M.MCF_QUERY_SUBGRAPH_CENTRALITY, coeffs=c, scale=1.0 / lam,
-                           walks_per_node=32, w_cutoff=1e-6, nodes=nodes))
-    for q in qs:   # warm the per-graph walk records and Katz term counts
-        pass
+            qs.append(dict(base, kind=M.MCF_QUERY_SUBGRAPH_CENTRALITY, coeffs=c, scale=1.0 / lam, w_cutoff=1e-6,
+                           nodes=nodes, **budgets["sc"]))
     srv = M.mcf_server_create(hbm_budget_bytes=64 << 30, max_inflight=4, max_batch=16, batch_window_ms=0.5)
-    for q in qs[:8]:
+    for q in qs[:8]:     # warm-up of the server path
         M.mcf_server_wait(srv, M.mcf_server_submit(srv, dict(q)))
     srv.close()
     srv = M.mcf_server_create(hbm_budget_bytes=64 << 30, max_inflight=4, max_batch=16, batch_window_ms=0.5)
@@ -437,36 +509,99 @@ def run_serving(M, R, I, scales, n_requests, rate=200.0, seed=5):
         tickets.append(M.mcf_server_submit(srv, q))
     outs = [M.mcf_server_wait(srv, tk)[0] for tk in tickets]
     wall = time.perf_counter() - t0
+    for tk in tickets:
+        M.mcf_server_release(srv, tk)
     st = M.mcf_server_get_stats(srv)
     srv.close()
-    # accuracy of a sample of requests on the smaller graphs, per kind
+    # accuracy of sampled requests per kind: TC and Katz on graphs up to 2^22
+    # nodes (whole vectors), SC on graphs up to 2^20 nodes (64 of the sampled nodes)
     errs = {"tc": [], "katz": [], "sc": []}
-    graph_of = {id(h): (g, lam) for g, h, lam in pool}
+    graph_of = {id(p[1]): p for p in pool}
+    seen = set()
     for q, y in zip(qs, outs):
-        g, lam = graph_of[id(q["graph"])]
-        kind = {M.MCF_QUERY_TOTAL_COMMUNICABILITY: "tc", M.MCF_QUERY_KATZ: "katz",
-                M.MCF_QUERY_SUBGRAPH_CENTRALITY: "sc"}[q["kind"]]
-        if g.n > (1 << 18) or len(errs[kind]) >= 6:
+        g, h, lam, kg, nodes, _ = graph_of[id(q["graph"])]
+        kind = _kind_of(M, q)
+        if (kind, g.n) in seen or g.n > (1 << (20 if kind == "sc" else 22)):
             continue
+        seen.add((kind, g.n))
         y = np.asarray(y)
         if kind == "tc":
             ref = R.series_action(g, c, 1.0 / lam)
         elif kind == "katz":
-            K = R.katz_terms_for_tail(q["katz_gamma"] * lam, 1e-4)
-            ref = R.series_action(g, R.katz_coeffs(K), q["katz_gamma"])
+            K = R.katz_terms_for_tail(kg * lam, 1e-4)
+            ref = R.series_action(g, R.katz_coeffs(K), kg)
         else:
-            sel = q["nodes"][:512]
-            ref = R.series_diag(g, c, sel, 1.0 / lam)
-            y = y[:512]
-        errs[kind].append(float(np.abs(y - ref).max() / np.abs(ref).max()))
-    for _, h, _ in pool:
-        h.close()
+            ref, y = R.series_diag(g, c, nodes[:64], 1.0 / lam), y[:64]
+        errs[kind].append((g.n, float(np.abs(y - ref).max() / np.abs(ref).max())))
+    for p_ in pool:
+        p_[1].close()
     return {"requests": n_requests, "rate_req_per_s": rate, "scales": [scales[0], scales[-1]],
-            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"], "mean_ms": st["mean_ms"],
             "solves_per_s": st["completed"] / wall, "batches": st["batches"], "rejected": st["rejected"],
-            "walk_steps_per_s": st["walk_steps"] / wall,
-            "max_rel_err_vs_fp64": {k: (max(v) if v else None) for k, v in errs.items()},
-            "walk_budgets": "TC 16 n walks, Katz (gamma 0.85/Gershgorin) 16 per node, SC 32 per node on 1e4 sampled nodes"}
+            "walk_steps_per_s": st["walk_steps"] / wall, "device_overlap_ms": st["device_overlap_ms"],
+            "max_concurrent_batches": st["max_concurrent_batches"], "wall_s": wall,
+            "worker_plan_s": st["plan_s"], "worker_run_s": st["run_s"],
+            "max_rel_err_vs_fp64": {k: (max(e for _, e in v) if v else None) for k, v in errs.items()},
+            "checked_graph_sizes": {k: sorted(n for n, _ in v) for k, v in errs.items()},
+            "walk_budgets": "calibrated per graph and kind to an estimated relative l_inf error of "
+                            f"{CAL_TARGET} (accuracy-targeted solve from a pilot budget)",
+            "katz_gamma": "0.85 / max_i sum_k |a_ik| (Gershgorin, Section 4.5)"}
+
+
+def run_sc_config3(M, R, I, steps=2):
+    """Subgraph centrality diag exp(A/lambda_max) of every node of the erased
+    configuration model n = 2e6 (k^-2.5, mean degree 20), 2000 walks per node,
+    W_c = 1e-6, float32 weights with float64 accumulation: time per solve,
+    walk-steps/s, the walk kernel's roofline at 12 algorithmic bytes per step,
+    the difference between float32 and float64 walk arithmetic on the same
+    walks (100 walks per node), and the error against the float64 series on
+    sampled nodes."""
+    import torch
+
+    peak, peak_kind = measured_peak()
+    g = I.config_powerlaw(2_000_000, 2.5, 20.0, 2)
+    h = M.mcf_create_graph(g.n, torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col_idx).cuda())
+    lam = M.mcf_spectral_radius(h, tol=1e-10, max_iter=10000)
+    gam = 1.0 / lam
+    c = exp_coeffs(30)
+    d = torch.empty(g.n, dtype=torch.float64, device="cuda")
+    kw = dict(scale=gam, walks_per_node=2000, w_cutoff=1e-6, seed=2, precision=M.MCF_F32W_F64ACC)
+    M.mcf_subgraph_centrality(h, c, out=d, request_id=100, **kw)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    kms, steps_ = [], 0
+    for i in range(steps):
+        _, st = M.mcf_subgraph_centrality(h, c, out=d, request_id=101 + i, stats=True, **kw)
+        kms.append(st["kernel_ms"])
+        steps_ += st["walk_steps"]
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    kernel_ms = float(np.mean(kms))
+    per = steps_ / steps
+    achieved = 12 * per / (kernel_ms / 1000.0) / 1e9
+    y = d.cpu().numpy()
+    nodes = np.random.default_rng(0).choice(g.n, size=8, replace=False)
+    ref = R.series_diag(g, c, nodes, gam)
+    # float32 against float64 walk arithmetic on the same walks (100 walks per node)
+    kw100 = dict(kw, walks_per_node=100)
+    d32 = M.mcf_subgraph_centrality(h, c, out=torch.empty_like(d), request_id=7, **kw100).cpu().numpy()
+    d64 = M.mcf_subgraph_centrality(h, c, out=torch.empty_like(d), request_id=7,
+                                    **dict(kw100, precision=M.MCF_F64)).cpu().numpy()
+    h.close()
+    return {"workload": "subgraph centrality diag exp(A/lambda_max), erased configuration model n=2e6 k^-2.5 "
+                        "mean 20, 2000 walks per node, K=30, W_c=1e-6",
+            "n": g.n, "nnz": g.nnz, "ms_per_solve": ms, "solves_per_s": 1000.0 / ms,
+            "walk_steps_per_solve": per, "walk_steps_per_s": per / (ms / 1000.0),
+            "roofline": {"bound": "hbm", "kernel": "walk_diag_od_kernel", "kernel_ms": kernel_ms,
+                         "algorithmic_bytes_per_step": 12, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind},
+            "rel_err_vs_fp64_sampled": float(np.abs(y[nodes] - ref).max() / np.abs(ref).max()),
+            "sampled_nodes": len(nodes),
+            "float32_vs_float64_walks_max_rel_diff": float(np.max(np.abs(d32 - d64) / np.abs(d64))),
+            "precision": "float32 walk weights with compensated float32 sums per walk, float64 accumulation; "
+                         "compared with float64 throughout on the same walks"}
 
 
 def run_subset(M, h, g, c, base, full_out, reps=5):
@@ -615,11 +750,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched, serving, dense RandFunm and classical-method measurements")
-    ap.add_argument("--batch-graphs", type=int, default=64)
-    ap.add_argument("--batch-log-n-max", type=float, default=5.0)
-    ap.add_argument("--serve-scales", default="16-22")
-    ap.add_argument("--serve-requests", type=int, default=600)
-    ap.add_argument("--section", default="main", choices=["main", "funm_full", "mc_classic", "batched", "serving"],
+    ap.add_argument("--batch-graphs", type=int, default=256)
+    ap.add_argument("--batch-log-n-max", type=float, default=6.0)
+    ap.add_argument("--serve-scales", default="16-24")
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--section", default="main",
+                    choices=["main", "funm_full", "mc_classic", "batched", "serving", "sc_config3"],
                     help="run only that measurement (1 GPU) and print its JSON")
     ap.add_argument("--funm-n", type=int, default=16384, help="nodes of the dense RandFunm measurement")
     ap.add_argument("--ref-seconds", type=float, default=60.0,
@@ -640,6 +776,8 @@ def main():
             res = run_mc_classic(M, R, I)
         elif args.section == "batched":
             res = run_batched(M, R, I, args.batch_graphs, args.batch_log_n_max)
+        elif args.section == "sc_config3":
+            res = run_sc_config3(M, R, I)
         else:
             lo, hi = (int(x) for x in args.serve_scales.split("-"))
             res = run_serving(M, R, I, list(range(lo, hi + 1)), args.serve_requests)
@@ -679,6 +817,7 @@ def main():
     # ---- timed region: K full solves, inputs resident in HBM (CSR 4 B/nnz >> L2)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     steps_total, walks_total, kern_ms = 0, 0, []
+    launches0 = M.mcf_kernel_launches()   # the library's own kernel-execution counter (synchronises)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -693,6 +832,7 @@ def main():
         torch.cuda.synchronize()
     if dist:
         dist.barrier()
+    launches = M.mcf_kernel_launches() - launches0
     ms = ev0.elapsed_time(ev1)
     tmax = ms
     steps_all = steps_total
@@ -708,6 +848,12 @@ def main():
     traffic = None
     if args.workload in NCU_DRAM_BYTES_PER_STEP:
         traffic = NCU_DRAM_BYTES_PER_STEP[args.workload] * steps_per_launch
+    # the random-read ceiling of this GPU, measured here: independent random
+    # 8-byte reads over an array the size of the per-entry walk records
+    gather = None
+    if w["query"] == "tc":
+        gather = M.mcf_gather_probe(max(g.nnz, 1) * 8, 1 << 28, stream.cuda_stream)
+    kernel_steps_per_s = steps_per_launch / (kernel_ms / 1000.0)
 
     # ---- accuracy of one solve against the float64 truncated series
     rel_err = None
@@ -760,16 +906,26 @@ def main():
         # the library's own standard-error estimate of one solve (Section 3.5)
         _, st_se = solve(h, c, out=out, request_id=88, stats=True, error_estimate=True, **base)
         max_rel_se = st_se["max_rel_se"]
-    batched = serving = funm_full = mc_classic = None
+    batched = serving = funm_full = mc_classic = sc3 = None
     if rank == 0 and world == 1 and not args.no_batch:
         from oracle import reference as R
         from paper_2308_01037_gb300 import inputs as I
 
+        h.close()    # the sections below bring their own graphs
+        t = time.time()
+        sc3 = run_sc_config3(M, R, I)
+        log(f"[bench] section sc_config3: {time.time() - t:.1f}s")
+        t = time.time()
         batched = run_batched(M, R, I, args.batch_graphs, args.batch_log_n_max)
+        log(f"[bench] section batched: {time.time() - t:.1f}s")
+        t = time.time()
         lo, hi = (int(x) for x in args.serve_scales.split("-"))
         serving = run_serving(M, R, I, list(range(lo, hi + 1)), args.serve_requests)
+        log(f"[bench] section serving: {time.time() - t:.1f}s")
+        t = time.time()
         funm_full = run_funm_full(M, R, I)
         mc_classic = run_mc_classic(M, R, I)
+        log(f"[bench] sections funm_full, mc_classic: {time.time() - t:.1f}s")
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_all_cores(g, lam, w)
@@ -796,10 +952,16 @@ def main():
                          "dram_frac": None if traffic is None else traffic / (kernel_ms / 1000.0) / 1e9 / peak,
                          "traffic_note": None if traffic is None else
                          "DRAM bytes per launch: ncu dram__bytes_read.sum + dram__bytes_write.sum per walk step on "
-                         "the R-MAT scale 21 case (one 32-B sector per random step) x the walk steps of a launch"},
-            "clocks": clk.summary(), "e2e": e2e, "gpu_launches": args.steps * LAUNCHES_PER_SOLVE[w["query"]],
+                         "the R-MAT scale 21 case (one 32-B sector per random step) x the walk steps of a launch",
+                         # one walk step is one random read of an 8-byte record: the rate of independent random
+                         # 8-byte reads this GPU serves over an array of the records' size, measured in this run
+                         "gather_ceiling": gather, "gather_ceiling_unit": "random 8-byte reads/s",
+                         "kernel_walk_steps_per_s": kernel_steps_per_s,
+                         "frac_of_gather_ceiling": None if not gather else kernel_steps_per_s / gather},
+            "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches,
             "cpu_baseline": cpu,
-            "subset": subset, "batched": batched, "serving": serving, "funm_full": funm_full,
+            "subset": subset, "subgraph_centrality_config3": sc3, "batched": batched, "serving": serving,
+            "funm_full": funm_full,
             "mc_classic": mc_classic,
         }
         print(json.dumps(line), flush=True)

@@ -62,7 +62,7 @@ typedef enum {
     MCF_ERR_ADMISSION = 5,        /* a request does not fit the caller's memory budget */
     MCF_ERR_TIMEOUT = 6,          /* mcf_server_wait gave up before the request completed */
     MCF_ERR_CANCELLED = 7,        /* reserved (not returned by this build) */
-    MCF_ERR_ACCURACY_BUDGET = 8,  /* reserved (not returned by this build) */
+    MCF_ERR_ACCURACY_BUDGET = 8,  /* an accuracy-targeted solve hit its walk cap above the target error */
     MCF_WARN_OVERFLOW = 9,        /* reserved: a float32 weight overflow sets bit 0 of mcf_stats.flags */
     MCF_ERR_UNSUPPORTED = 10      /* a valid request this build does not implement */
 } mcf_status;
@@ -101,7 +101,24 @@ typedef struct {
                                single-query RandFunmAction solve (mcf_action, mcf_action_nodes,
                                mcf_total_communicability, mcf_katz); 0: off. Ignored elsewhere. */
     void* stream;           /* cudaStream_t                                                      */
+    double target_rel_err;  /* > 0: accuracy-targeted solve (below); 0: the walks above, once    */
+    int64_t max_walks;      /* accuracy-targeted solves: cap on the total walks (0: 2^34)        */
 } mcf_params;
+
+/* Accuracy-targeted solves (params.target_rel_err = t > 0; mcf_action,
+ * mcf_action_nodes, mcf_total_communicability, mcf_katz,
+ * mcf_subgraph_centrality, and batch queries, which then run through the
+ * single-query path).  The solve runs independent replicas of the plain
+ * solve with the walk budget above (replica r uses seed + r *
+ * 0x9E3779B97F4A7C15, so replica 0 is the plain solve; every replica keeps
+ * request_id) and returns their mean.  Replicas alternate between two
+ * halves; est = max_i |mean of half 1 - mean of half 2|_i / 2 / max_i |mean|_i
+ * estimates the relative l_inf error of the returned mean (its spread is that
+ * error's: the estimator's error falls like N^-1/2, Theorem 1 and Section
+ * 3.5).  Two replicas run first; while est > t the count grows to
+ * R (est/t)^2 x 1.25 (even), within max_walks and 4096 replicas.  If est is
+ * still above t at the cap the mean is returned with MCF_ERR_ACCURACY_BUDGET.
+ * mcf_stats reports the total walks and steps, est_rel_err and replicas. */
 
 #define MCF_MAX_COEFFS 256
 
@@ -117,6 +134,8 @@ typedef struct {
      * variance, Section 3.5) and s_i^2 the sample variance of the N_i walk
      * sums from column i (columns with N_i = 1 contribute 0); else 0. */
     double max_rel_se;
+    double est_rel_err;     /* accuracy-targeted solves: the estimated relative l_inf error; else 0 */
+    int32_t replicas;       /* accuracy-targeted solves: replicas run; else 1                      */
 } mcf_stats;
 
 /* ------------------------------------------------------------------ graphs */
@@ -150,6 +169,19 @@ mcf_status mcf_spectral_radius(mcf_graph_t g, double tol, int32_t max_iter, doub
 
 /* Gershgorin bound max_i sum_k |a_ik| on the spectral radius of A (Section 4.5). */
 mcf_status mcf_gershgorin(mcf_graph_t g, double* bound);
+
+/* Spectral radius rho of M = diag(s') |A'|, s'_i = sum_j |a'_ij|, A' = scale * A
+ * (scale 0 means 1): the second moment of a walk's weighted term at step k
+ * grows like rho^k (E[W^(k)2 ...] = (M^k ...), from Definition 1 and
+ * Eq. weights), so rho < 1 bounds the estimator's variance however long the
+ * walks (the role of Theorem 1's condition alpha < 1, for which alpha >= rho);
+ * with rho > 1 the variance grows geometrically with the truncation K (e.g.
+ * Katz with gamma = 0.85 / lambda_max on graphs with hubs).  Power iteration
+ * on the symmetric D^1/2 |A| D^1/2 (similar to M) in float64, shifted by the
+ * current Rayleigh quotient, until it changes by at most tol (relative) or
+ * max_iter iterations.  Errors: MCF_ERR_INVALID_ARG, MCF_ERR_UNSUPPORTED (A not
+ * symmetric), MCF_ERR_OOM, MCF_ERR_CUDA. */
+mcf_status mcf_second_moment_radius(mcf_graph_t g, double scale, double tol, int32_t max_iter, double* rho);
 
 /* ------------------------------------------------------------------ solves */
 
@@ -296,6 +328,8 @@ typedef struct {
      * largest number of batches whose windows overlapped at once. */
     double device_overlap_ms;
     int64_t max_concurrent_batches;
+    double plan_s, run_s;      /* host time the workers spent planning (mcf_batch_create) and
+                                  running (mcf_batch_run) batches, summed over the workers     */
 } mcf_server_stats;
 
 /* Starts a request server on the current device: a scheduler thread that

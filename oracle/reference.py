@@ -8,6 +8,10 @@ What the estimators of the paper converge to, computed without sampling:
 * ``series_action`` / ``series_diag``: the truncated series
   sum_{k<=K} zeta_k A'^k v (and its diagonal on chosen nodes) by repeated
   float64 sparse products, for large graphs.
+* ``second_moment_radius``: the spectral radius of M = diag(sum_j |a'_ij|) |A'|,
+  the matrix whose powers carry the second moments of the walk weights
+  (Definition 1 and Eq. weights: E[(W^(k))^2 ...] = (M^k ...)), from a dense
+  eigendecomposition (or ARPACK) of the similar symmetric D^1/2 |A'| D^1/2.
 * ``enumerate_action`` / ``enumerate_diag``: the exact expectation and
   variance of one walk's contribution, by enumerating every walk with its
   probability p_{l0} t_{l0 l1} ... (Definition 1) and weight (Eq. weights),
@@ -70,6 +74,23 @@ def gershgorin(g, values=None) -> float:
 
 
 # ---------------------------------------------------------------- dense (small graphs)
+def second_moment_radius(g, gamma: float = 1.0, values=None) -> float:
+    """rho(diag(s') |A'|), s'_i = sum_j |a'_ij|, A' = gamma A: one step of a walk
+    multiplies its weight by s'_l (Eq. weights) and moves to j with
+    probability |a'_lj| / s'_l (Definition 1), so the expected squared weight
+    after k steps is (M^k 1)_l-weighted with M = diag(s') |A'|, and rho(M) is
+    its growth factor.  M = D^1/2 (D^1/2 |A'| D^1/2) D^-1/2 with D = diag(s')
+    for a symmetric A, so its spectrum is that of the symmetric middle factor."""
+    A = abs(csr_matrix(g, values, gamma))
+    s = np.asarray(A.sum(axis=1)).ravel()
+    r = np.sqrt(s)
+    S = sp.diags(r) @ A @ sp.diags(r)
+    if g.n <= 2000:
+        return float(np.abs(np.linalg.eigvalsh(S.toarray())).max())
+    vals = spla.eigsh(S.tocsc(), k=1, which="LM", return_eigenvectors=False, tol=1e-12)
+    return float(np.abs(vals).max())
+
+
 def dense_funm(A: np.ndarray, coeffs) -> np.ndarray:
     """sum_k zeta_k A^k for symmetric A through its eigendecomposition."""
     lam, V = np.linalg.eigh(A)

@@ -631,20 +631,26 @@ struct mcf_batch {
     void* scan_tmp = nullptr;
     size_t scan_bytes = 0;
     // outputs staged on the device for host destinations
+    std::vector<mcf_status> qstatus;   // per query: MCF_OK, or MCF_ERR_ACCURACY_BUDGET from an accuracy-targeted query
     std::vector<std::pair<double*, double*>> out_copies;   // (device staging, host dst)
     std::vector<int64_t> out_sizes;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int device = 0;
     size_t bytes = 0;                         // device memory the plan holds
+    cudaStream_t stream = nullptr;            // the planning stream (allocations and frees)
     unsigned long long* stamps = nullptr;     // device: global-timer ns at the start and end of the last run
     unsigned long long window[2] = {0, 0};    // host copy of the last run's stamps
 };
 
+// Plan buffers come from the device's stream-ordered pool (which keeps freed
+// memory, keep_pool_memory) on the planning stream: a server planning a batch
+// per request group then neither maps new pages nor synchronises the device.
 template <class T>
 static mcf_status balloc(mcf_batch* b, T** p, size_t count) {
     void* q = nullptr;
-    if (cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) {
+    keep_pool_memory();
+    if (cudaMallocAsync(&q, std::max<size_t>(count, 1) * sizeof(T), b->stream) != cudaSuccess) {
         cudaGetLastError();
         return fail(MCF_ERR_OOM, "device allocation for the batch failed");
     }
@@ -711,7 +717,8 @@ static int64_t query_footprint(const mcf_query& q, int64_t* out) {
                                                      + (!is_device_ptr(q.nodes) ? 8 * m : 0)
                                                : 0;
     int64_t b = 16 + 4096;   // stamps, descriptor and offsets
-    if ((tc_kind && binary32 && tc_walks < B_FUSED_MAX_WALKS) || (sc_kind && binary32)) {
+    const bool plain = p.target_rel_err == 0.0;
+    if (plain && ((tc_kind && binary32 && tc_walks < B_FUSED_MAX_WALKS) || (sc_kind && binary32))) {
         b += 60 * n + 8 + 8 * B_RED_BLOCKS + 8 + BC_N * 8 + 12 * MCF_MAX_COEFFS + (int64_t)scan_tmp_bytes(n);
         if (tc_kind) {
             b += 4 * (walks / B_CHUNK + 3) + 4 * (md + 1) + 4;
@@ -729,6 +736,7 @@ static int64_t query_footprint(const mcf_query& q, int64_t* out) {
         // 4864 CTAs x 16384 float64 values)
         b += 200 * n + 4 * (walks / 32 + 3) + 4 * (md + 1) + (int64_t)scan_tmp_bytes(n) + 8 * MCF_MAX_COEFFS;
         if (sc_kind) b += 9 * n + lists + (int64_t)4864 * 16384 * 8;
+        if (!plain) b += 32 * m + 16;   // replica output, two half sums, the mean
     }
     *out = b;
     return b;
@@ -748,6 +756,8 @@ static mcf_status check_query(const mcf_query& q, int idx) {
     if (p.walks_per_node > 0 ? (n > 0 && p.walks_per_node > lim / n) : p.n_walks > lim - n)
         return fail(MCF_ERR_INVALID_ARG, where + "more than 2^36 walks per query");
     if (!(p.w_cutoff >= 0.0)) return fail(MCF_ERR_INVALID_ARG, where + "w_cutoff must be >= 0");
+    if (!(p.target_rel_err >= 0.0) || !isfinite(p.target_rel_err) || p.max_walks < 0)
+        return fail(MCF_ERR_INVALID_ARG, where + "target_rel_err must be finite and >= 0, max_walks >= 0");
     if (p.precision != MCF_F64 && p.precision != MCF_F32W_F64ACC)
         return fail(MCF_ERR_INVALID_ARG, where + "unknown precision");
     if (p.deterministic != 0) return fail(MCF_ERR_INVALID_ARG, where + "deterministic is reserved and must be 0");
@@ -881,6 +891,8 @@ static mcf_status autotune(mcf_batch* b, cudaStream_t st) {
     return MCF_OK;
 }
 
+mcf_status mcf::batch_query_status(const mcf_batch* b, int i) { return b->qstatus[i]; }
+
 void mcf::batch_window(const mcf_batch* b, uint64_t* begin_ns, uint64_t* end_ns) {
     *begin_ns = b->window[0];
     *end_ns = b->window[1];
@@ -907,10 +919,13 @@ mcf_status mcf_batch_device_bytes(mcf_batch_t b, size_t* bytes) {
 
 mcf_status mcf_batch_destroy(mcf_batch_t b) {
     if (!b) return MCF_OK;
-    cudaDeviceSynchronize();
+    // every run ends with a synchronisation of its stream, so no work of the
+    // plan is pending; the buffers go back to the pool in stream order
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
-    for (void* p : b->bufs) cudaFree(p);
+    for (void* p : b->bufs) cudaFreeAsync(p, b->stream);
+    cudaStreamSynchronize(b->stream);
+    cudaGetLastError();
     delete b;
     return MCF_OK;
 }
@@ -930,11 +945,13 @@ mcf_status mcf_batch_create(const mcf_query* queries, int32_t n_queries, uint32_
         return s;
     };
     cudaGetDevice(&b->device);
+    b->stream = st;
     {
         mcf_status rs = balloc(b, &b->stamps, 2);
         if (rs != MCF_OK) return bail(rs);
     }
     b->queries.assign(queries, queries + n_queries);
+    b->qstatus.assign(n_queries, MCF_OK);
     b->params.resize(n_queries);
     b->coeffs.resize(n_queries);
     std::vector<int> tc, sc;
@@ -968,10 +985,11 @@ mcf_status mcf_batch_create(const mcf_query* queries, int32_t n_queries, uint32_
         b->params[i] = p;
         const bool binary32 = !q.graph->weighted && p.precision == MCF_F32W_F64ACC && q.graph->nnz < ((int64_t)1 << 32);
         const int64_t tc_walks = p.walks_per_node > 0 ? p.walks_per_node * q.graph->n : p.n_walks;
+        const bool plain = p.target_rel_err == 0.0;   // accuracy-targeted queries run as replicas (single path)
         if ((q.kind == MCF_QUERY_TOTAL_COMMUNICABILITY || q.kind == MCF_QUERY_KATZ) && binary32 && p.n_coeffs >= 3 &&
-            tc_walks < B_FUSED_MAX_WALKS)
+            tc_walks < B_FUSED_MAX_WALKS && plain)
             tc.push_back(i);
-        else if (q.kind == MCF_QUERY_SUBGRAPH_CENTRALITY && binary32 && p.n_coeffs >= 3)
+        else if (q.kind == MCF_QUERY_SUBGRAPH_CENTRALITY && binary32 && p.n_coeffs >= 3 && plain)
             sc.push_back(i);
         else
             b->single.push_back(i);
@@ -1224,7 +1242,8 @@ mcf_status mcf_batch_run(mcf_batch_t b, void* stream, mcf_stats* stats) {
                 break;
             default: rc = mcf_total_communicability(q.graph, &p, q.out, stats ? &s1 : nullptr); break;
         }
-        if (rc != MCF_OK) return rc;
+        b->qstatus[i] = rc;
+        if (rc != MCF_OK && rc != MCF_ERR_ACCURACY_BUDGET) return rc;
         walks += s1.walks;
         steps += s1.walk_steps;
         ms += (float)s1.kernel_ms;
@@ -1239,7 +1258,14 @@ mcf_status mcf_batch_run(mcf_batch_t b, void* stream, mcf_stats* stats) {
         stats->walk_steps = steps;
         stats->kernel_ms = ms;
         stats->flags = fl;
+        stats->max_rel_se = 0.0;
+        stats->est_rel_err = 0.0;
+        stats->replicas = 1;
     }
+    for (mcf_status q : b->qstatus)
+        if (q == MCF_ERR_ACCURACY_BUDGET)
+            return fail(MCF_ERR_ACCURACY_BUDGET, "an accuracy-targeted query stopped at its walk cap; every result "
+                                                 "is written");
     return MCF_OK;
 }
 

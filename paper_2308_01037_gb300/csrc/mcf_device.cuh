@@ -397,49 +397,6 @@ __device__ int diag_walk(const DiagTable& t, uint32_t k0, int64_t g, int from, i
     return -1;
 }
 
-// diag_walk for a binary matrix with float32 weights, reading one 16-byte
-// neighbour record {row offset, degree, node, 0} per step (erec: one per CSR
-// entry) instead of the state's record and then a column index; rm[d] =
-// float(gamma * d) is the weight multiplier of a state of degree d (the
-// value the node record holds).  Same walks, visits and rounding as
-// diag_walk<false, false, DENSE>.
-__device__ __forceinline__ uint4 load_erec(const uint4* p, uint64_t pol) {
-    uint4 v;
-    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
-                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-                 : "l"(p), "l"(pol));
-    return v;
-}
-
-template <bool DENSE>
-__device__ int diag_walk_edge(const DiagTable& t, uint32_t k0, uint2 od0, int64_t g, int from, int count_from,
-                              const uint4* __restrict__ erec, const float* __restrict__ rm, const float* zeta, int K,
-                              float wc32, uint2 key, uint32_t req, uint32_t& steps, uint32_t& flags) {
-    uint32_t l = k0, off = od0.x, deg = od0.y;
-    float W = 1.f;
-    uint4 u = make_uint4(0u, 0u, 0u, 0u);
-    const uint32_t glo = (uint32_t)g, ghi = (uint32_t)((uint64_t)g >> 32);
-    for (int k = 0; k <= K; ++k) {
-        if (!(fabsf(W) > wc32)) break;
-        uint32_t w0, w1;
-        walk_words<false>(u, k, glo, ghi, req, key, w0, w1);
-        if (k >= from) {
-            const int h = q_slot<DENSE>(t, l);
-            if (h < 0) return k;
-            atomicAdd(&t.val[h], (double)__fmul_rn(zeta[k + 2], W));
-        }
-        if (k + 2 >= K || deg == 0) break;
-        const uint4 e = load_erec(erec + (int64_t)off + __umulhi(w0, deg), policy_evict_first());
-        W = __fmul_rn(W, __ldg(rm + deg));
-        l = e.z;
-        off = e.x;
-        deg = e.y;
-        if (k >= count_from) ++steps;
-    }
-    if (!isfinite(W)) flags |= 1u;
-    return -1;
-}
-
 // The requested rows of each column for a RandFunmDiag node subset S:
 // column k lists the nodes i in S with a_ik != 0 (row[ptr[k] .. ptr[k+1]))
 // and, for a weighted A, the entries a_ik (val).  Built from the rows of the

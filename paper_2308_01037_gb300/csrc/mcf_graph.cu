@@ -337,6 +337,42 @@ __global__ void power_update(int64_t n, double* __restrict__ x, const double* __
         x[i] = (x[i] + y[i]) * inv;
 }
 
+// y_i = sqrt(s_i) sum_j |a_ij| sqrt(s_j) x_j with s_i = sum_j |a_ij| (deg_i for
+// a binary A): the product with S = D^1/2 |A| D^1/2, which is similar to the
+// second-moment matrix D |A| of the walk weights (D = diag(s)).  Thread per row.
+__global__ void moment_spmv(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                            const float* __restrict__ val, const double* __restrict__ row_abs,
+                            const double* __restrict__ x, double* __restrict__ y) {
+    MCF_KERNEL_ENTRY();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+            const int32_t j = col[p];
+            const double sj = row_abs ? row_abs[j] : (double)(rp[j + 1] - rp[j]);
+            acc += (val ? fabs((double)val[p]) : 1.0) * sqrt(sj) * x[j];
+        }
+        const double si = row_abs ? row_abs[i] : (double)(rp[i + 1] - rp[i]);
+        y[i] = sqrt(si) * acc;
+    }
+}
+
+// x <- (y + c x) / ||y + c x|| with c = stats[0] (the current Rayleigh quotient:
+// a positive shift that keeps the Perron root dominant on bipartite graphs).
+__global__ void moment_update(int64_t n, double* __restrict__ x, const double* __restrict__ y,
+                              const double* __restrict__ stats, double* __restrict__ z) {
+    MCF_KERNEL_ENTRY();
+    const double c = stats[0];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        z[i] = y[i] + c * x[i];
+}
+
+// dst = a * src
+__global__ void scale_copy(int64_t n, const double* __restrict__ src, double a, double* __restrict__ dst) {
+    MCF_KERNEL_ENTRY();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = a * src[i];
+}
+
 __global__ void fill_f64(int64_t n, double* __restrict__ x, double v) {
     MCF_KERNEL_ENTRY();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -572,7 +608,7 @@ mcf_status mcf_destroy_graph(mcf_graph_t g) {
     graph_free(g->went);
     graph_free(g->node_od);
     graph_free(g->edge_od);
-    graph_free(g->edge_rec);
+    graph_free(g->edge_key);
     if (!g->symmetric) {
         graph_free(g->col_ptr);
         graph_free(g->row_idx);
@@ -642,6 +678,68 @@ mcf_status mcf_spectral_radius(mcf_graph_t g, double tol, int32_t max_iter, doub
     if (rc != MCF_OK) return rc;
     g->lambda_max = lam;
     *lambda_max = lam;
+    return MCF_OK;
+}
+
+mcf_status mcf_second_moment_radius(mcf_graph_t g, double scale, double tol, int32_t max_iter, double* rho) {
+    set_error("");
+    if (!g || !rho) return fail(MCF_ERR_INVALID_ARG, "NULL argument");
+    if (!g->symmetric)
+        return fail(MCF_ERR_UNSUPPORTED, "the power iteration needs a symmetric A");
+    if (!(tol > 0.0) || max_iter < 1 || !(scale >= 0.0) || !isfinite(scale))
+        return fail(MCF_ERR_INVALID_ARG, "tol > 0, max_iter >= 1 and a finite scale >= 0 required");
+    const double gam = scale == 0.0 ? 1.0 : scale;
+    if (g->n == 0 || g->nnz == 0) {
+        *rho = 0.0;
+        return MCF_OK;
+    }
+    cudaStream_t st = 0;
+    const int64_t n = g->n;
+    double *x = nullptr, *y = nullptr, *z = nullptr, *part = nullptr, *hst = nullptr;
+    if (cudaMalloc(&x, n * sizeof(double)) != cudaSuccess || cudaMalloc(&y, n * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&z, n * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&part, (2 * RED_BLOCKS + 4) * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost(&hst, 2 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(x); cudaFree(y); cudaFree(z); cudaFree(part); cudaFreeHost(hst);
+        return fail(MCF_ERR_OOM, "power iteration scratch");
+    }
+    mcf_status rc = MCF_OK;
+    const int grid = num_sms() * 4;
+    fill_f64<<<grid, 256, 0, st>>>(n, x, 1.0 / sqrt((double)n));
+    cudaMemsetAsync(part + 2 * RED_BLOCKS + 2, 0, 2 * sizeof(double), st);   // shift 0 in the first step
+    double lam = 0.0, prev = 0.0;
+    for (int it = 0; it < max_iter; ++it) {
+        moment_spmv<<<grid, 256, 0, st>>>(n, g->row_ptr, g->col_idx, g->values, g->row_abs, x, y);
+        // z = S x + c x; x . S x (the Rayleigh quotient, ||x|| = 1) and ||z||^2
+        moment_update<<<grid, 256, 0, st>>>(n, x, y, part + 2 * RED_BLOCKS + 2, z);
+        power_partials<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, x, y, part);
+        power_finish<<<1, RED_THREADS, 0, st>>>(part, RED_BLOCKS, part + 2 * RED_BLOCKS);
+        if (cudaMemcpy(hst, part + 2 * RED_BLOCKS, 2 * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            rc = fail(MCF_ERR_CUDA, std::string("power iteration: ") + cudaGetErrorString(cudaGetLastError()));
+            break;
+        }
+        lam = hst[0];
+        // next iterate: z / ||z||, shift = this Rayleigh quotient
+        double zz = 0.0;
+        power_partials<<<RED_BLOCKS, RED_THREADS, 0, st>>>(n, z, z, part);
+        power_finish<<<1, RED_THREADS, 0, st>>>(part, RED_BLOCKS, part + 2 * RED_BLOCKS);
+        if (cudaMemcpy(hst, part + 2 * RED_BLOCKS, 2 * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            rc = fail(MCF_ERR_CUDA, std::string("power iteration: ") + cudaGetErrorString(cudaGetLastError()));
+            break;
+        }
+        zz = hst[0];
+        if (!(zz > 0.0)) break;
+        scale_copy<<<grid, 256, 0, st>>>(n, z, 1.0 / sqrt(zz), x);
+        const double shift = lam;
+        cudaMemcpyAsync(part + 2 * RED_BLOCKS + 2, &shift, sizeof(double), cudaMemcpyHostToDevice, st);
+        cudaStreamSynchronize(st);
+        if (it > 0 && fabs(lam - prev) <= tol * fabs(lam)) break;
+        prev = lam;
+    }
+    cudaFree(x); cudaFree(y); cudaFree(z); cudaFree(part); cudaFreeHost(hst);
+    if (rc != MCF_OK) return rc;
+    *rho = gam * gam * lam;
     return MCF_OK;
 }
 

@@ -72,10 +72,10 @@ struct mcf_graph {
     // column index and then a node record.
     uint2* node_od = nullptr;     // n
     uint2* edge_od = nullptr;     // nnz
-    // Binary graphs, built on the first subgraph-centrality solve: per CSR
-    // entry the neighbour's {row offset, degree, node id, 0} (16 bytes), so a
-    // RandFunmDiag step is one random read that also names the visited node.
-    uint4* edge_rec = nullptr;    // nnz
+    // Symmetric binary graphs, built on the first subgraph-centrality solve:
+    // per CSR entry the row offset of the neighbour it leads to (the key of
+    // that neighbour in a row Q_k), read by the dot phase.
+    uint32_t* edge_key = nullptr; // nnz
     // Column-major copy of A (column i: rows row_idx[col_ptr[i] .. col_ptr[i+1])
     // in increasing order, values col_values) and sum_j a_ji^2 per column.
     // For a symmetric A these alias the row arrays; a general A (created with
@@ -323,10 +323,12 @@ constexpr int DIAG_CAP_LOG2 = 12;
 
 // Global-timer window (ns) of a batch's last run: from its first kernel to its last.
 void batch_window(const mcf_batch* b, uint64_t* begin_ns, uint64_t* end_ns);
+// Outcome of query i of a batch's last run (MCF_OK or MCF_ERR_ACCURACY_BUDGET).
+mcf_status batch_query_status(const mcf_batch* b, int i);
 
 // Builds the graph's node_od / edge_od arrays on first use (binary, nnz < 2^32).
 mcf_status ensure_edge_od(mcf_graph* g, cudaStream_t st);
-mcf_status ensure_edge_rec(mcf_graph* g, cudaStream_t st);
+mcf_status ensure_edge_key(mcf_graph* g, cudaStream_t st);
 // Keeps freed stream-ordered scratch in the device's default pool.
 void keep_pool_memory();
 

@@ -73,6 +73,10 @@ struct mcf_server {
     // global-timer windows (ns) of the completed batches' device work
     std::vector<std::pair<uint64_t, uint64_t>> windows;
     int64_t submitted = 0, completed = 0, rejected = 0, batches = 0, steps = 0;
+    double plan_s = 0.0, run_s = 0.0;
+    // the walk kernels' L2 fetch granularity, held for the server's life so
+    // that concurrent batches do not switch the context-wide setting back and forth
+    mcf::ScopedL2Fetch* fetch = nullptr;
     bool any_submit = false;
     Clock::time_point t_first, t_last;
 };
@@ -95,23 +99,33 @@ static void worker_loop(mcf_server* s, Worker* w) {
         for (Request* r : job) qs.push_back(r->q);
         mcf_batch_t b = nullptr;
         mcf_stats st{};
+        const auto t_plan = Clock::now();
         mcf_status rc = mcf_batch_create(qs.data(), (int32_t)qs.size(), 0, w->stream, &b);
+        const auto t_run = Clock::now();
         if (rc == MCF_OK) rc = mcf_batch_run(b, w->stream, &st);
+        const auto t_end = Clock::now();
         uint64_t t0 = 0, t1 = 0;
-        if (rc == MCF_OK) mcf::batch_window(b, &t0, &t1);
+        std::vector<mcf_status> qs_status(job.size(), rc);
+        if (rc == MCF_OK || rc == MCF_ERR_ACCURACY_BUDGET) {
+            mcf::batch_window(b, &t0, &t1);
+            for (size_t i = 0; i < job.size(); ++i) qs_status[i] = mcf::batch_query_status(b, (int)i);
+        }
         mcf_batch_destroy(b);
         const auto now = Clock::now();
         {
             std::lock_guard<std::mutex> lk(s->mu);
-            for (Request* r : job) {
+            for (size_t i = 0; i < job.size(); ++i) {
+                Request* r = job[i];
                 r->state = 2;
-                r->status = rc;
+                r->status = qs_status[i];
                 r->t_done = now;
                 s->inflight_bytes -= r->bytes;
                 s->latencies.push_back(std::chrono::duration<double, std::milli>(now - r->t_submit).count());
                 ++s->completed;
             }
             s->steps += st.walk_steps;
+            s->plan_s += std::chrono::duration<double>(t_run - t_plan).count();
+            s->run_s += std::chrono::duration<double>(t_end - t_run).count();
             if (t1 > t0) s->windows.push_back({t0, t1});
             ++s->batches;
             s->t_last = now;
@@ -179,6 +193,7 @@ mcf_status mcf_server_create(const mcf_server_config* config, mcf_server_t* out)
     if (!s) return fail(MCF_ERR_OOM, "host allocation failed");
     s->cfg = *config;
     cudaGetDevice(&s->device);
+    s->fetch = new mcf::ScopedL2Fetch(mcf::L2_FETCH_BYTES);
     for (int i = 0; i < config->max_inflight; ++i) {
         Worker* w = new Worker();
         if (cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -313,6 +328,8 @@ mcf_status mcf_server_get_stats(mcf_server_t s, mcf_server_stats* out) {
     }
     out->device_overlap_ms = (double)overlap_ns * 1e-6;
     out->max_concurrent_batches = most;
+    out->plan_s = s->plan_s;
+    out->run_s = s->run_s;
     return MCF_OK;
 }
 
@@ -352,6 +369,7 @@ mcf_status mcf_server_destroy(mcf_server_t s) {
         delete w;
     }
     for (auto& kv : s->all) delete kv.second;
+    delete s->fetch;
     delete s;
     return MCF_OK;
 }

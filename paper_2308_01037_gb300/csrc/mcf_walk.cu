@@ -18,6 +18,12 @@
 
 namespace mcf {
 
+// Launch variants measured against each other (compile-time; the defaults are the measured best).
+#ifndef MCF_TC_ALIGN
+#define MCF_TC_ALIGN 0
+#endif
+constexpr bool TC_ALIGN = MCF_TC_ALIGN != 0;
+
 // r = A' v evaluated as gamma * sum_j (a_ij v_j), the sum in CSR order with
 // every product and sum rounded on its own (thread per row); v == nullptr
 // means v = 1, where a binary row gives gamma * deg exactly.
@@ -354,11 +360,19 @@ __global__ void __launch_bounds__(256, WALK_MINB) walk_tc_kernel(
     uint4 u = make_uint4(0u, 0u, 0u, 0u);
     F2Acc a32;
     uint32_t my_steps = 0, my_walks = 0, flags = 0;
-    for (;;) {
+    uint32_t it = 0;
+    for (;; ++it) {
         unsigned idle = __ballot_sync(FULL, !active);
-        // refill once at least refill_min lanes are idle (or all are): fewer
-        // refill passes against a few idle lanes for a step or two
-        if (idle != FULL && __popc(idle) < refill_min) idle = 0u;
+        if (TC_ALIGN) {
+            // walks start at iterations it = 0 mod 4 only, so a warp's lanes
+            // evaluate their Philox blocks (one per four steps) together
+            if (idle == FULL) it = (it + 3u) & ~3u;
+            if ((it & 3u) != 0u) idle = 0u;
+        } else {
+            // refill once at least refill_min lanes are idle (or all are): fewer
+            // refill passes against a few idle lanes for a step or two
+            if (idle != FULL && __popc(idle) < refill_min) idle = 0u;
+        }
         while (idle && !exhausted) {
             if (p >= valid) {
                 ++c;
@@ -572,18 +586,16 @@ __global__ void se_rows(int64_t m, const int64_t* __restrict__ rows, const int64
 // partial row and the stopped walks resume from their first unrecorded visit
 // (walks are deterministic in their Philox counters and Q_k enters d
 // linearly).
-template <bool F64, bool WEIGHTED, bool DENSE, bool EDGE>
+template <bool F64, bool WEIGHTED, bool DENSE>
 __global__ void __launch_bounds__(256) walk_diag_kernel(
     const Rec<F64>* __restrict__ rec, const int64_t* __restrict__ cp, const int32_t* __restrict__ ri,
     const float* __restrict__ cv, const int32_t* __restrict__ col, const WEntry* __restrict__ went,
-    const uint4* __restrict__ erec, const uint2* __restrict__ nod, const float* __restrict__ rm,
     const int32_t* __restrict__ starts,
     const int64_t* __restrict__ woff, const int64_t* __restrict__ nw, SubList sub, double gamma,
     const double* __restrict__ zeta_g, int K, double wc, float wc32, uint2 key, uint32_t req, int64_t n, int cap_log2,
     double* __restrict__ qval, double* __restrict__ dacc, unsigned long long* __restrict__ counters) {
     MCF_KERNEL_ENTRY();
     using real = typename std::conditional<F64, double, float>::type;
-    static_assert(!EDGE || (!F64 && !WEIGHTED), "neighbour records serve binary float32 walks");
     extern __shared__ int32_t smem_i[];
     __shared__ real zeta[MCF_MAX_COEFFS];
     __shared__ int64_t cur;
@@ -617,8 +629,6 @@ __global__ void __launch_bounds__(256) walk_diag_kernel(
         const uint32_t k0 = (uint32_t)starts[s];
         const int64_t Nk = nw[k0];
         const int64_t g0 = woff[k0];
-        uint2 od0 = make_uint2(0u, 0u);
-        if constexpr (EDGE) od0 = nod[k0];
         if (threadIdx.x == 0 && visit0 && K >= 2) {
             double z2;
             if constexpr (F64) z2 = zeta[2];
@@ -633,13 +643,8 @@ __global__ void __launch_bounds__(256) walk_diag_kernel(
         for (;;) {
             bool stopped = false;
             while (w < Nk) {
-                int f;
-                if constexpr (EDGE)
-                    f = diag_walk_edge<DENSE>(t, k0, od0, g0 + w, from, cfrom, erec, rm, zeta, K, wc32, key, req, steps,
-                                              flags);
-                else
-                    f = diag_walk<F64, WEIGHTED, DENSE>(t, k0, g0 + w, from, cfrom, rec, col, went, zeta, K, wc, wc32,
-                                                        key, req, steps, flags);
+                const int f = diag_walk<F64, WEIGHTED, DENSE>(t, k0, g0 + w, from, cfrom, rec, col, went, zeta, K, wc,
+                                                              wc32, key, req, steps, flags);
                 if (f >= 0) {
                     from = f;
                     cfrom = f;
@@ -674,6 +679,606 @@ __global__ void __launch_bounds__(256) walk_diag_kernel(
         ws += __shfl_down_sync(0xffffffffu, ws, d);
         ww += __shfl_down_sync(0xffffffffu, ww, d);
         flags |= __shfl_down_sync(0xffffffffu, flags, d);
+    }
+    if (lane == 0) {
+        atomicAdd(&counters[C_STEPS], ws);
+        atomicAdd(&counters[C_WALKS], ww);
+        if (flags) atomicOr(&counters[C_FLAGS], (unsigned long long)flags);
+    }
+}
+
+// ---------------------------------------------------------------- RandFunmDiag, symmetric binary graphs
+// The RandFunmDiag kernel for a symmetric binary A in float32 weights on a
+// graph too large for a dense row Q_k.  A step reads the 8-byte record
+// {row offset, degree} of the state it moves to (edge_od, as the
+// total-communicability walks), and row Q_k is keyed by the row offset of the
+// visited node instead of its id: every visited node has degree >= 1 (walks
+// move along entries), and nodes of degree >= 1 have distinct row offsets.
+// The keys live in a shared-memory open-addressing table (no slot list: a
+// flush clears by scanning the table), the float64 values in a per-CTA
+// region of global memory updated by L2 reductions.
+//
+// One CTA serves one start column k at a time.  Its lanes take the N_k walks
+// from a shared counter and each lane starts the next walk as soon as its
+// previous one ends (no lane waits for the longest walk of its warp).  A
+// lane whose new key does not fit (the table holds its fill limit) keeps its
+// walk in registers and pauses; once every lane of the CTA has paused or run
+// out of walks, the CTA adds the partial row into d (the dot phase of
+// Eq. rand_funm_formula_diag, which is linear in Q_k), clears the table and
+// the paused walks go on from where they stopped.  The N_k step-0 visits
+// (weight 1 at k) are added once as N_k * zeta_2.
+constexpr uint32_t OD_EMPTY = 0xffffffffu;
+#ifndef MCF_DIAG_OD_ALIGN
+#define MCF_DIAG_OD_ALIGN 0
+#endif
+constexpr bool DIAG_OD_ALIGN = MCF_DIAG_OD_ALIGN != 0;
+
+struct OdTable {
+    uint32_t* key;     // shared: row offset of the node in each slot, OD_EMPTY when free
+    double* val;       // global, per CTA
+    int cap_log2;
+    int limit;         // largest number of keys admitted
+    int* count;        // shared
+};
+
+__device__ __forceinline__ int od_insert(const OdTable& t, uint32_t key) {
+    const uint32_t mask = (1u << t.cap_log2) - 1u;
+    uint32_t h = (key * 0x9E3779B1u) >> (32 - t.cap_log2);
+    for (uint32_t probe = 0; probe <= mask; ++probe, h = (h + 1) & mask) {
+        const uint32_t k = t.key[h];
+        if (k == key) return (int)h;
+        if (k == OD_EMPTY) {
+            if (*(volatile int*)t.count >= t.limit) return -1;
+            const uint32_t prev = atomicCAS(&t.key[h], OD_EMPTY, key);
+            if (prev == OD_EMPTY) {
+                atomicAdd(t.count, 1);
+                return (int)h;
+            }
+            if (prev == key) return (int)h;
+        }
+    }
+    return -1;
+}
+
+__device__ __forceinline__ double od_get(const OdTable& t, uint32_t key) {
+    const uint32_t mask = (1u << t.cap_log2) - 1u;
+    uint32_t h = (key * 0x9E3779B1u) >> (32 - t.cap_log2);
+    for (uint32_t probe = 0; probe <= mask; ++probe, h = (h + 1) & mask) {
+        const uint32_t k = t.key[h];
+        if (k == key) return __ldcg(t.val + h);
+        if (k == OD_EMPTY) return 0.0;
+    }
+    return 0.0;
+}
+
+// d_i += a'_ik <Q_k, C'_i> / N_k for the rows i of column k (= row k), or the
+// rows the subset lists for column k; the entries of row i name their
+// neighbours' keys in edge_key (4 bytes per entry).  Warp per row.
+__device__ __forceinline__ void od_apply(const OdTable& t, uint32_t k0, int64_t Nk, const int64_t* __restrict__ rp,
+                                         const int32_t* __restrict__ col, const uint32_t* __restrict__ ekey,
+                                         const SubList& sub, double gamma, double* __restrict__ dacc) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int64_t* lp = sub.ptr ? sub.ptr : rp;
+    const int32_t* lrow = sub.ptr ? sub.row : col;
+    const double scale = (gamma * gamma) / (double)Nk;
+    for (int64_t p = lp[k0] + wid; p < lp[k0 + 1]; p += nwarp) {
+        const int32_t i = lrow[p];
+        double dot = 0.0;
+        for (int64_t q = rp[i] + lane; q < rp[i + 1]; q += 32) {
+            const double qv = od_get(t, __ldg(&ekey[q]));
+            if (__double_as_longlong(qv) != 0) dot += qv;   // exact zeros change no sum
+        }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, d);
+        if (lane == 0) atomicAdd(&dacc[i], dot * scale);
+    }
+}
+
+__device__ __forceinline__ void od_clear(const OdTable& t) {
+    const int cap = 1 << t.cap_log2;
+    for (int h = threadIdx.x; h < cap; h += blockDim.x) {
+        if (t.key[h] != OD_EMPTY) {
+            t.key[h] = OD_EMPTY;
+            __stcg(t.val + h, 0.0);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) walk_diag_od_kernel(
+    const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const uint2* __restrict__ nod,
+    const uint2* __restrict__ eod, const uint32_t* __restrict__ ekey, const float* __restrict__ rm,
+    const int32_t* __restrict__ starts,
+    const int64_t* __restrict__ woff, const int64_t* __restrict__ nw, SubList sub, double gamma,
+    const double* __restrict__ zeta_g, int K, float wc32, uint2 key, uint32_t req, int cap_log2,
+    double* __restrict__ qval, double* __restrict__ dacc, unsigned long long* __restrict__ counters) {
+    MCF_KERNEL_ENTRY();
+    extern __shared__ uint32_t od_keys[];
+    __shared__ float zeta[MCF_MAX_COEFFS];
+    __shared__ int64_t cur;
+    __shared__ int count;
+    __shared__ unsigned long long next_walk;
+    for (int k = threadIdx.x; k <= K; k += blockDim.x) zeta[k] = (float)zeta_g[k];
+    OdTable t;
+    const int cap = 1 << cap_log2;
+    t.key = od_keys;
+    t.val = qval + (int64_t)blockIdx.x * cap;
+    t.cap_log2 = cap_log2;
+    t.limit = cap - cap / 4 - (int)blockDim.x;
+    t.count = &count;
+    for (int h = threadIdx.x; h < cap; h += blockDim.x) {
+        od_keys[h] = OD_EMPTY;
+        __stcg(t.val + h, 0.0);
+    }
+    if (threadIdx.x == 0) count = 0;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const int64_t S = (int64_t)counters[C_STARTS];
+    const bool visit0 = 1.0f > wc32;   // the step-0 visit (weight 1 at k), as in the walks
+    uint32_t steps = 0, walks = 0, flags = 0;
+    __syncthreads();
+    for (;;) {
+        if (threadIdx.x == 0) {
+            cur = (int64_t)atomicAdd(&counters[C_NEXT], 1ull);
+            next_walk = 0ull;
+        }
+        __syncthreads();
+        const int64_t s = cur;
+        if (s >= S) break;
+        const uint32_t k0 = (uint32_t)starts[s];
+        const int64_t Nk = nw[k0];
+        const int64_t g0 = woff[k0];
+        const uint2 od0 = nod[k0];
+        if (threadIdx.x == 0 && visit0 && K >= 2) {
+            const int h = od_insert(t, od0.x);     // empty table: always succeeds
+            atomicAdd(&t.val[h], (double)Nk * (double)zeta[2]);
+        }
+        __syncthreads();
+        // lane state
+        bool active = false, paused = false, exhausted = false;
+        int64_t g = 0;
+        uint32_t off = 0, deg = 0;
+        int k = 0;
+        float W = 1.f;
+        uint4 u = make_uint4(0u, 0u, 0u, 0u);
+        // Walks start only at iterations it = 0 mod 4, so the lanes of a warp
+        // stay at the same step modulo 4 and evaluate their Philox blocks
+        // (one per four transitions) together instead of one lane group at a time.
+        uint32_t it = 0;
+        for (;;) {
+            for (;; ++it) {
+                // hand the next walks of this start to the idle lanes
+                unsigned idle = __ballot_sync(FULL, !active);
+                if (DIAG_OD_ALIGN) {
+                    if (idle && !exhausted && (it & 3u) != 0u && !__any_sync(FULL, active && !paused))
+                        it = (it + 3u) & ~3u;   // nothing runs until the next start point: go there at once
+                    if ((it & 3u) != 0u) idle = 0u;
+                }
+                if (idle && !exhausted) {
+                    unsigned long long base = 0;
+                    if (lane == __ffs(idle) - 1) base = atomicAdd(&next_walk, (unsigned long long)__popc(idle));
+                    base = __shfl_sync(FULL, base, __ffs(idle) - 1);
+                    if (base + __popc(idle) >= (unsigned long long)Nk) exhausted = true;
+                    if (!active) {
+                        const int64_t w = (int64_t)base + __popc(idle & lt_mask);
+                        if (w < Nk) {
+                            g = g0 + w;
+                            off = od0.x;
+                            deg = od0.y;
+                            k = 0;
+                            W = 1.f;
+                            active = true;
+                        }
+                    }
+                }
+                const bool run = active && !paused;
+                if (!__any_sync(FULL, run)) break;
+                if (run) {
+                    bool done = !(fabsf(W) > wc32);
+                    if (!done && k >= 1) {
+                        const int h = od_insert(t, off);
+                        if (h < 0) paused = true;
+                        else atomicAdd(&t.val[h], (double)__fmul_rn(zeta[k + 2], W));
+                    }
+                    if (!done && !paused) {
+                        if (k + 2 >= K || deg == 0) {
+                            done = true;
+                        } else {
+                            uint32_t w0, w1;
+                            walk_words<false>(u, k, (uint32_t)g, (uint32_t)((uint64_t)g >> 32), req, key, w0, w1);
+                            const uint2 nx = load_od(eod + (int64_t)off + __umulhi(w0, deg), policy_evict_first());
+                            W = __fmul_rn(W, __ldg(rm + deg));
+                            off = nx.x;
+                            deg = nx.y;
+                            ++k;
+                            ++steps;
+                        }
+                    }
+                    if (done) {
+                        if (!isfinite(W)) flags |= 1u;
+                        ++walks;
+                        active = false;
+                    }
+                }
+            }
+            // every lane has paused or run out of walks
+            const bool any_paused = __syncthreads_or(paused);
+            __threadfence_block();
+            od_apply(t, k0, Nk, rp, col, ekey, sub, gamma, dacc);
+            __syncthreads();
+            od_clear(t);
+            if (threadIdx.x == 0) count = 0;
+            __syncthreads();
+            if (!any_paused) break;
+            paused = false;   // the table is empty again: the paused walks go on
+        }
+    }
+    unsigned long long ws = steps, ww = walks;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        ws += __shfl_down_sync(FULL, ws, d);
+        ww += __shfl_down_sync(FULL, ww, d);
+        flags |= __shfl_down_sync(FULL, flags, d);
+    }
+    if (lane == 0) {
+        atomicAdd(&counters[C_STEPS], ws);
+        atomicAdd(&counters[C_WALKS], ww);
+        if (flags) atomicOr(&counters[C_FLAGS], (unsigned long long)flags);
+    }
+}
+
+// ---------------------------------------------------------------- RandFunmDiag, two starts per CTA
+// The walks and visits of walk_diag_od_kernel (same rows Q_k, keys, Philox
+// streams and results), with two start columns in flight per CTA (slots 0
+// and 1, a key table each) and no CTA-wide barrier: a lane whose slot has
+// handed out all its walks takes walks of the other slot, and the dot phase
+// of a finished (or full) slot is shared out row by row to the warps while
+// the other slot's walks go on.
+//
+// Per slot, one 64-bit shared word holds the state (bits 62-63: 0 no more
+// starts, 1 walking, 2 dot phase), the walks paused on a full table (bits
+// 32-61) and the walks handed out and not finished (bits 0-31).  Every change
+// of the counts goes through this word, and the change that leaves every
+// handed-out walk paused (table full) or every walk of the start finished
+// switches the state to the dot phase in the same atomic operation, so
+// exactly one lane triggers each dot phase and no walk starts on a table
+// that is being read or cleared.  The warp that finishes the last row of a
+// dot phase clears the table, then lets the paused walks go on (a new flush
+// generation) or loads the next start column into the slot.  Waiting is
+// bounded: a warp that makes no progress for 2^24 iterations sets flag bit 2
+// and leaves.
+constexpr int OD2_SLOTS = 2;
+constexpr int OD2_ST_DONE = 0, OD2_ST_WALK = 1, OD2_ST_DOT = 2;
+constexpr uint32_t OD2_SPIN_LIMIT = 1u << 24;
+
+constexpr int OD2_ROW_BITS = 40;
+constexpr unsigned long long OD2_ROW_MASK = (1ull << OD2_ROW_BITS) - 1ull;
+
+struct Od2Slot {
+    unsigned long long word;       // state | paused | live
+    unsigned long long next_walk;  // walks handed out (may overshoot N_k)
+    unsigned long long dot_next;   // dot phase number (bits 40-63) | next row of it (bits 0-39)
+    unsigned long long dot_done;   // rows of the current dot phase finished
+    unsigned long long dot_seq;    // number of the current dot phase
+    long long Nk, g0;
+    long long dot_base, dot_rows;  // first row position and number of rows
+    unsigned int k0, off0, deg0;
+    int count;                     // keys in the slot's table
+    int gen;                       // flushes of the current start
+    int posted;                    // the dot phase's fields are valid
+    int final_;                    // the dot phase ends the start (else a flush)
+};
+
+__device__ __forceinline__ int od2_state(unsigned long long w) { return (int)(w >> 62); }
+__device__ __forceinline__ uint32_t od2_paused(unsigned long long w) { return (uint32_t)((w >> 32) & 0x3fffffffu); }
+__device__ __forceinline__ uint32_t od2_live(unsigned long long w) { return (uint32_t)w; }
+__device__ __forceinline__ unsigned long long od2_pack(int st, uint32_t paused, uint32_t live) {
+    return ((unsigned long long)st << 62) | ((unsigned long long)paused << 32) | (unsigned long long)live;
+}
+__device__ __forceinline__ unsigned long long od2_word(Od2Slot& sl) {
+    return *(volatile unsigned long long*)&sl.word;
+}
+
+// A walk of a slot leaves the running set: it paused on a full table, or
+// ended (or a reservation is given back).  Returns 1 when this change starts
+// a flush, 2 when it ends the start, else 0.
+__device__ __forceinline__ int od2_release(Od2Slot& sl, bool pause) {
+    unsigned long long o = od2_word(sl);
+    for (;;) {
+        int st = od2_state(o);
+        uint32_t p = od2_paused(o), l = od2_live(o);
+        if (pause) ++p;
+        else --l;
+        int trig = 0;
+        if (st == OD2_ST_WALK) {
+            if (p > 0 && p == l) trig = 1;
+            else if (!pause && l == 0 && p == 0 &&
+                     *(volatile unsigned long long*)&sl.next_walk >= (unsigned long long)*(volatile long long*)&sl.Nk)
+                trig = 2;
+            if (trig) st = OD2_ST_DOT;
+        }
+        const unsigned long long prev = atomicCAS(&sl.word, o, od2_pack(st, p, l));
+        if (prev == o) return trig;
+        o = prev;
+    }
+}
+
+// Sets the state (walking with no paused walks, or no more starts), keeping
+// the live count: a reservation that is on its way back may be counted in it.
+__device__ __forceinline__ void od2_set_state(Od2Slot& sl, int st) {
+    unsigned long long o = od2_word(sl);
+    for (;;) {
+        const unsigned long long prev = atomicCAS(&sl.word, o, od2_pack(st, 0u, od2_live(o)));
+        if (prev == o) return;
+        o = prev;
+    }
+}
+
+// Publishes the dot phase the calling lane triggered for slot sl.  Its rows
+// are handed out by one counter that also carries the phase's number, so a
+// warp that took a row index of an earlier, finished phase (past its last
+// row) recognises it and never processes a row twice or skips one.
+__device__ __forceinline__ void od2_post(Od2Slot& sl, int trig, const int64_t* __restrict__ rp, const SubList& sub) {
+    const uint32_t k0 = *(volatile unsigned int*)&sl.k0;
+    const int64_t b = sub.ptr ? sub.ptr[k0] : rp[k0];
+    const int64_t e = sub.ptr ? sub.ptr[k0 + 1] : rp[k0 + 1];
+    const unsigned long long seq = *(volatile unsigned long long*)&sl.dot_seq + 1ull;
+    *(volatile int*)&sl.final_ = trig == 2;
+    *(volatile long long*)&sl.dot_base = b;
+    *(volatile long long*)&sl.dot_rows = e - b;
+    *(volatile unsigned long long*)&sl.dot_done = 0ull;
+    *(volatile unsigned long long*)&sl.dot_seq = seq;
+    __threadfence_block();
+    atomicExch(&sl.dot_next, seq << OD2_ROW_BITS);
+    __threadfence_block();
+    *(volatile int*)&sl.posted = 1;
+}
+
+__global__ void __launch_bounds__(256) walk_diag_od2_kernel(
+    const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const uint2* __restrict__ nod,
+    const uint2* __restrict__ eod, const uint32_t* __restrict__ ekey, const float* __restrict__ rm,
+    const int32_t* __restrict__ starts, const int64_t* __restrict__ woff, const int64_t* __restrict__ nw, SubList sub,
+    double gamma, const double* __restrict__ zeta_g, int K, float wc32, uint2 key, uint32_t req, int cap_log2,
+    double* __restrict__ qval, double* __restrict__ dacc, unsigned long long* __restrict__ counters) {
+    MCF_KERNEL_ENTRY();
+    extern __shared__ uint32_t od_keys[];
+    __shared__ float zeta[MCF_MAX_COEFFS];
+    __shared__ Od2Slot slot[OD2_SLOTS];
+    for (int k = threadIdx.x; k <= K; k += blockDim.x) zeta[k] = (float)zeta_g[k];
+    const int cap = 1 << cap_log2;
+    double* const val0 = qval + (int64_t)blockIdx.x * OD2_SLOTS * cap;
+    auto table = [&](int x) {
+        OdTable t;
+        t.key = od_keys + x * cap;
+        t.val = val0 + x * cap;
+        t.cap_log2 = cap_log2;
+        t.limit = cap - cap / 4 - (int)blockDim.x;
+        t.count = &slot[x].count;
+        return t;
+    };
+    for (int h = threadIdx.x; h < OD2_SLOTS * cap; h += blockDim.x) {
+        od_keys[h] = OD_EMPTY;
+        __stcg(val0 + h, 0.0);
+    }
+    const int64_t S = (int64_t)counters[C_STARTS];
+    const bool visit0 = 1.0f > wc32;
+    const double gg = gamma * gamma;
+    if (threadIdx.x < OD2_SLOTS) {
+        slot[threadIdx.x].word = od2_pack(OD2_ST_DOT, 0u, 0u);   // not open until loaded
+        slot[threadIdx.x].count = 0;
+        slot[threadIdx.x].posted = 0;
+        slot[threadIdx.x].dot_seq = 0ull;
+        slot[threadIdx.x].dot_next = 0ull;
+    }
+    __syncthreads();
+    // Loads the next start column into slot x (one thread; its table is empty).
+    auto load_start = [&](int x) {
+        Od2Slot& sl = slot[x];
+        const int64_t s = (int64_t)atomicAdd(&counters[C_NEXT], 1ull);
+        if (s >= S) {
+            __threadfence_block();
+            od2_set_state(sl, OD2_ST_DONE);
+            return;
+        }
+        const uint32_t k0 = (uint32_t)starts[s];
+        const uint2 od0 = nod[k0];
+        const int64_t Nk = nw[k0];
+        *(volatile unsigned int*)&sl.k0 = k0;
+        *(volatile unsigned int*)&sl.off0 = od0.x;
+        *(volatile unsigned int*)&sl.deg0 = od0.y;
+        *(volatile long long*)&sl.Nk = Nk;
+        *(volatile long long*)&sl.g0 = woff[k0];
+        *(volatile unsigned long long*)&sl.next_walk = 0ull;
+        *(volatile int*)&sl.gen = 0;
+        *(volatile int*)&sl.posted = 0;
+        *(volatile int*)&sl.count = 0;
+        if (visit0 && K >= 2) {
+            const OdTable t = table(x);
+            const int h = od_insert(t, od0.x);    // empty table: always succeeds
+            atomicAdd(&t.val[h], (double)Nk * (double)zeta[2]);
+        }
+        __threadfence_block();
+        od2_set_state(sl, OD2_ST_WALK);
+    };
+    // Clears slot y's table after its dot phase, then resumes or reloads it (one warp).
+    auto finish_dot = [&](int y) {
+        Od2Slot& sl = slot[y];
+        const OdTable t = table(y);
+        __threadfence_block();
+        for (int h = (int)(threadIdx.x & 31); h < cap; h += 32) {
+            if (t.key[h] != OD_EMPTY) {
+                t.key[h] = OD_EMPTY;
+                __stcg(t.val + h, 0.0);
+            }
+        }
+        __syncwarp();
+        __threadfence_block();
+        if ((threadIdx.x & 31) == 0) {
+            *(volatile int*)&sl.count = 0;
+            *(volatile int*)&sl.posted = 0;
+            if (*(volatile int*)&sl.final_) {
+                load_start(y);
+            } else {
+                od2_set_state(sl, OD2_ST_WALK);
+                __threadfence_block();
+                atomicAdd(&sl.gen, 1);
+            }
+        }
+        __syncwarp();
+    };
+    if (threadIdx.x < OD2_SLOTS) load_start(threadIdx.x);
+    __syncthreads();
+
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    uint32_t steps = 0, walks = 0, flags = 0;
+    bool active = false, paused = false;
+    int x = (threadIdx.x >> 5) & 1, pgen = 0;
+    int64_t g = 0;
+    uint32_t off = 0, deg = 0;
+    int k = 0;
+    float W = 1.f;
+    uint4 u = make_uint4(0u, 0u, 0u, 0u);
+    uint32_t idle_iters = 0;
+    for (;;) {
+        bool progress = false;
+        // ---- the posted dot phases: one row per slot per iteration
+        for (int y = 0; y < OD2_SLOTS; ++y) {
+            Od2Slot& sl = slot[y];
+            int ready = 0;
+            if (lane == 0) ready = od2_state(od2_word(sl)) == OD2_ST_DOT && *(volatile int*)&sl.posted;
+            if (!__shfl_sync(FULL, ready, 0)) continue;
+            __threadfence_block();
+            unsigned long long rr = 0;
+            if (lane == 0) rr = atomicAdd(&sl.dot_next, 1ull);
+            rr = __shfl_sync(FULL, rr, 0);
+            __threadfence_block();
+            if ((rr >> OD2_ROW_BITS) != *(volatile unsigned long long*)&sl.dot_seq) continue;   // an earlier phase's
+            const unsigned long long r = rr & OD2_ROW_MASK;
+            const long long rows = *(volatile long long*)&sl.dot_rows;
+            if (rows == 0) {
+                // no rows to add (not expected: a start column has rows): just clear and go on
+                if (r == 0) finish_dot(y);
+                continue;
+            }
+            if (r >= (unsigned long long)rows) continue;
+            progress = true;
+            const OdTable t = table(y);
+            const int64_t pos = *(volatile long long*)&sl.dot_base + (int64_t)r;
+            const int32_t i = sub.ptr ? sub.row[pos] : col[pos];
+            double dot = 0.0;
+            for (int64_t q = rp[i] + lane; q < rp[i + 1]; q += 32) {
+                const double qv = od_get(t, __ldg(&ekey[q]));
+                if (__double_as_longlong(qv) != 0) dot += qv;   // exact zeros change no sum
+            }
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) dot += __shfl_xor_sync(FULL, dot, d);
+            unsigned long long done = 0;
+            if (lane == 0) {
+                atomicAdd(&dacc[i], dot * (gg / (double)*(volatile long long*)&sl.Nk));
+                __threadfence_block();
+                done = atomicAdd(&sl.dot_done, 1ull);
+            }
+            done = __shfl_sync(FULL, done, 0);
+            if (done + 1 == (unsigned long long)rows) finish_dot(y);
+        }
+        // ---- paused walks go on once their slot's table is clear
+        if (paused && *(volatile int*)&slot[x].gen != pgen) {
+            __threadfence_block();
+            paused = false;
+        }
+        // ---- an idle lane takes a walk: from its slot first, else the other one
+        int trig = 0, tslot = 0;
+        for (int tries = 0; tries < OD2_SLOTS && !active && !trig; ++tries) {
+            const int y = (x + tries) % OD2_SLOTS;
+            Od2Slot& sl = slot[y];
+            const unsigned long long o = od2_word(sl);
+            if (od2_state(o) != OD2_ST_WALK || od2_paused(o) != 0 ||
+                *(volatile unsigned long long*)&sl.next_walk >= (unsigned long long)*(volatile long long*)&sl.Nk)
+                continue;
+            const unsigned long long prev = atomicAdd(&sl.word, 1ull);   // reserve: live + 1
+            if (od2_state(prev) == OD2_ST_WALK) {
+                const unsigned long long w = atomicAdd(&sl.next_walk, 1ull);
+                if (w < (unsigned long long)*(volatile long long*)&sl.Nk) {
+                    __threadfence_block();
+                    x = y;
+                    g = *(volatile long long*)&sl.g0 + (int64_t)w;
+                    off = *(volatile unsigned int*)&sl.off0;
+                    deg = *(volatile unsigned int*)&sl.deg0;
+                    k = 0;
+                    W = 1.f;
+                    active = true;
+                    progress = true;
+                    break;
+                }
+            }
+            trig = od2_release(sl, false);      // give the reservation back
+            tslot = y;
+        }
+        // ---- one step of every running walk
+        if (active && !paused) {
+            progress = true;
+            Od2Slot& sl = slot[x];
+            const OdTable t = table(x);
+            bool done = !(fabsf(W) > wc32);
+            if (!done && k >= 1) {
+                const int h = od_insert(t, off);
+                if (h < 0) {
+                    paused = true;
+                    pgen = *(volatile int*)&sl.gen;
+                    __threadfence_block();
+                    trig = od2_release(sl, true);
+                    tslot = x;
+                } else {
+                    atomicAdd(&t.val[h], (double)__fmul_rn(zeta[k + 2], W));
+                }
+            }
+            if (!done && !paused) {
+                if (k + 2 >= K || deg == 0) {
+                    done = true;
+                } else {
+                    uint32_t w0, w1;
+                    walk_words<false>(u, k, (uint32_t)g, (uint32_t)((uint64_t)g >> 32), req, key, w0, w1);
+                    const uint2 nx = load_od(eod + (int64_t)off + __umulhi(w0, deg), policy_evict_first());
+                    W = __fmul_rn(W, __ldg(rm + deg));
+                    off = nx.x;
+                    deg = nx.y;
+                    ++k;
+                    ++steps;
+                }
+            }
+            if (done) {
+                if (!isfinite(W)) flags |= 1u;
+                ++walks;
+                active = false;
+                __threadfence_block();
+                trig = od2_release(sl, false);
+                tslot = x;
+            }
+        }
+        if (trig) {
+            od2_post(slot[tslot], trig, rp, sub);
+            progress = true;
+        }
+        // ---- leave when no start is left and this warp holds no walk
+        int all_done = 1;
+        if (lane == 0)
+            for (int y = 0; y < OD2_SLOTS; ++y) all_done &= od2_state(od2_word(slot[y])) == OD2_ST_DONE;
+        all_done = __shfl_sync(FULL, all_done, 0);
+        if (all_done && !__any_sync(FULL, active)) break;
+        if (__any_sync(FULL, progress)) {
+            idle_iters = 0;
+        } else if (++idle_iters >= OD2_SPIN_LIMIT) {
+            flags |= 4u;
+            break;
+        }
+    }
+    unsigned long long ws = steps, ww = walks;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        ws += __shfl_down_sync(FULL, ws, d);
+        ww += __shfl_down_sync(FULL, ww, d);
+        flags |= __shfl_down_sync(FULL, flags, d);
     }
     if (lane == 0) {
         atomicAdd(&counters[C_STEPS], ws);
@@ -865,6 +1470,8 @@ static mcf_status finish_stats(mcf_stats* stats, const unsigned long long* count
     stats->walk_steps = (int64_t)h[C_STEPS];
     stats->flags = (uint32_t)h[C_FLAGS];
     stats->max_rel_se = 0.0;
+    stats->est_rel_err = 0.0;
+    stats->replicas = 1;
     float ms = 0.f;
     if (e0 && e1) cudaEventElapsedTime(&ms, e0, e1);
     stats->kernel_ms = ms;
@@ -917,29 +1524,26 @@ mcf_status ensure_edge_od(mcf_graph* g, cudaStream_t st) {
     return MCF_OK;
 }
 
-__global__ void build_edge_rec(int64_t nnz, const int32_t* __restrict__ col, const uint2* __restrict__ nod,
-                               uint4* __restrict__ erec) {
+__global__ void build_edge_key(int64_t nnz, const int32_t* __restrict__ col, const uint2* __restrict__ nod,
+                               uint32_t* __restrict__ ekey) {
     MCF_KERNEL_ENTRY();
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t c = col[p];
-        const uint2 od = nod[c];
-        erec[p] = make_uint4(od.x, od.y, (uint32_t)c, 0u);
-    }
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x)
+        ekey[p] = nod[col[p]].x;
 }
 
-mcf_status ensure_edge_rec(mcf_graph* g, cudaStream_t st) {
+mcf_status ensure_edge_key(mcf_graph* g, cudaStream_t st) {
     std::lock_guard<std::mutex> lk(g_records_mu);
-    if (g->edge_rec) return MCF_OK;
+    if (g->edge_key) return MCF_OK;
     MCF_TRY(ensure_node_od_locked(g, st));
-    uint4* er = nullptr;
-    if (graph_alloc(&er, (size_t)std::max<int64_t>(g->nnz, 1) * sizeof(uint4), st) != cudaSuccess) {
+    uint32_t* ek = nullptr;
+    if (graph_alloc(&ek, (size_t)std::max<int64_t>(g->nnz, 1) * sizeof(uint32_t), st) != cudaSuccess) {
         cudaGetLastError();
-        return fail(MCF_ERR_OOM, "device allocation of the per-entry neighbour records failed");
+        return fail(MCF_ERR_OOM, "device allocation of the per-entry row keys failed");
     }
-    build_edge_rec<<<grid_for(g->nnz, 256), 256, 0, st>>>(g->nnz, g->col_idx, g->node_od, er);
+    build_edge_key<<<grid_for(g->nnz, 256), 256, 0, st>>>(g->nnz, g->col_idx, g->node_od, ek);
     MCF_CUDA_TRY(cudaGetLastError());
     MCF_CUDA_TRY(cudaStreamSynchronize(st));
-    g->edge_rec = er;
+    g->edge_key = ek;
     return MCF_OK;
 }
 
@@ -1102,7 +1706,6 @@ static mcf_status solve_action(mcf_graph* g, const mcf_params* p, const double* 
 }
 
 constexpr int64_t DIAG_DENSE_MAX = 16384;   // dense row Q_k (global memory) up to this many nodes
-constexpr int64_t DIAG_EDGE_MIN_NNZ = (int64_t)1 << 20;
 
 // Launch shape of the diag kernel: threads per CTA follow the walks per start
 // (64 .. 256) and the hash holds about four visits per walk of a start, at
@@ -1112,15 +1715,7 @@ constexpr int64_t DIAG_EDGE_MIN_NNZ = (int64_t)1 << 20;
 template <bool F64, bool WEIGHTED, bool DENSE>
 static mcf_status launch_diag(const mcf_graph* g, const Prep& P, const SubList& sub, double gamma, int K, double wc,
                               uint2 key, uint32_t req, int64_t nk_hint, double* dacc, Scratch& sc, cudaStream_t st) {
-    // binary float32 walks read 16-byte neighbour records when the graph has them
-    constexpr bool can_edge = !F64 && !WEIGHTED;
-    const bool edge = can_edge && g->edge_rec != nullptr;
-    auto kern = edge ? walk_diag_kernel<F64, WEIGHTED, DENSE, can_edge> : walk_diag_kernel<F64, WEIGHTED, DENSE, false>;
-    float* rm = nullptr;
-    if (edge) {
-        MCF_TRY(sc.get(&rm, (size_t)g->max_degree + 1));
-        degree_table<<<grid_for(g->max_degree + 1, 256), 256, 0, st>>>(g->max_degree, gamma, rm);
-    }
+    auto kern = walk_diag_kernel<F64, WEIGHTED, DENSE>;
     int threads = 256;
     if (nk_hint > 0 && nk_hint <= 64) threads = 64;
     else if (nk_hint > 0 && nk_hint <= 128) threads = 128;
@@ -1140,8 +1735,72 @@ static mcf_status launch_diag(const mcf_graph* g, const Prep& P, const SubList& 
     MCF_TRY(sc.get(&qval, (size_t)grid * (size_t)std::max<int64_t>(cap, 1)));
     ScopedL2Fetch fetch(L2_FETCH_BYTES);
     kern<<<grid, threads, smem, st>>>((const Rec<F64>*)P.rec, g->col_ptr, g->row_idx, g->col_values, g->col_idx,
-                                      g->went, g->edge_rec, g->node_od, rm, P.starts, P.woff, P.nw, sub, gamma, P.zeta,
+                                      g->went, P.starts, P.woff, P.nw, sub, gamma, P.zeta,
                                       K, wc, cutoff_f32(wc), key, req, g->n, cap_log2, qval, dacc, P.counters);
+    MCF_CUDA_TRY(cudaGetLastError());
+    return MCF_OK;
+}
+
+// Launch shape of walk_diag_od_kernel: threads per CTA follow the walks per
+// start (64 .. 256); the key table holds about 16 visits per walk of a start,
+// between 2^10 and 2^DIAG_OD_CAP_LOG2 slots (4 bytes each in shared memory);
+// a start with more distinct visits adds and clears its partial row on the way.
+#ifndef MCF_DIAG_OD_CAP_LOG2
+#define MCF_DIAG_OD_CAP_LOG2 13
+#endif
+#ifndef MCF_DIAG_OD_MAX_THREADS
+#define MCF_DIAG_OD_MAX_THREADS 256
+#endif
+#ifndef MCF_DIAG_OD2
+#define MCF_DIAG_OD2 0
+#endif
+constexpr int DIAG_OD_CAP_LOG2 = MCF_DIAG_OD_CAP_LOG2;
+constexpr bool DIAG_OD2 = MCF_DIAG_OD2 != 0;
+constexpr int DIAG_OD_MAX_THREADS = MCF_DIAG_OD_MAX_THREADS;
+
+static mcf_status launch_diag_od(mcf_graph* g, const Prep& P, const SubList& sub, double gamma, int K, double wc,
+                                 uint2 key, uint32_t req, int64_t nk_hint, double* dacc, Scratch& sc, cudaStream_t st) {
+    MCF_TRY(ensure_edge_od(g, st));
+    MCF_TRY(ensure_edge_key(g, st));
+    float* rm;
+    MCF_TRY(sc.get(&rm, (size_t)g->max_degree + 1));
+    degree_table<<<grid_for(g->max_degree + 1, 256), 256, 0, st>>>(g->max_degree, gamma, rm);
+    int threads = DIAG_OD_MAX_THREADS;
+    if (nk_hint > 0 && nk_hint <= 64) threads = 64;
+    else if (nk_hint > 0 && nk_hint <= 128) threads = std::min(128, threads);
+    const int64_t want_slots = std::max<int64_t>(16 * std::max<int64_t>(nk_hint, 1), 4 * threads);
+    int cap_log2 = 10;
+    while (cap_log2 < DIAG_OD_CAP_LOG2 && ((int64_t)1 << cap_log2) < want_slots) ++cap_log2;
+    if (DIAG_OD2) {
+        // two start columns in flight per CTA, a table of 2^(cap_log2 - 1) slots each
+        const int c2 = std::max(10, cap_log2 - 1);
+        const size_t smem = (size_t)OD2_SLOTS * ((size_t)1 << c2) * sizeof(uint32_t);
+        MCF_CUDA_TRY(cudaFuncSetAttribute(walk_diag_od2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const int grid = persistent_grid(walk_diag_od2_kernel, threads, smem);
+        double* qval;
+        MCF_TRY(sc.get(&qval, (size_t)grid * OD2_SLOTS << c2));
+        ScopedL2Fetch fetch(L2_FETCH_BYTES);
+        walk_diag_od2_kernel<<<grid, threads, smem, st>>>(g->row_ptr, g->col_idx, g->node_od, g->edge_od, g->edge_key,
+                                                          rm, P.starts, P.woff, P.nw, sub, gamma, P.zeta, K,
+                                                          cutoff_f32(wc), key, req, c2, qval, dacc, P.counters);
+        MCF_CUDA_TRY(cudaGetLastError());
+        // the kernel bounds its waits; a stall it reports (flag bit 2) is an error, not a result
+        unsigned long long fl = 0;
+        MCF_CUDA_TRY(cudaMemcpyAsync(&fl, &P.counters[C_FLAGS], sizeof(fl), cudaMemcpyDeviceToHost, st));
+        MCF_CUDA_TRY(cudaStreamSynchronize(st));
+        if (fl & 4ull) return fail(MCF_ERR_CUDA, "internal: the subgraph-centrality kernel stopped waiting (no progress)");
+        return MCF_OK;
+    }
+    const size_t smem = ((size_t)1 << cap_log2) * sizeof(uint32_t);
+    MCF_CUDA_TRY(cudaFuncSetAttribute(walk_diag_od_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int grid = persistent_grid(walk_diag_od_kernel, threads, smem);
+    double* qval;
+    MCF_TRY(sc.get(&qval, (size_t)grid << cap_log2));
+    ScopedL2Fetch fetch(L2_FETCH_BYTES);
+    walk_diag_od_kernel<<<grid, threads, smem, st>>>(g->row_ptr, g->col_idx, g->node_od, g->edge_od, g->edge_key, rm,
+                                                     P.starts,
+                                                     P.woff, P.nw, sub, gamma, P.zeta, K, cutoff_f32(wc), key, req,
+                                                     cap_log2, qval, dacc, P.counters);
     MCF_CUDA_TRY(cudaGetLastError());
     return MCF_OK;
 }
@@ -1261,14 +1920,14 @@ static mcf_status solve_diag(mcf_graph* g, const mcf_params* p, const int64_t* n
             }
             const uint2 key = philox_key(p->seed);
             const bool dense = n <= DIAG_DENSE_MAX;
-            // larger graphs: one 16-byte neighbour record per step (on a small
-            // graph the node records and column indices stay in L1 and L2)
-            if (!f64 && !g->weighted && g->nnz >= DIAG_EDGE_MIN_NNZ && g->nnz < ((int64_t)1 << 32))
-                MCF_TRY(ensure_edge_rec(g, st));
             mcf_status rc;
             const int64_t nk_hint = p->walks_per_node > 0 ? p->walks_per_node : std::max<int64_t>(1, p->n_walks / std::max<int64_t>(n, 1));
 #define MCF_DIAG(F, W, D) rc = launch_diag<F, W, D>(g, P, sub, gamma, K, p->w_cutoff, key, p->request_id, nk_hint, dacc, sc, st)
-            if (f64) {
+            if (!f64 && !g->weighted && g->symmetric && !dense && g->nnz < ((int64_t)1 << 32)) {
+                // a symmetric binary graph too large for a dense row: one
+                // 8-byte record per step, rows keyed by row offset
+                rc = launch_diag_od(g, P, sub, gamma, K, p->w_cutoff, key, p->request_id, nk_hint, dacc, sc, st);
+            } else if (f64) {
                 if (g->weighted) { if (dense) MCF_DIAG(true, true, true); else MCF_DIAG(true, true, false); }
                 else { if (dense) MCF_DIAG(true, false, true); else MCF_DIAG(true, false, false); }
             } else {
@@ -1806,6 +2465,8 @@ static mcf_status solve_tc_noalloc(int64_t n, int64_t nnz, const int64_t* row_pt
     if (p->precision != MCF_F64 && p->precision != MCF_F32W_F64ACC)
         return fail(MCF_ERR_INVALID_ARG, "unknown precision");
     if (p->deterministic != 0) return fail(MCF_ERR_INVALID_ARG, "deterministic is reserved and must be 0");
+    if (p->target_rel_err != 0.0)
+        return fail(MCF_ERR_INVALID_ARG, "accuracy-targeted solves need scratch: target_rel_err must be 0 here");
     if (!(p->scale >= 0.0) || !isfinite(p->scale)) return fail(MCF_ERR_INVALID_ARG, "scale must be finite and >= 0");
     for (int k = 0; k < p->n_coeffs; ++k)
         if (!isfinite(p->coeffs[k])) return fail(MCF_ERR_INVALID_ARG, "coefficients must be finite");
@@ -1882,6 +2543,139 @@ static mcf_status solve_tc_noalloc(int64_t n, int64_t nnz, const int64_t* row_pt
     return MCF_OK;
 }
 
+// ====================================================================== accuracy-targeted solves
+// A solve with params.target_rel_err > 0 runs independent replicas of the
+// plain solve (replica r: seed + r * 0x9E3779B97F4A7C15, so replica 0 is the
+// plain solve) and returns their mean.  The replicas alternate between two
+// halves H1, H2; est = max_i |mean_H1,i - mean_H2,i| / 2 / max_i |mean_i| has the
+// spread of the relative l_inf error of the mean of all replicas (the two
+// half-means differ by twice that error's standard deviation per entry), an
+// estimate of the error in the standard-error sense of Section 3.5 that
+// needs no variance formula, so it serves every query kind.  Starting from two
+// replicas, the count grows to R (est / target)^2 x 1.25 (Theorem 1: the error
+// falls like N^-1/2) until est <= target or the walk cap is reached.
+__global__ void rep_add(int64_t m, const double* __restrict__ y, double* __restrict__ h) {
+    MCF_KERNEL_ENTRY();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+        h[i] += y[i];
+}
+
+// out = (H1 + H2) / (c1 + c2); mx[0] = max |H1/c1 - H2/c2| / 2, mx[1] = max |out|
+// (as the bits of non-negative doubles, which order like the values).
+__global__ void rep_finish(int64_t m, const double* __restrict__ h1, const double* __restrict__ h2, double c1,
+                           double c2, double* __restrict__ out, unsigned long long* __restrict__ mx) {
+    MCF_KERNEL_ENTRY();
+    double d = 0.0, a = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        const double mean = (h1[i] + h2[i]) / (c1 + c2);
+        out[i] = mean;
+        d = fmax(d, 0.5 * fabs(h1[i] / c1 - h2[i] / c2));
+        a = fmax(a, fabs(mean));
+    }
+#pragma unroll
+    for (int k = 16; k > 0; k >>= 1) {
+        d = fmax(d, __shfl_xor_sync(0xffffffffu, d, k));
+        a = fmax(a, __shfl_xor_sync(0xffffffffu, a, k));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (d > 0.0) atomicMax(&mx[0], (unsigned long long)__double_as_longlong(d));
+        if (a > 0.0) atomicMax(&mx[1], (unsigned long long)__double_as_longlong(a));
+    }
+}
+
+using SolveOnce = std::function<mcf_status(const mcf_params&, double*, mcf_stats*)>;
+constexpr int64_t BUDGET_DEFAULT_MAX_WALKS = (int64_t)1 << 34;
+constexpr int BUDGET_MAX_REPLICAS = 4096;
+
+static mcf_status solve_budgeted(int64_t m, double* out, const mcf_params* p, mcf_stats* stats, const SolveOnce& one) {
+    const double target = p->target_rel_err;
+    const int64_t cap = p->max_walks > 0 ? p->max_walks : BUDGET_DEFAULT_MAX_WALKS;
+    cudaStream_t st = (cudaStream_t)p->stream;
+    keep_pool_memory();
+    Scratch sc(st);
+    double *yr, *h1, *h2, *mean;
+    unsigned long long* mx;
+    const int64_t mm = std::max<int64_t>(m, 1);
+    MCF_TRY(sc.get(&yr, mm));
+    MCF_TRY(sc.get(&h1, mm));
+    MCF_TRY(sc.get(&h2, mm));
+    MCF_TRY(sc.get(&mx, 2));
+    const bool out_on_dev = is_device_ptr(out);
+    if (out_on_dev) mean = out;
+    else MCF_TRY(sc.get(&mean, mm));
+    MCF_CUDA_TRY(cudaMemsetAsync(h1, 0, mm * sizeof(double), st));
+    MCF_CUDA_TRY(cudaMemsetAsync(h2, 0, mm * sizeof(double), st));
+    int R = 0;
+    int64_t walks = 0, steps = 0, per_replica = 0;
+    double kernel_ms = 0.0, est = INFINITY;
+    uint32_t flags = 0;
+    auto run_to = [&](int R_next) -> mcf_status {
+        for (; R < R_next; ++R) {
+            mcf_params q = *p;
+            q.target_rel_err = 0.0;
+            q.error_estimate = 0;
+            q.seed = p->seed + (uint64_t)R * 0x9E3779B97F4A7C15ull;
+            mcf_stats s1{};
+            MCF_TRY(one(q, yr, &s1));
+            if (m > 0) rep_add<<<grid_for(m, 256), 256, 0, st>>>(m, yr, (R & 1) ? h2 : h1);
+            walks += s1.walks;
+            steps += s1.walk_steps;
+            kernel_ms += s1.kernel_ms;
+            flags |= s1.flags;
+            per_replica = std::max<int64_t>(per_replica, s1.walks);
+        }
+        const double c1 = (double)((R + 1) / 2), c2 = (double)(R / 2);
+        MCF_CUDA_TRY(cudaMemsetAsync(mx, 0, 2 * sizeof(unsigned long long), st));
+        if (m > 0) rep_finish<<<grid_for(m, 256), 256, 0, st>>>(m, h1, h2, c1, c2, mean, mx);
+        MCF_CUDA_TRY(cudaGetLastError());
+        unsigned long long hm[2];
+        MCF_CUDA_TRY(cudaMemcpyAsync(hm, mx, sizeof(hm), cudaMemcpyDeviceToHost, st));
+        MCF_CUDA_TRY(cudaStreamSynchronize(st));
+        double d, a;
+        memcpy(&d, &hm[0], sizeof(d));
+        memcpy(&a, &hm[1], sizeof(a));
+        est = a > 0.0 ? d / a : 0.0;
+        return MCF_OK;
+    };
+    MCF_TRY(run_to(2));
+    while (est > target) {
+        const int64_t by_cap = per_replica > 0 ? cap / per_replica : BUDGET_MAX_REPLICAS;
+        const int R_cap = (int)std::min<int64_t>(BUDGET_MAX_REPLICAS, by_cap) & ~1;
+        const double want = (double)R * (est / target) * (est / target) * 1.25;
+        int R_next = (int)std::min<double>((double)R_cap, ceil(want));
+        R_next = (R_next + 1) & ~1;
+        if (R_next > R_cap) R_next = R_cap;
+        if (R_next <= R) break;   // the walk cap is reached
+        MCF_TRY(run_to(R_next));
+    }
+    if (!out_on_dev && m > 0) {
+        MCF_CUDA_TRY(cudaMemcpyAsync(out, mean, m * sizeof(double), cudaMemcpyDeviceToHost, st));
+        MCF_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    if (stats) {
+        stats->walks = walks;
+        stats->walk_steps = steps;
+        stats->kernel_ms = kernel_ms;
+        stats->flags = flags;
+        stats->max_rel_se = 0.0;
+        stats->est_rel_err = est;
+        stats->replicas = R;
+    }
+    if (est > target)
+        return fail(MCF_ERR_ACCURACY_BUDGET, "estimated relative error " + std::to_string(est) + " above the target " +
+                                                 std::to_string(target) + " at the walk cap (" + std::to_string(walks) +
+                                                 " walks in " + std::to_string(R) + " replicas); the mean is returned");
+    return MCF_OK;
+}
+
+static mcf_status check_budget(const mcf_params* p) {
+    if (!p) return fail(MCF_ERR_INVALID_ARG, "params is NULL");
+    if (!(p->target_rel_err >= 0.0) || !isfinite(p->target_rel_err))
+        return fail(MCF_ERR_INVALID_ARG, "target_rel_err must be finite and >= 0");
+    if (p->max_walks < 0) return fail(MCF_ERR_INVALID_ARG, "max_walks must be >= 0");
+    return MCF_OK;
+}
+
 }  // namespace mcf
 
 using namespace mcf;
@@ -1890,23 +2684,48 @@ uint64_t mcf::kernel_runs_walk() { return this_unit_kernel_runs(); }
 
 extern "C" {
 
+// The single-query entry points: with params->target_rel_err > 0 the solve
+// runs as replicas until the estimated error meets the target.
+static mcf_status action_entry(mcf_graph_t g, const mcf_params* params, const double* v, double* y, mcf_stats* stats,
+                               bool ones, const int64_t* nodes, int64_t n_nodes) {
+    set_error("");
+    MCF_TRY(check_budget(params));
+    if (params->target_rel_err == 0.0) return solve_action(g, params, v, y, stats, ones, nodes, n_nodes);
+    MCF_TRY(check_params(g, params));
+    if (!y) return fail(MCF_ERR_INVALID_ARG, "y is NULL");
+    if (nodes && n_nodes < 0) return fail(MCF_ERR_INVALID_ARG, "n_nodes must be >= 0");
+    const int64_t m = nodes ? n_nodes : g->n;
+    return solve_budgeted(m, y, params, stats, [&](const mcf_params& q, double* yr, mcf_stats* s1) {
+        return solve_action(g, &q, v, yr, s1, ones, nodes, n_nodes);
+    });
+}
+
 mcf_status mcf_action(mcf_graph_t g, const mcf_params* params, const double* v, double* y, mcf_stats* stats) {
-    return solve_action(g, params, v, y, stats, false);
+    return action_entry(g, params, v, y, stats, false, nullptr, -1);
 }
 
 mcf_status mcf_action_nodes(mcf_graph_t g, const mcf_params* params, const double* v, const int64_t* nodes,
                             int64_t n_nodes, double* y, mcf_stats* stats) {
     if (!nodes) return fail(MCF_ERR_INVALID_ARG, "nodes is NULL");
-    return solve_action(g, params, v, y, stats, v == nullptr, nodes, n_nodes);
+    return action_entry(g, params, v, y, stats, v == nullptr, nodes, n_nodes);
 }
 
 mcf_status mcf_total_communicability(mcf_graph_t g, const mcf_params* params, double* y, mcf_stats* stats) {
-    return solve_action(g, params, nullptr, y, stats, true);
+    return action_entry(g, params, nullptr, y, stats, true, nullptr, -1);
 }
 
 mcf_status mcf_subgraph_centrality(mcf_graph_t g, const mcf_params* params, const int64_t* nodes, int64_t n_nodes,
                                    double* d, mcf_stats* stats) {
-    return solve_diag(g, params, nodes, n_nodes, d, stats);
+    set_error("");
+    MCF_TRY(check_budget(params));
+    if (params->target_rel_err == 0.0) return solve_diag(g, params, nodes, n_nodes, d, stats);
+    MCF_TRY(check_params(g, params));
+    if (!d) return fail(MCF_ERR_INVALID_ARG, "d is NULL");
+    if (nodes && n_nodes < 0) return fail(MCF_ERR_INVALID_ARG, "n_nodes must be >= 0");
+    const int64_t m = nodes ? n_nodes : g->n;
+    return solve_budgeted(m, d, params, stats, [&](const mcf_params& q, double* dr, mcf_stats* s1) {
+        return solve_diag(g, &q, nodes, n_nodes, dr, s1);
+    });
 }
 
 mcf_status mcf_katz(mcf_graph_t g, double gamma, int32_t K, const mcf_params* params, double* y, mcf_stats* stats) {
@@ -1931,7 +2750,7 @@ mcf_status mcf_katz(mcf_graph_t g, double gamma, int32_t K, const mcf_params* pa
     p.coeffs = ones;
     p.n_coeffs = K + 1;
     p.scale = gamma;
-    return solve_action(g, &p, nullptr, y, stats, true);
+    return action_entry(g, &p, nullptr, y, stats, true, nullptr, -1);
 }
 
 mcf_status mcf_funm_full(mcf_graph_t g, const mcf_params* params, double* F, mcf_stats* stats) {

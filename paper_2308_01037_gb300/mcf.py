@@ -41,7 +41,8 @@ class mcf_params(ctypes.Structure):
     _fields_ = [("coeffs", ctypes.c_void_p), ("n_coeffs", ctypes.c_int32), ("scale", ctypes.c_double),
                 ("n_walks", ctypes.c_int64), ("walks_per_node", ctypes.c_int64), ("w_cutoff", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("request_id", ctypes.c_uint32), ("precision", ctypes.c_int32),
-                ("deterministic", ctypes.c_int32), ("error_estimate", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+                ("deterministic", ctypes.c_int32), ("error_estimate", ctypes.c_int32), ("stream", ctypes.c_void_p),
+                ("target_rel_err", ctypes.c_double), ("max_walks", ctypes.c_int64)]
 
 
 class mcf_query(ctypes.Structure):
@@ -68,7 +69,7 @@ class mcf_server_stats(ctypes.Structure):
                 ("batches", ctypes.c_int64), ("walk_steps", ctypes.c_int64), ("p50_ms", ctypes.c_double),
                 ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
                 ("busy_s", ctypes.c_double), ("device_overlap_ms", ctypes.c_double),
-                ("max_concurrent_batches", ctypes.c_int64)]
+                ("max_concurrent_batches", ctypes.c_int64), ("plan_s", ctypes.c_double), ("run_s", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -76,11 +77,11 @@ class mcf_server_stats(ctypes.Structure):
 
 class mcf_stats(ctypes.Structure):
     _fields_ = [("walks", ctypes.c_int64), ("walk_steps", ctypes.c_int64), ("kernel_ms", ctypes.c_double),
-                ("flags", ctypes.c_uint32), ("max_rel_se", ctypes.c_double)]
+                ("flags", ctypes.c_uint32), ("max_rel_se", ctypes.c_double), ("est_rel_err", ctypes.c_double),
+                ("replicas", ctypes.c_int32)]
 
     def as_dict(self):
-        return {"walks": self.walks, "walk_steps": self.walk_steps, "kernel_ms": self.kernel_ms, "flags": self.flags,
-                "max_rel_se": self.max_rel_se}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 # Every entry point declared in include/mcf.h, with its ctypes signature.
@@ -112,6 +113,7 @@ SIGNATURES = {
     "mcf_batch_device_bytes": ([_P, _P], ctypes.c_int),
     "mcf_total_communicability_noalloc": ([_I64, _I64, _P, _P, _P, _P], ctypes.c_int),
     "mcf_gather_probe": ([_I64, _I64, _P, _P], ctypes.c_int),
+    "mcf_second_moment_radius": ([_P, _D, _D, _I32, _P], ctypes.c_int),
     "mcf_kernel_launches": ([_P], ctypes.c_int),
     "mcf_last_error": ([], ctypes.c_char_p),
     "mcf_version": ([], ctypes.c_char_p),
@@ -145,6 +147,23 @@ def load():
 def _check(status: int):
     if status != MCF_OK:
         raise McfError(status, (load().mcf_last_error() or b"").decode())
+
+
+MCF_ERR_ACCURACY_BUDGET = 8
+
+
+def _solved(status: int, y, st, stats: bool):
+    """Result of a solve entry point.  An accuracy-targeted solve that stops at
+    its walk cap still returns its mean: with ``stats=True`` the result comes
+    back with ``budget_met = False`` in the stats; without, the binding raises."""
+    met = status != MCF_ERR_ACCURACY_BUDGET
+    if status != MCF_OK and not (stats and not met):
+        _check(status)
+    if stats:
+        d = st.as_dict()
+        d["budget_met"] = met
+        return y, d
+    return y
 
 
 # ---------------------------------------------------------------- marshalling helpers
@@ -193,11 +212,11 @@ def _stream_of(*arrays):
 
 
 def _params(coeffs, scale=0.0, n_walks=0, walks_per_node=0, w_cutoff=0.0, seed=0, request_id=0,
-            precision=MCF_F32W_F64ACC, stream=None, error_estimate=False):
+            precision=MCF_F32W_F64ACC, stream=None, error_estimate=False, target_rel_err=0.0, max_walks=0):
     c = np.ascontiguousarray(coeffs, dtype=np.float64)
     p = mcf_params(c.ctypes.data, len(c), float(scale), int(n_walks), int(walks_per_node), float(w_cutoff),
                    int(seed) & 0xFFFFFFFFFFFFFFFF, int(request_id) & 0xFFFFFFFF, int(precision), 0,
-                   1 if error_estimate else 0, stream if stream else None)
+                   1 if error_estimate else 0, stream if stream else None, float(target_rel_err), int(max_walks))
     return p, c
 
 
@@ -253,6 +272,13 @@ def mcf_spectral_radius(g: GraphHandle, tol=1e-10, max_iter=10000) -> float:
     return out.value
 
 
+def mcf_second_moment_radius(g: GraphHandle, scale, tol=1e-8, max_iter=10000) -> float:
+    """Spectral radius of diag(sum_j |a'_ij|) |A'| with A' = scale * A (the walk weights' second-moment growth)."""
+    out = ctypes.c_double()
+    _check(load().mcf_second_moment_radius(g.handle, float(scale), float(tol), int(max_iter), ctypes.byref(out)))
+    return out.value
+
+
 def mcf_gershgorin(g: GraphHandle) -> float:
     out = ctypes.c_double()
     _check(load().mcf_gershgorin(g.handle, ctypes.byref(out)))
@@ -276,8 +302,8 @@ def mcf_action(g: GraphHandle, v, coeffs, out=None, device_out=None, stats=False
     yp, ky = _out_ptr(y)
     st = mcf_stats()
     p, kc = _params(coeffs, stream=kw.pop("stream", None) or _stream_of(v, y), **kw)
-    _check(load().mcf_action(g.handle, ctypes.byref(p), vp, yp, ctypes.byref(st) if stats else None))
-    return (y, st.as_dict()) if stats else y
+    rc = load().mcf_action(g.handle, ctypes.byref(p), vp, yp, ctypes.byref(st) if stats else None)
+    return _solved(rc, y, st, stats)
 
 
 def mcf_action_nodes(g: GraphHandle, nodes, coeffs, v=None, out=None, device_out=None, stats=False, **kw):
@@ -288,9 +314,9 @@ def mcf_action_nodes(g: GraphHandle, nodes, coeffs, v=None, out=None, device_out
     yp, ky = _out_ptr(y)
     st = mcf_stats()
     p, kc = _params(coeffs, stream=kw.pop("stream", None) or _stream_of(nodes, y), **kw)
-    _check(load().mcf_action_nodes(g.handle, ctypes.byref(p), vp, npt, int(len(nodes)), yp,
-                                   ctypes.byref(st) if stats else None))
-    return (y, st.as_dict()) if stats else y
+    rc = load().mcf_action_nodes(g.handle, ctypes.byref(p), vp, npt, int(len(nodes)), yp,
+                                 ctypes.byref(st) if stats else None)
+    return _solved(rc, y, st, stats)
 
 
 def mcf_total_communicability(g: GraphHandle, coeffs, out=None, device_out=None, stats=False, **kw):
@@ -299,8 +325,8 @@ def mcf_total_communicability(g: GraphHandle, coeffs, out=None, device_out=None,
     yp, ky = _out_ptr(y)
     st = mcf_stats()
     p, kc = _params(coeffs, stream=kw.pop("stream", None) or _stream_of(y), **kw)
-    _check(load().mcf_total_communicability(g.handle, ctypes.byref(p), yp, ctypes.byref(st) if stats else None))
-    return (y, st.as_dict()) if stats else y
+    rc = load().mcf_total_communicability(g.handle, ctypes.byref(p), yp, ctypes.byref(st) if stats else None)
+    return _solved(rc, y, st, stats)
 
 
 def mcf_subgraph_centrality(g: GraphHandle, coeffs, nodes=None, out=None, device_out=None, stats=False, **kw):
@@ -311,9 +337,9 @@ def mcf_subgraph_centrality(g: GraphHandle, coeffs, nodes=None, out=None, device
     dp, kd = _out_ptr(d)
     st = mcf_stats()
     p, kc = _params(coeffs, stream=kw.pop("stream", None) or _stream_of(nodes, d), **kw)
-    _check(load().mcf_subgraph_centrality(g.handle, ctypes.byref(p), npt, int(m), dp,
-                                          ctypes.byref(st) if stats else None))
-    return (d, st.as_dict()) if stats else d
+    rc = load().mcf_subgraph_centrality(g.handle, ctypes.byref(p), npt, int(m), dp,
+                                        ctypes.byref(st) if stats else None)
+    return _solved(rc, d, st, stats)
 
 
 def mcf_katz(g: GraphHandle, gamma, K=0, out=None, device_out=None, stats=False, **kw):
@@ -322,9 +348,8 @@ def mcf_katz(g: GraphHandle, gamma, K=0, out=None, device_out=None, stats=False,
     yp, ky = _out_ptr(y)
     st = mcf_stats()
     p, kc = _params([1.0], stream=kw.pop("stream", None) or _stream_of(y), **kw)
-    _check(load().mcf_katz(g.handle, float(gamma), int(K), ctypes.byref(p), yp,
-                           ctypes.byref(st) if stats else None))
-    return (y, st.as_dict()) if stats else y
+    rc = load().mcf_katz(g.handle, float(gamma), int(K), ctypes.byref(p), yp, ctypes.byref(st) if stats else None)
+    return _solved(rc, y, st, stats)
 
 
 MCF_FULL_MAX_NODES = 16384
@@ -370,8 +395,8 @@ def _query_struct(q):
     op, ko = _out_ptr(out)
     vp, kv = _ptr(q.get("v"), np.float64)
     npt, kn = _ptr(nodes, np.int64)
-    pkw = {k: q[k] for k in ("scale", "n_walks", "walks_per_node", "w_cutoff", "seed", "request_id", "precision")
-           if k in q}
+    pkw = {k: q[k] for k in ("scale", "n_walks", "walks_per_node", "w_cutoff", "seed", "request_id", "precision",
+                             "target_rel_err", "max_walks") if k in q}
     p, kc = _params(q.get("coeffs", [1.0]), **pkw)
     st = mcf_query(g.handle, kind, int(q.get("katz_terms", 0)), float(q.get("katz_gamma", 0.0)), p, vp, npt,
                    int(0 if nodes is None else len(nodes)), op)
@@ -465,12 +490,15 @@ def mcf_server_poll(s: ServerHandle, ticket: int):
     return bool(done.value), res.value
 
 
-def mcf_server_wait(s: ServerHandle, ticket: int, timeout_s: float = -1.0):
-    """Waits for a ticket; returns (output array, latency in ms); raises on a failed request."""
+def mcf_server_wait(s: ServerHandle, ticket: int, timeout_s: float = -1.0, accept_budget_miss: bool = False):
+    """Waits for a ticket; returns (output array, latency in ms); raises on a failed request
+    (an accuracy-targeted request that stopped at its walk cap counts as served when
+    ``accept_budget_miss`` is set: its mean is in the output)."""
     res, lat = ctypes.c_int(), ctypes.c_double()
     _check(load().mcf_server_wait(s.handle, ctypes.c_uint64(ticket), float(timeout_s), ctypes.byref(res),
                                   ctypes.byref(lat)))
-    _check(res.value)
+    if not (accept_budget_miss and res.value == MCF_ERR_ACCURACY_BUDGET):
+        _check(res.value)
     out, _ = s.pending.pop(ticket)
     return out, lat.value
 

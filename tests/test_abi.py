@@ -32,6 +32,22 @@ def test_header_declares_the_survey_boundary():
         assert required in names
 
 
+def declared_arg_counts():
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    out = {}
+    for name, args in re.findall(r"\b(mcf_[a-z_0-9]+)\s*\(([^)]*)\)\s*;", text):
+        args = args.strip()
+        out[name] = 0 if args in ("", "void") else args.count(",") + 1
+    return out
+
+
+def test_binding_signatures_have_the_header_argument_counts():
+    counts = declared_arg_counts()
+    assert set(counts) == set(M.SIGNATURES)
+    for name, (args, _) in M.SIGNATURES.items():
+        assert len(args) == counts[name], name
+
+
 def test_library_exports_every_declared_symbol(lib):
     for name in declared_entry_points():
         assert hasattr(lib, name), name

@@ -48,13 +48,21 @@ class _Graph:
         self.closed = True
 
 
+LAUNCHES_PER_SOLVE = 17
+GATHER = 4.0e10
+
+
 def _fake_library(g):
     M = types.SimpleNamespace(MCF_F32W_F64ACC=1)
     M.load = lambda: None
+    M.launches = 0
+    M.mcf_kernel_launches = lambda: M.launches
+    M.mcf_gather_probe = lambda nbytes, reads, stream=None: GATHER
     M.mcf_create_graph = lambda n, rp, ci, *a, **k: _Graph(n)
     M.mcf_spectral_radius = lambda h, tol=1e-10, max_iter=1000: R.lambda_max(g)
 
     def solve(h, coeffs, out=None, stats=False, scale=1.0, **kw):
+        M.launches += LAUNCHES_PER_SOLVE
         y = R.series_action(g, coeffs, scale)
         out.copy_(torch.from_numpy(y))
         st = {"walks": WALKS_PER_SOLVE, "walk_steps": STEPS_PER_SOLVE, "kernel_ms": KERNEL_MS, "flags": 0,
@@ -106,7 +114,9 @@ def test_main_prints_one_contract_line(monkeypatch):
     assert d["config"]["workload"] == w["label"]
     # value = all walk steps of the timed solves / the timed region
     assert d["value"] == pytest.approx(STEPS_PER_SOLVE / (d["ms_per_step"] / 1000.0), rel=1e-9)
-    assert d["gpu_launches"] == 3 * bench.LAUNCHES_PER_SOLVE["tc"]
+    assert d["gpu_launches"] == 3 * LAUNCHES_PER_SOLVE      # counted over the timed solves only
+    assert d["roofline"]["gather_ceiling"] == GATHER
+    assert d["roofline"]["frac_of_gather_ceiling"] == pytest.approx(STEPS_PER_SOLVE / (KERNEL_MS / 1000.0) / GATHER)
     rf = d["roofline"]
     assert rf["bound"] == "hbm" and rf["unit"] == "GB/s" and rf["kernel"] == "walk_tc_kernel"
     achieved = 16 * STEPS_PER_SOLVE / (KERNEL_MS / 1000.0) / 1e9

@@ -181,6 +181,12 @@ REFERENCE_MUTANTS = [
      "var[i] += a * a * max(e2[i] - e1[i] ** 2, 0.0) / nw[i]"),
     ("enum_rows_transposed", "a visit of l adds row l of A'",
      "Arow[i, j] += a\n", "Arow[j, i] += a\n"),
+    ("moment_signed_entries", "second moments carry |a'_ij| (Definition 1, Eq. weights)",
+     "A = abs(csr_matrix(g, values, gamma))", "A = csr_matrix(g, values, gamma)"),
+    ("moment_without_row_sums", "M = diag(s') |A'|: the weight multiplier s'_l",
+     "S = sp.diags(r) @ A @ sp.diags(r)", "S = A"),
+    ("moment_rows_squared", "M = diag(s') |A'| is similar to D^1/2 |A'| D^1/2",
+     "r = np.sqrt(s)", "r = s"),
 ]
 
 

@@ -115,3 +115,41 @@ def test_weighted_series_matches_dense():
     c = R.exp_coeffs(30)
     F = R.dense_funm(gam * A, c)
     assert np.allclose(R.series_action(g, c, gam, values=w), F.sum(1), rtol=1e-12, atol=1e-12)
+
+
+# ---------------------------------------------------------------- second-moment growth rho(diag(s') |A'|)
+def test_second_moment_radius_closed_forms():
+    """rho(diag(s')|A'|) in closed form: K_n (s' = gamma (n-1) everywhere, so
+    M = gamma^2 (n-1) A: rho = gamma^2 (n-1)^2); the star S_n (S = D^1/2 A D^1/2
+    = sqrt(n-1) A: rho = gamma^2 (n-1)); the complete bipartite K_{p,q}
+    (S = sqrt(pq) A, rho(A) = sqrt(pq): rho = gamma^2 p q); K_n with every weight
+    w (rho = gamma^2 w^2 (n-1)^2), and with random signs (|A'| enters)."""
+    gam = 0.37
+    for n in (3, 6, 11):
+        assert R.second_moment_radius(I.complete(n), gam) == pytest.approx(gam ** 2 * (n - 1) ** 2, rel=1e-12)
+        assert R.second_moment_radius(I.star(n), gam) == pytest.approx(gam ** 2 * (n - 1), rel=1e-12)
+    p, q = 3, 5
+    kpq = I.from_edges(p + q, [(i, p + j) for i in range(p) for j in range(q)])
+    assert R.second_moment_radius(kpq, gam) == pytest.approx(gam ** 2 * p * q, rel=1e-12)
+    g = I.complete(7)
+    w = np.full(g.nnz, 1.5, np.float32)
+    assert R.second_moment_radius(g, gam, values=w) == pytest.approx(gam ** 2 * 1.5 ** 2 * 36, rel=1e-6)
+    signs = np.where(np.random.default_rng(1).random(g.nnz) < 0.5, -1.5, 1.5).astype(np.float32)
+    assert R.second_moment_radius(g, gam, values=signs) == pytest.approx(gam ** 2 * 1.5 ** 2 * 36, rel=1e-6)
+
+
+def test_second_moment_radius_is_the_growth_of_the_enumerated_second_moment():
+    """With the single coefficient zeta_K = 1 the exact second moment of a
+    walk's contribution (Lemma 2 enumerated term by term) grows by rho per
+    step for large K, on an irregular graph (BA n = 9)."""
+    g = I.barabasi_albert(9, 2, 4)
+    gam = 0.3
+    rho = R.second_moment_radius(g, gam)
+    m2 = []
+    for K in (8, 9):
+        c = np.zeros(K + 1)
+        c[K] = 1.0
+        ex = R.enumerate_action(g, c, gamma=gam)
+        m2.append(np.sum(ex["var_walk"] + ex["Eq"] ** 2))
+    assert rho > 1.0    # this graph's hubs make the second moment grow
+    assert m2[1] / m2[0] == pytest.approx(rho, rel=0.01)
