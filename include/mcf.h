@@ -61,7 +61,7 @@ typedef enum {
     MCF_ERR_CUDA = 4,             /* a CUDA runtime call failed; see mcf_last_error() */
     MCF_ERR_ADMISSION = 5,        /* a request does not fit the caller's memory budget */
     MCF_ERR_TIMEOUT = 6,          /* mcf_server_wait gave up before the request completed */
-    MCF_ERR_CANCELLED = 7,        /* reserved (not returned by this build) */
+    MCF_ERR_CANCELLED = 7,        /* a queued server request was cancelled (mcf_server_cancel) */
     MCF_ERR_ACCURACY_BUDGET = 8,  /* an accuracy-targeted solve hit its walk cap above the target error */
     MCF_WARN_OVERFLOW = 9,        /* reserved: a float32 weight overflow sets bit 0 of mcf_stats.flags */
     MCF_ERR_UNSUPPORTED = 10      /* a valid request this build does not implement */
@@ -96,7 +96,13 @@ typedef struct {
     uint64_t seed;          /* Philox key                                                        */
     uint32_t request_id;    /* fourth Philox counter word: independent streams per request       */
     int32_t precision;      /* mcf_precision                                                     */
-    int32_t deterministic;  /* reserved, must be 0                                               */
+    int32_t deterministic;  /* 1: RandFunmAction solves (mcf_action, mcf_action_nodes,
+                               mcf_total_communicability, mcf_katz) give bit-identical results
+                               on every run: each walk writes its value to a float64 slot of its
+                               own (8 bytes of device scratch per walk) and the walks of a start
+                               are summed in walk order with a fixed reduction tree, instead of
+                               float64 atomics in arrival order.  Other solves return
+                               MCF_ERR_UNSUPPORTED with 1.  0: atomics (faster).              */
     int32_t error_estimate; /* 1: also estimate the standard error (mcf_stats.max_rel_se) of a
                                single-query RandFunmAction solve (mcf_action, mcf_action_nodes,
                                mcf_total_communicability, mcf_katz); 0: off. Ignored elsewhere. */
@@ -318,7 +324,8 @@ typedef struct {
 } mcf_server_config;
 
 typedef struct {
-    int64_t submitted, completed, rejected, batches;
+    int64_t submitted, completed, rejected, batches;   /* completed includes cancelled requests */
+    int64_t cancelled;
     int64_t walk_steps;        /* over completed requests                          */
     double p50_ms, p99_ms, max_ms, mean_ms;  /* latency submit -> result ready      */
     double busy_s;             /* wall time from the first submit to the last completion */
@@ -361,6 +368,12 @@ mcf_status mcf_batch_device_bytes(mcf_batch_t batch, size_t* bytes);
  * Completed requests stay listed, so every ticket can be polled or waited on
  * again, until mcf_server_release or mcf_server_destroy releases them. */
 mcf_status mcf_server_submit(mcf_server_t s, const mcf_query* query, uint64_t* ticket);
+
+/* Cancels a request that is still queued: it completes at once with status
+ * MCF_ERR_CANCELLED and its output is not written.  A request that is already
+ * running (or done) is not affected: the call returns MCF_ERR_INVALID_ARG.
+ * Errors: MCF_ERR_INVALID_ARG (unknown ticket, or not queued). */
+mcf_status mcf_server_cancel(mcf_server_t s, uint64_t ticket);
 
 /* Forgets a completed request (its ticket becomes unknown), so a long-running
  * server does not keep every request it ever served.
@@ -435,6 +448,14 @@ mcf_status mcf_gather_probe(int64_t array_bytes, int64_t reads, void* stream, do
  * counts its own execution, so a replayed CUDA graph counts again.
  * Synchronises with the device (the counters are read back). */
 mcf_status mcf_kernel_launches(uint64_t* count);
+
+/* Host-side fault injection for testing callers' error paths; the paper has
+ * no counterpart.  After `after` more successful device scratch allocations
+ * of solves and batch plans (any thread), the next one fails as if the
+ * device were full: the call returns MCF_ERR_OOM and releases what it had
+ * taken; later allocations succeed again.
+ * after < 0 switches the injection off.  Nothing runs on the GPU. */
+mcf_status mcf_inject_allocation_failure(int64_t after);
 
 /* Thread-local description of the last error of this thread ("" if none). */
 const char* mcf_last_error(void);

@@ -2,8 +2,9 @@
 //
 // Total-communicability and Katz queries (RandFunmAction with v = 1,
 // Algorithm 3) on binary graphs in MCF_F32W_F64ACC with fewer than
-// B_FUSED_MAX_WALKS walks share ONE persistent walk launch; subgraph-centrality queries (RandFunmDiag, Section 3.3) on binary
-// graphs in MCF_F32W_F64ACC share one diag launch.  Their preparation
+// B_FUSED_MAX_WALKS walks share ONE persistent walk launch; subgraph-centrality
+// queries (RandFunmDiag, Section 3.3) on symmetric binary graphs in
+// MCF_F32W_F64ACC share one diag launch.  Their preparation
 // (Definition 1's allocation) and epilogues are segmented kernels over the
 // concatenation of all their node sets.  Each query keeps its own walk ids
 // (the exclusive prefix of N_i over its own nodes) and Philox streams, and the
@@ -37,9 +38,8 @@ constexpr int B_RED_BLOCKS = 256;    // must equal the single-query colnorm grid
 constexpr int64_t B_FUSED_MAX_WALKS = (int64_t)1 << 25;
 constexpr int B_RED_THREADS = 256;
 constexpr int B_CHUNK = 32;
-constexpr int64_t B_DENSE_MAX = 16384;
 enum { BC_NEXT = 0, BC_STEPS = 1, BC_WALKS = 2, BC_FLAGS = 3, BC_TOTAL = 4, BC_STARTS = 5, BC_STARTS_TC = 6,
-       BC_CHUNKS = 7, BC_NEXT_SC = 8, BC_N = 16 };
+       BC_CHUNKS = 7, BC_NEXT_SC = 8 /* .. 11: one per diag launch */, BC_N = 16 };
 
 // Device descriptor of one fused query.
 struct BQuery {
@@ -48,7 +48,7 @@ struct BQuery {
     int64_t walk_base;  // TC: first padded global walk id (device-filled)
     int64_t walk_end;   // TC: walk_base + walks of the query (device-filled)
     int64_t gw_base;    // exclusive prefix of N_i at node_off (device-filled)
-    int64_t rm_off;     // TC: offset of the degree table
+    int64_t rm_off;     // offset of the degree table
     int64_t blk_off;    // first 32-entry output block
     int64_t n_out;      // outputs: n, or the size of the SC subset
     const int64_t* rp;
@@ -57,6 +57,7 @@ struct BQuery {
     const int32_t* ri;
     const uint2* nod;
     const uint2* eod;
+    const uint32_t* ekey;  // SC: row offset of each entry's neighbour (keys of the rows Q_k)
     const double* diag;
     const int64_t* nodes;  // SC subset (device) or null
     const int64_t* sub_ptr;   // SC subset: per-column lists of the requested rows (SubList)
@@ -71,7 +72,6 @@ struct BQuery {
     float wc32;
     int32_t K;
     int32_t kind;   // 0: TC/Katz, 1: SC
-    int32_t dense;  // SC: dense row Q_k
     int32_t subset; // SC: only the requested nodes
 };
 
@@ -192,30 +192,12 @@ __global__ void bq_chunks(const uint32_t* __restrict__ starts, const int64_t* __
 }
 
 // rm_q[d] = float(gamma_q * d): r_l and the weight multiplier of a state of degree d.
-__global__ void bq_degree_tables(const BQuery* __restrict__ desc, const int64_t* __restrict__ rmoff, int Q_tc,
+__global__ void bq_degree_tables(const BQuery* __restrict__ desc, const int64_t* __restrict__ rmoff, int Q,
                                  int64_t total, float* __restrict__ rm) {
     MCF_KERNEL_ENTRY();
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-        const int q = find_le(rmoff, Q_tc, t);
+        const int q = find_le(rmoff, Q, t);
         rm[t] = __double2float_rn(__dmul_rn(desc[q].gamma, (double)(t - rmoff[q])));
-    }
-}
-
-// Node records of the SC queries' nodes (float32 multiplier gamma * deg).
-__global__ void bq_records(const BQuery* __restrict__ desc, const int64_t* __restrict__ qoff, int Q, int64_t u0,
-                           int64_t NT, Rec<false>* __restrict__ rec) {
-    MCF_KERNEL_ENTRY();
-    for (int64_t u = u0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < NT; u += (int64_t)gridDim.x * blockDim.x) {
-        const int q = find_le(qoff, Q, u);
-        const BQuery& d = desc[q];
-        const int64_t i = u - d.node_off;
-        const int64_t b = d.rp[i], deg = d.rp[i + 1] - b;
-        Rec<false> x;
-        x.off = (uint32_t)b;
-        x.deg = (uint32_t)deg;
-        x.r = 0.f;
-        x.mult = __double2float_rn(__dmul_rn(d.gamma, (double)deg));
-        rec[u - u0] = x;
     }
 }
 
@@ -402,133 +384,199 @@ __global__ void __launch_bounds__(256, MINB) bwalk_tc_kernel(
 }
 
 // ---------------------------------------------------------------- SC walks
-// walk_diag_kernel over the start columns of all SC queries: a CTA takes one
-// start at a time and reads its query's parameters; row Q_k is dense for
-// graphs up to B_DENSE_MAX nodes and hashed otherwise.
-struct CtaQuery {
+// walk_diag_od_kernel over the start columns of the SC queries [q_lo, q_hi)
+// (one launch per row-table size; cls picks the launch's start counter): a
+// CTA takes one start at a time, reads its query's parameters into shared
+// memory when the query changes and runs the start's walks with per-lane
+// refill, recording visits in a row Q_k keyed by row offset (one random
+// 8-byte record per step), then the dot phase over the requested rows and
+// the clear.  Every SC query of a batch is on a symmetric binary graph.
+struct CtaOdQuery {
+    int64_t node_off;
     const int64_t* rp;
     const int32_t* col;
-    const int64_t* cp;
-    const int32_t* ri;
+    const uint2* nod;
+    const uint2* eod;
+    const uint32_t* ekey;
+    const float* rm;
     SubList sub;
-    const Rec<false>* rec;
     double* dacc;
-    int64_t n;
     double gamma;
     uint2 key;
     uint32_t req;
     float wc32;
     int32_t K;
-    int32_t dense;
     float zeta[MCF_MAX_COEFFS];
 };
 
-template <bool DENSE>
-__device__ void bdiag_start(const CtaQuery& cq, DiagTable& t, uint32_t k0, int64_t Nk, int64_t g0, uint32_t& steps,
-                            uint32_t& walks, uint32_t& flags) {
-    if (threadIdx.x == 0 && 1.0f > cq.wc32 && cq.K >= 2) {
-        const int h = q_slot<DENSE>(t, k0);
-        atomicAdd(&t.val[h], (double)Nk * (double)cq.zeta[2]);
-    }
-    __syncthreads();
-    int64_t w = threadIdx.x;
-    int from = 1, cfrom = 0;
-    walks += (uint32_t)(Nk > (int64_t)threadIdx.x ? (Nk - 1 - threadIdx.x) / blockDim.x + 1 : 0);
-    for (;;) {
-        bool stopped = false;
-        while (w < Nk) {
-            const int f = diag_walk<false, false, DENSE>(t, k0, g0 + w, from, cfrom, cq.rec, cq.col, nullptr, cq.zeta, cq.K,
-                                                         0.0, cq.wc32, cq.key, cq.req, steps, flags);
-            if (f >= 0) {
-                from = f;
-                cfrom = f;
-                stopped = true;
-                break;
-            }
-            w += blockDim.x;
-            from = 1;
-            cfrom = 0;
-        }
-        if (!__syncthreads_or(stopped)) break;
-        __threadfence_block();
-        diag_apply<DENSE>(t, k0, Nk, cq.cp, cq.ri, nullptr, cq.sub, cq.gamma, cq.dacc);
-        __syncthreads();
-        diag_clear<DENSE>(t, cq.n);
-        __syncthreads();
-        if (threadIdx.x == 0) *t.count = 0;
-        __syncthreads();
-    }
-    __threadfence_block();
-    diag_apply<DENSE>(t, k0, Nk, cq.cp, cq.ri, nullptr, cq.sub, cq.gamma, cq.dacc);
-    __syncthreads();
-    diag_clear<DENSE>(t, cq.n);
-    __syncthreads();
-    if (threadIdx.x == 0) *t.count = 0;
-}
-
 __global__ void __launch_bounds__(256) bwalk_diag_kernel(
     const BQuery* __restrict__ desc, const int64_t* __restrict__ qoff, int Q, const uint32_t* __restrict__ starts,
-    const int64_t* __restrict__ soff, const int64_t* __restrict__ nw, const Rec<false>* __restrict__ rec_sc,
-    int64_t sc_node0, int cap_log2, int64_t region, double* __restrict__ qval,
-    double* __restrict__ dacc, unsigned long long* __restrict__ counters) {
+    const int64_t* __restrict__ soff, const int64_t* __restrict__ nw, const float* __restrict__ rm_all,
+    const int64_t* __restrict__ rmoff, int q_lo, int q_hi, int cls, int cap_log2, double* __restrict__ qval,
+    double* __restrict__ acc, unsigned long long* __restrict__ counters) {
     MCF_KERNEL_ENTRY();
-    extern __shared__ int32_t smem_i[];
-    __shared__ CtaQuery cq;
-    __shared__ int64_t cur;
+    extern __shared__ uint32_t od_keys[];
+    __shared__ CtaOdQuery cq;
+    __shared__ int64_t cur, cq_lo, cq_hi, s_lo, s_hi;
     __shared__ int count;
-    const int64_t cap = (int64_t)1 << cap_log2;
-    double* val = qval + (int64_t)blockIdx.x * region;
-    for (int64_t i = threadIdx.x; i < region; i += blockDim.x) __stcg(val + i, 0.0);
-    for (int64_t i = threadIdx.x; i < cap; i += blockDim.x) smem_i[i] = -1;
+    __shared__ unsigned long long next_walk;
+    OdTable t;
+    const int cap = 1 << cap_log2;
+    t.key = od_keys;
+    t.val = qval + (int64_t)blockIdx.x * cap;
+    t.cap_log2 = cap_log2;
+    t.limit = cap - cap / 4 - (int)blockDim.x;
+    t.count = &count;
+    for (int h = threadIdx.x; h < cap; h += blockDim.x) {
+        od_keys[h] = OD_EMPTY;
+        __stcg(t.val + h, 0.0);
+    }
     if (threadIdx.x == 0) count = 0;
-    const int64_t S_tc = (int64_t)counters[BC_STARTS_TC];
-    const int64_t S = (int64_t)counters[BC_STARTS];
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
     uint32_t steps = 0, walks = 0, flags = 0;
+    // Takes the next start (thread 0): its query's parameters are loaded into
+    // shared memory only when the query changes (consecutive starts of a CTA
+    // mostly belong to one query).
+    auto next_start = [&]() {
+        cur = s_lo + (int64_t)atomicAdd(&counters[BC_NEXT_SC + cls], 1ull);
+        next_walk = 0ull;
+        if (cur >= s_hi) return;
+        const int64_t ug = (int64_t)starts[cur];
+        if (ug >= cq_lo && ug < cq_hi) return;
+        const int q = find_le(qoff, Q, ug);
+        const BQuery& d = desc[q];
+        cq.rp = d.rp;
+        cq.col = d.col;
+        cq.nod = d.nod;
+        cq.eod = d.eod;
+        cq.ekey = d.ekey;
+        cq.rm = rm_all + rmoff[q];
+        cq.sub = SubList{d.subset ? d.sub_ptr : nullptr, d.sub_row, nullptr};
+        cq.dacc = acc + d.node_off;
+        cq.node_off = d.node_off;
+        cq.gamma = d.gamma;
+        cq.key = d.key;
+        cq.req = d.req;
+        cq.wc32 = d.wc32;
+        cq.K = d.K;
+        for (int k = 0; k <= d.K; ++k) cq.zeta[k] = (float)d.zeta[k];
+        cq_lo = qoff[q];
+        cq_hi = qoff[q + 1];
+    };
+    if (threadIdx.x == 0) {
+        // the starts of queries [q_lo, q_hi): starts[] holds the global
+        // indices of all start columns in increasing order
+        const int64_t S_tc = (int64_t)counters[BC_STARTS_TC];
+        const int64_t S = (int64_t)counters[BC_STARTS];
+        auto first_at = [&](int64_t node) {
+            int64_t lo = S_tc, hi = S;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if ((int64_t)starts[mid] < node) lo = mid + 1;
+                else hi = mid;
+            }
+            return lo;
+        };
+        s_lo = first_at(qoff[q_lo]);
+        s_hi = first_at(qoff[q_hi]);
+        cq_lo = cq_hi = -1;
+        next_start();
+    }
     __syncthreads();
     for (;;) {
-        if (threadIdx.x == 0) cur = S_tc + (int64_t)atomicAdd(&counters[BC_NEXT_SC], 1ull);
-        __syncthreads();
         const int64_t s = cur;
-        if (s >= S) break;
+        if (s >= s_hi) break;
         const uint32_t ug = starts[s];
-        const int q = find_le(qoff, Q, (int64_t)ug);
-        const BQuery& d = desc[q];
-        if (threadIdx.x == 0) {
-            cq.rp = d.rp;
-            cq.col = d.col;
-            cq.cp = d.cp;
-            cq.ri = d.ri;
-            cq.sub = SubList{d.subset ? d.sub_ptr : nullptr, d.sub_row, nullptr};
-            cq.rec = rec_sc + (d.node_off - sc_node0);
-            cq.dacc = dacc + d.node_off;
-            cq.n = d.n;
-            cq.gamma = d.gamma;
-            cq.key = d.key;
-            cq.req = d.req;
-            cq.wc32 = d.wc32;
-            cq.K = d.K;
-            cq.dense = d.dense;
+        const uint32_t k0 = (uint32_t)(ug - cq.node_off);
+        const int64_t Nk = nw[ug];
+        const int64_t g0 = soff[s];
+        const uint2 od0 = cq.nod[k0];
+        const int K = cq.K;
+        const float wc32 = cq.wc32;
+        if (threadIdx.x == 0 && 1.0f > wc32 && K >= 2) {
+            // the N_k step-0 visits, into the cleared table while the walks begin
+            const int h = od_insert_always(t, od0.x);
+            atomicAdd(&t.val[h], (double)Nk * (double)cq.zeta[2]);
         }
-        for (int t = threadIdx.x; t <= d.K; t += blockDim.x) cq.zeta[t] = (float)d.zeta[t];
-        __syncthreads();
-        const uint32_t k0 = (uint32_t)(ug - d.node_off);
-        DiagTable t;
-        t.val = val;
-        t.key = smem_i;
-        t.used = smem_i + cap;
-        t.cap_log2 = cap_log2;
-        t.limit = (int)(cap - cap / 4 - (int64_t)blockDim.x);
-        t.count = &count;
-        if (cq.dense) bdiag_start<true>(cq, t, k0, nw[ug], soff[s], steps, walks, flags);
-        else bdiag_start<false>(cq, t, k0, nw[ug], soff[s], steps, walks, flags);
+        bool active = false, paused = false, exhausted = false;
+        int64_t g = 0;
+        uint32_t off = 0, deg = 0;
+        int k = 0;
+        float W = 1.f;
+        uint4 u = make_uint4(0u, 0u, 0u, 0u);
+        for (;;) {
+            for (;;) {
+                const unsigned idle = __ballot_sync(FULL, !active);
+                if (idle && !exhausted) {
+                    unsigned long long base = 0;
+                    if (lane == __ffs(idle) - 1) base = atomicAdd(&next_walk, (unsigned long long)__popc(idle));
+                    base = __shfl_sync(FULL, base, __ffs(idle) - 1);
+                    if (base + __popc(idle) >= (unsigned long long)Nk) exhausted = true;
+                    if (!active) {
+                        const int64_t w = (int64_t)base + __popc(idle & lt_mask);
+                        if (w < Nk) {
+                            g = g0 + w;
+                            off = od0.x;
+                            deg = od0.y;
+                            k = 0;
+                            W = 1.f;
+                            active = true;
+                        }
+                    }
+                }
+                const bool run = active && !paused;
+                if (!__any_sync(FULL, run)) break;
+                if (run) {
+                    bool done = !(fabsf(W) > wc32);
+                    if (!done && k >= 1) {
+                        const int h = od_insert(t, off);
+                        if (h < 0) paused = true;
+                        else atomicAdd(&t.val[h], (double)__fmul_rn(cq.zeta[k + 2], W));
+                    }
+                    if (!done && !paused) {
+                        if (k + 2 >= K || deg == 0) {
+                            done = true;
+                        } else {
+                            uint32_t w0, w1;
+                            walk_words<false>(u, k, (uint32_t)g, (uint32_t)((uint64_t)g >> 32), cq.req, cq.key, w0,
+                                              w1);
+                            const uint2 nx = load_od(cq.eod + (int64_t)off + __umulhi(w0, deg), policy_evict_first());
+                            W = __fmul_rn(W, __ldg(cq.rm + deg));
+                            off = nx.x;
+                            deg = nx.y;
+                            ++k;
+                            ++steps;
+                        }
+                    }
+                    if (done) {
+                        if (!isfinite(W)) flags |= 1u;
+                        ++walks;
+                        active = false;
+                    }
+                }
+            }
+            const bool any_paused = __syncthreads_or(paused);
+            __threadfence_block();
+            od_apply(t, k0, Nk, cq.rp, cq.col, cq.ekey, cq.sub, cq.gamma, cq.dacc);
+            __syncthreads();
+            od_clear(t);
+            if (threadIdx.x == 0) {
+                count = 0;
+                if (!any_paused) next_start();   // the start is done
+            }
+            __syncthreads();
+            if (!any_paused) break;
+            paused = false;   // the table is empty again: the paused walks go on
+        }
     }
-    const int lane = threadIdx.x & 31;
     unsigned long long ws = steps, ww = walks;
 #pragma unroll
-    for (int d = 16; d > 0; d >>= 1) {
-        ws += __shfl_down_sync(0xffffffffu, ws, d);
-        ww += __shfl_down_sync(0xffffffffu, ww, d);
-        flags |= __shfl_down_sync(0xffffffffu, flags, d);
+    for (int dd = 16; dd > 0; dd >>= 1) {
+        ws += __shfl_down_sync(FULL, ws, dd);
+        ww += __shfl_down_sync(FULL, ww, dd);
+        flags |= __shfl_down_sync(FULL, flags, dd);
     }
     if (lane == 0) {
         atomicAdd(&counters[BC_STEPS], ws);
@@ -601,6 +649,19 @@ struct BatchTuning {
 static std::mutex g_tune_mu;
 static std::map<std::string, BatchTuning> g_tune_cache;
 
+constexpr int B_DIAG_CAP_LOG2 = 13;   // largest row table of the fused diag kernel
+struct DiagShape {
+    int cap_log2 = 10;
+    int threads = 256;
+    size_t smem = 0;
+    int grid = 0;
+};
+static_assert(BC_NEXT_SC + (B_DIAG_CAP_LOG2 - 10) < BC_N, "a start counter per diag launch");
+struct DiagClass {   // SC queries [q_lo, q_hi) of the fused list, one diag launch
+    int q_lo = 0, q_hi = 0;
+    DiagShape sh;
+};
+
 struct mcf_batch {
     std::vector<mcf_query> queries;
     std::vector<int> fused;       // query indices: TC/Katz first, then SC
@@ -609,11 +670,8 @@ struct mcf_batch {
     std::vector<mcf_params> params;            // per query, with owned coefficients
     int Q = 0, Q_tc = 0;
     int64_t NT = 0, NT_tc = 0, rm_total = 0, n_blocks = 0, max_chunks = 0, sc_nodes = 0;
-    int cap_log2 = 10;
-    int64_t region = 0;
-    int diag_grid = 0, diag_threads = 256;
+    std::vector<DiagClass> diag;   // SC queries grouped by row-table size (2^10 .. 2^13: at most 4)
     int tc_grid[4] = {0, 0, 0, 0};   // persistent grids of the walk kernel for 5, 6, 8 and 4 blocks per SM
-    size_t diag_smem = 0;
     BatchTuning tune;
     std::vector<void*> bufs;
     // device arrays
@@ -625,7 +683,6 @@ struct mcf_batch {
     int64_t *nw = nullptr, *flag = nullptr, *gw = nullptr, *spos = nullptr, *soff = nullptr;
     uint32_t *starts = nullptr, *chunk_s0 = nullptr;
     float* rm = nullptr;
-    Rec<false>* rec_sc = nullptr;
     uint8_t* need = nullptr;
     unsigned long long* counters = nullptr;
     void* scan_tmp = nullptr;
@@ -650,6 +707,7 @@ template <class T>
 static mcf_status balloc(mcf_batch* b, T** p, size_t count) {
     void* q = nullptr;
     keep_pool_memory();
+    if (injected_allocation_failure()) return fail(MCF_ERR_OOM, "device allocation for the batch failed (injected)");
     if (cudaMallocAsync(&q, std::max<size_t>(count, 1) * sizeof(T), b->stream) != cudaSuccess) {
         cudaGetLastError();
         return fail(MCF_ERR_OOM, "device allocation for the batch failed");
@@ -660,29 +718,28 @@ static mcf_status balloc(mcf_batch* b, T** p, size_t count) {
     return MCF_OK;
 }
 
-// Launch shape of the fused diag kernel: threads per CTA follow the walks
-// per start, the hashed row holds about 16 visits per walk (2^10 .. 2^12
-// slots), and the per-CTA region of Q_k values spans the largest dense row
-// (graphs up to B_DENSE_MAX nodes) or the hash.
-struct DiagShape {
-    int cap_log2 = 10;
-    int threads = 256;
-    size_t smem = 0;
-    int64_t region = 0;
-    int grid = 0;
-};
+// Table size of the fused diag kernel for starts of about nk walks, as the
+// single-query kernel sizes it: about 16 visits per walk, 2^10 .. 2^13 slots
+// (4 bytes each in shared memory), each CTA with a region of as many float64
+// values in global memory.  Threads per CTA follow from it (64 for 2^10, 128
+// for 2^11, 256 above): a CTA serves one start at a time, so lanes beyond its
+// walks idle.  SC queries of a batch are grouped by this size, one launch per
+// group, so that a query with long starts does not shrink every CTA's
+// occupancy to its table.
+static int diag_cap_log2(int64_t nk) {
+    const int threads = nk <= 64 ? 64 : (nk <= 128 ? 128 : 256);
+    const int64_t want_slots = std::max<int64_t>(16 * nk, 4 * threads);
+    int c = 10;
+    while (c < B_DIAG_CAP_LOG2 && ((int64_t)1 << c) < want_slots) ++c;
+    return c;
+}
 
-static mcf_status diag_shape(int64_t nk_hint, bool any_hash, int64_t dense_max, DiagShape* sh) {
-    sh->cap_log2 = 10;
-    if (any_hash) {
-        const int64_t want_slots = std::max<int64_t>(16 * nk_hint, 1024);
-        while (sh->cap_log2 < 12 && ((int64_t)1 << sh->cap_log2) < want_slots) ++sh->cap_log2;
-    }
-    sh->region = std::max<int64_t>(dense_max, (int64_t)1 << sh->cap_log2);
-    sh->smem = ((size_t)1 << sh->cap_log2) * 2 * sizeof(int32_t);
-    sh->threads = nk_hint <= 64 ? 64 : (nk_hint <= 128 ? 128 : 256);
-    if (cudaFuncSetAttribute(bwalk_diag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh->smem) !=
-        cudaSuccess) {
+static mcf_status diag_shape(int64_t nk, DiagShape* sh) {
+    sh->cap_log2 = diag_cap_log2(nk);
+    sh->threads = sh->cap_log2 == 10 ? 64 : (sh->cap_log2 == 11 ? 128 : 256);
+    sh->smem = ((size_t)1 << sh->cap_log2) * sizeof(uint32_t);
+    if (cudaFuncSetAttribute(bwalk_diag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(((size_t)1 << B_DIAG_CAP_LOG2) * sizeof(uint32_t))) != cudaSuccess) {
         cudaGetLastError();
         return fail(MCF_ERR_CUDA, "diag kernel shared memory");
     }
@@ -717,15 +774,16 @@ static int64_t query_footprint(const mcf_query& q, int64_t* out) {
                                                      + (!is_device_ptr(q.nodes) ? 8 * m : 0)
                                                : 0;
     int64_t b = 16 + 4096;   // stamps, descriptor and offsets
-    const bool plain = p.target_rel_err == 0.0;
-    if (plain && ((tc_kind && binary32 && tc_walks < B_FUSED_MAX_WALKS) || (sc_kind && binary32))) {
+    const bool plain = p.target_rel_err == 0.0 && p.deterministic == 0;
+    if (plain && ((tc_kind && binary32 && tc_walks < B_FUSED_MAX_WALKS) || (sc_kind && binary32 && g->symmetric))) {
         b += 60 * n + 8 + 8 * B_RED_BLOCKS + 8 + BC_N * 8 + 12 * MCF_MAX_COEFFS + (int64_t)scan_tmp_bytes(n);
+        b += 4 * (md + 1) + 4;   // degree table
         if (tc_kind) {
-            b += 4 * (walks / B_CHUNK + 3) + 4 * (md + 1) + 4;
+            b += 4 * (walks / B_CHUNK + 3);
         } else {
             DiagShape sh;
-            if (diag_shape(sc_walk_hint(p, n), n > B_DENSE_MAX, n <= B_DENSE_MAX ? n : 0, &sh) != MCF_OK) return -1;
-            b += 17 * n + 8 + (int64_t)sh.grid * sh.region * 8 + lists;
+            if (diag_shape(sc_walk_hint(p, n), &sh) != MCF_OK) return -1;
+            b += 1 * n + 8 + (int64_t)sh.grid * ((int64_t)1 << sh.cap_log2) * 8 + lists;
         }
         if (host_out) b += 8 * m;
     } else {
@@ -736,7 +794,8 @@ static int64_t query_footprint(const mcf_query& q, int64_t* out) {
         // 4864 CTAs x 16384 float64 values)
         b += 200 * n + 4 * (walks / 32 + 3) + 4 * (md + 1) + (int64_t)scan_tmp_bytes(n) + 8 * MCF_MAX_COEFFS;
         if (sc_kind) b += 9 * n + lists + (int64_t)4864 * 16384 * 8;
-        if (!plain) b += 32 * m + 16;   // replica output, two half sums, the mean
+        if (p.target_rel_err != 0.0) b += 32 * m + 16;   // replica output, two half sums, the mean
+        if (p.deterministic) b += 8 * walks;               // one float64 slot per walk
     }
     *out = b;
     return b;
@@ -760,7 +819,7 @@ static mcf_status check_query(const mcf_query& q, int idx) {
         return fail(MCF_ERR_INVALID_ARG, where + "target_rel_err must be finite and >= 0, max_walks >= 0");
     if (p.precision != MCF_F64 && p.precision != MCF_F32W_F64ACC)
         return fail(MCF_ERR_INVALID_ARG, where + "unknown precision");
-    if (p.deterministic != 0) return fail(MCF_ERR_INVALID_ARG, where + "deterministic is reserved and must be 0");
+    if (p.deterministic != 0 && p.deterministic != 1) return fail(MCF_ERR_INVALID_ARG, where + "deterministic is 0 or 1");
     if (q.kind == MCF_QUERY_ACTION && !q.v) return fail(MCF_ERR_INVALID_ARG, where + "v is NULL");
     if (q.kind == MCF_QUERY_SUBGRAPH_CENTRALITY && q.nodes && q.n_nodes < 0)
         return fail(MCF_ERR_INVALID_ARG, where + "n_nodes must be >= 0");
@@ -789,9 +848,9 @@ static mcf_status record(mcf_batch* b, cudaStream_t st) {
     bq_compact<<<grid_for(b->NT, 256), 256, 0, st>>>(b->desc, b->qoff, Q, b->Q_tc, b->NT, b->flag, b->spos, b->gw,
                                                      b->starts, b->soff);
     MCF_CUDA_TRY(cudaGetLastError());
+    bq_degree_tables<<<grid_for(b->rm_total, 256), 256, 0, st>>>(b->desc, b->rmoff, Q, b->rm_total, b->rm);
     if (b->Q_tc > 0) {
         bq_chunks<<<grid_for(b->NT_tc, 256), 256, 0, st>>>(b->starts, b->soff, b->nw, b->counters, b->chunk_s0);
-        bq_degree_tables<<<grid_for(b->rm_total, 256), 256, 0, st>>>(b->desc, b->rmoff, b->Q_tc, b->rm_total, b->rm);
         auto launch = [&](auto kern, int grid) {
             kern<<<grid, 256, 0, st>>>(b->desc, b->Q_tc, b->rm, b->rmoff, b->starts, b->soff, b->chunk_s0, b->wbase,
                                        b->tune.grab, b->acc, b->counters);
@@ -804,11 +863,13 @@ static mcf_status record(mcf_batch* b, cudaStream_t st) {
         bq_finalize<<<grid_for(b->NT_tc, 256), 256, 0, st>>>(b->NT_tc, b->acc, b->nw);
     }
     if (Q > b->Q_tc) {
-        bq_records<<<grid_for(b->sc_nodes, 256), 256, 0, st>>>(b->desc, b->qoff, Q, b->NT_tc, b->NT, b->rec_sc);
-        bwalk_diag_kernel<<<b->diag_grid, b->diag_threads, b->diag_smem, st>>>(
-            b->desc, b->qoff, Q, b->starts, b->soff, b->nw, b->rec_sc, b->NT_tc, b->cap_log2, b->region,
-            b->qval, b->acc, b->counters);
-        MCF_CUDA_TRY(cudaGetLastError());
+        for (size_t c = 0; c < b->diag.size(); ++c) {
+            const DiagClass& dc = b->diag[c];
+            bwalk_diag_kernel<<<dc.sh.grid, dc.sh.threads, dc.sh.smem, st>>>(
+                b->desc, b->qoff, Q, b->starts, b->soff, b->nw, b->rm, b->rmoff, dc.q_lo, dc.q_hi, (int)c,
+                dc.sh.cap_log2, b->qval, b->acc, b->counters);
+            MCF_CUDA_TRY(cudaGetLastError());
+        }
     }
     bq_epilogue<<<grid_for(b->n_blocks * 32, 256), 256, 0, st>>>(b->desc, b->boff, Q, b->n_blocks, b->acc);
     MCF_CUDA_TRY(cudaGetLastError());
@@ -985,32 +1046,37 @@ mcf_status mcf_batch_create(const mcf_query* queries, int32_t n_queries, uint32_
         b->params[i] = p;
         const bool binary32 = !q.graph->weighted && p.precision == MCF_F32W_F64ACC && q.graph->nnz < ((int64_t)1 << 32);
         const int64_t tc_walks = p.walks_per_node > 0 ? p.walks_per_node * q.graph->n : p.n_walks;
-        const bool plain = p.target_rel_err == 0.0;   // accuracy-targeted queries run as replicas (single path)
+        // accuracy-targeted queries run as replicas, deterministic ones with per-walk
+        // slots: both through the single-query path
+        const bool plain = p.target_rel_err == 0.0 && p.deterministic == 0;
         if ((q.kind == MCF_QUERY_TOTAL_COMMUNICABILITY || q.kind == MCF_QUERY_KATZ) && binary32 && p.n_coeffs >= 3 &&
             tc_walks < B_FUSED_MAX_WALKS && plain)
             tc.push_back(i);
-        else if (q.kind == MCF_QUERY_SUBGRAPH_CENTRALITY && binary32 && p.n_coeffs >= 3 && plain)
+        else if (q.kind == MCF_QUERY_SUBGRAPH_CENTRALITY && binary32 && q.graph->symmetric && p.n_coeffs >= 3 && plain)
             sc.push_back(i);
         else
             b->single.push_back(i);
     }
     b->fused = tc;
+    // SC queries grouped by row-table size (one diag launch per group)
+    auto sc_cap = [&](int i) { return diag_cap_log2(sc_walk_hint(b->params[i], b->queries[i].graph->n)); };
+    std::stable_sort(sc.begin(), sc.end(), [&](int x, int y) { return sc_cap(x) < sc_cap(y); });
     b->fused.insert(b->fused.end(), sc.begin(), sc.end());
     b->Q = (int)b->fused.size();
     b->Q_tc = (int)tc.size();
     if (b->Q > 0) {
         // ---- host-side layout
         std::vector<BQuery> d(b->Q);
-        std::vector<int64_t> qoff(b->Q + 1), rmoff(b->Q_tc + 1), boff(b->Q + 1);
-        int64_t node = 0, rmt = 0, blocks = 0, max_chunks = 0, nk_hint = 1, dense_max = 0;
-        bool any_hash = false;
+        std::vector<int64_t> qoff(b->Q + 1), rmoff(b->Q + 1), boff(b->Q + 1);
+        int64_t node = 0, rmt = 0, blocks = 0, max_chunks = 0;
         for (int f = 0; f < b->Q; ++f) {
             const int i = b->fused[f];
             const mcf_query& q = b->queries[i];
             const mcf_params& p = b->params[i];
             mcf_graph* g = q.graph;
-            if (f < b->Q_tc) {
+            {
                 mcf_status rc = ensure_edge_od(g, st);
+                if (rc == MCF_OK && f >= b->Q_tc) rc = ensure_edge_key(g, st);
                 if (rc != MCF_OK) return bail(rc);
             }
             BQuery& x = d[f];
@@ -1023,6 +1089,7 @@ mcf_status mcf_batch_create(const mcf_query* queries, int32_t n_queries, uint32_
             x.ri = g->row_idx;
             x.nod = g->node_od;
             x.eod = g->edge_od;
+            x.ekey = g->edge_key;
             x.diag = g->diag;
             x.gamma = p.scale == 0.0 ? 1.0 : p.scale;
             x.K = p.n_coeffs - 1;
@@ -1037,28 +1104,23 @@ mcf_status mcf_batch_create(const mcf_query* queries, int32_t n_queries, uint32_
             x.kind = f < b->Q_tc ? 0 : 1;
             x.subset = (x.kind == 1 && q.nodes) ? 1 : 0;
             x.n_out = x.subset ? q.n_nodes : g->n;
-            x.dense = g->n <= B_DENSE_MAX;
             qoff[f] = node;
             boff[f] = blocks;
             x.blk_off = blocks;
             blocks += (x.n_out + 31) / 32;
             node += g->n;
+            rmoff[f] = rmt;
+            x.rm_off = rmt;
+            rmt += g->max_degree + 1;
             if (f < b->Q_tc) {
-                rmoff[f] = rmt;
-                x.rm_off = rmt;
-                rmt += g->max_degree + 1;
                 const int64_t mw = p.walks_per_node > 0 ? p.walks_per_node * g->n : p.n_walks + g->n;
                 max_chunks += mw / B_CHUNK + 2;
-            } else {
-                nk_hint = std::max(nk_hint, sc_walk_hint(p, g->n));
-                if (x.dense) dense_max = std::max(dense_max, g->n);
-                else any_hash = true;
             }
             if (f == b->Q_tc - 1) b->NT_tc = node;
         }
         if (b->Q_tc == 0) b->NT_tc = 0;
         qoff[b->Q] = node;
-        rmoff[b->Q_tc] = rmt;
+        rmoff[b->Q] = rmt;
         boff[b->Q] = blocks;
         b->NT = node;
         b->rm_total = rmt;
@@ -1066,16 +1128,20 @@ mcf_status mcf_batch_create(const mcf_query* queries, int32_t n_queries, uint32_
         b->max_chunks = max_chunks + 1;
         b->sc_nodes = b->NT - b->NT_tc;
         if (b->NT >= ((int64_t)1 << 32)) return bail(fail(MCF_ERR_INVALID_ARG, "a batch spans at most 2^32 nodes"));
-        // diag launch shape
-        if (b->Q > b->Q_tc) {
-            DiagShape sh;
-            mcf_status rs = diag_shape(nk_hint, any_hash, dense_max, &sh);
+        // diag launch shapes: one per run of SC queries with equal table size
+        b->diag.clear();
+        for (int f = b->Q_tc; f < b->Q;) {
+            const int i = b->fused[f];
+            const int c = diag_cap_log2(sc_walk_hint(b->params[i], b->queries[i].graph->n));
+            DiagClass dc;
+            dc.q_lo = f;
+            while (f < b->Q &&
+                   diag_cap_log2(sc_walk_hint(b->params[b->fused[f]], b->queries[b->fused[f]].graph->n)) == c)
+                ++f;
+            dc.q_hi = f;
+            mcf_status rs = diag_shape(sc_walk_hint(b->params[i], b->queries[i].graph->n), &dc.sh);
             if (rs != MCF_OK) return bail(rs);
-            b->cap_log2 = sh.cap_log2;
-            b->region = sh.region;
-            b->diag_smem = sh.smem;
-            b->diag_threads = sh.threads;
-            b->diag_grid = sh.grid;
+            b->diag.push_back(dc);
         }
         b->tc_grid[0] = persistent_grid(bwalk_tc_kernel<5>, 256, 0);
         b->tc_grid[1] = persistent_grid(bwalk_tc_kernel<6>, 256, 0);
@@ -1088,7 +1154,7 @@ mcf_status mcf_batch_create(const mcf_query* queries, int32_t n_queries, uint32_
         };
         A(&b->desc, b->Q);
         A(&b->qoff, b->Q + 1);
-        A(&b->rmoff, b->Q_tc + 1);
+        A(&b->rmoff, b->Q + 1);
         A(&b->boff, b->Q + 1);
         A(&b->wbase, std::max(b->Q_tc, 1));
         A(&b->colnorm, b->NT);
@@ -1106,11 +1172,14 @@ mcf_status mcf_batch_create(const mcf_query* queries, int32_t n_queries, uint32_
         A(&b->rm, b->rm_total);
         A(&b->zeta, (size_t)b->Q * MCF_MAX_COEFFS);
         A(&b->zf, (size_t)b->Q * MCF_MAX_COEFFS);
-        A(&b->rec_sc, b->sc_nodes);
         A(&b->need, b->sc_nodes);
         b->scan_bytes = scan_tmp_bytes(b->NT);
         A((char**)&b->scan_tmp, b->scan_bytes);
-        if (b->Q > b->Q_tc) A(&b->qval, (size_t)b->diag_grid * (size_t)b->region);
+        if (b->Q > b->Q_tc) {
+            size_t qv = 0;   // the launches run one after another on the stream: one region serves all
+            for (const DiagClass& dc : b->diag) qv = std::max(qv, (size_t)dc.sh.grid << dc.sh.cap_log2);
+            A(&b->qval, qv);
+        }
         if (rc != MCF_OK) return bail(rc);
         // coefficients, subsets and outputs
         for (int f = 0; f < b->Q; ++f) {
@@ -1164,7 +1233,7 @@ mcf_status mcf_batch_create(const mcf_query* queries, int32_t n_queries, uint32_
         }
         if (cudaMemcpyAsync(b->desc, d.data(), b->Q * sizeof(BQuery), cudaMemcpyHostToDevice, st) != cudaSuccess ||
             cudaMemcpyAsync(b->qoff, qoff.data(), (b->Q + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-            cudaMemcpyAsync(b->rmoff, rmoff.data(), (b->Q_tc + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaMemcpyAsync(b->rmoff, rmoff.data(), (b->Q + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st) != cudaSuccess ||
             cudaMemcpyAsync(b->boff, boff.data(), (b->Q + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st) != cudaSuccess)
             return bail(fail(MCF_ERR_CUDA, "descriptor upload failed"));
         if (cudaStreamSynchronize(st) != cudaSuccess) return bail(fail(MCF_ERR_CUDA, "batch setup failed"));

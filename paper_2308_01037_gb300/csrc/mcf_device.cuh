@@ -412,6 +412,106 @@ struct SubList {
 // waits for the stream.
 mcf_status check_nodes_on_device(const int64_t* nodes_dev, int64_t m, int64_t n, cudaStream_t st);
 
+// ---------------------------------------------------------------- RandFunmDiag rows keyed by row offset
+// Row Q_k of a symmetric binary graph keyed by the row offset of the visited
+// node (every visited node has degree >= 1, and such nodes have distinct row
+// offsets): keys in a shared-memory open-addressing table, float64 values in
+// a per-CTA region of global memory updated by L2 reductions.
+constexpr uint32_t OD_EMPTY = 0xffffffffu;
+
+struct OdTable {
+    uint32_t* key;     // shared: row offset of the node in each slot, OD_EMPTY when free
+    double* val;       // global, per CTA
+    int cap_log2;
+    int limit;         // largest number of keys admitted
+    int* count;        // shared
+};
+
+__device__ __forceinline__ int od_insert(const OdTable& t, uint32_t key) {
+    const uint32_t mask = (1u << t.cap_log2) - 1u;
+    uint32_t h = (key * 0x9E3779B1u) >> (32 - t.cap_log2);
+    for (uint32_t probe = 0; probe <= mask; ++probe, h = (h + 1) & mask) {
+        const uint32_t k = t.key[h];
+        if (k == key) return (int)h;
+        if (k == OD_EMPTY) {
+            if (*(volatile int*)t.count >= t.limit) return -1;
+            const uint32_t prev = atomicCAS(&t.key[h], OD_EMPTY, key);
+            if (prev == OD_EMPTY) {
+                atomicAdd(t.count, 1);
+                return (int)h;
+            }
+            if (prev == key) return (int)h;
+        }
+    }
+    return -1;
+}
+
+// Inserts key regardless of the fill limit (the table keeps room for the
+// limit plus one in-flight insertion per thread plus this one): the bulk
+// step-0 visit of a start, made while the other threads may start inserting.
+__device__ __forceinline__ int od_insert_always(const OdTable& t, uint32_t key) {
+    const uint32_t mask = (1u << t.cap_log2) - 1u;
+    uint32_t h = (key * 0x9E3779B1u) >> (32 - t.cap_log2);
+    for (uint32_t probe = 0; probe <= mask; ++probe, h = (h + 1) & mask) {
+        const uint32_t k = t.key[h];
+        if (k == key) return (int)h;
+        if (k == OD_EMPTY) {
+            const uint32_t prev = atomicCAS(&t.key[h], OD_EMPTY, key);
+            if (prev == OD_EMPTY) {
+                atomicAdd(t.count, 1);
+                return (int)h;
+            }
+            if (prev == key) return (int)h;
+        }
+    }
+    return -1;
+}
+
+__device__ __forceinline__ double od_get(const OdTable& t, uint32_t key) {
+    const uint32_t mask = (1u << t.cap_log2) - 1u;
+    uint32_t h = (key * 0x9E3779B1u) >> (32 - t.cap_log2);
+    for (uint32_t probe = 0; probe <= mask; ++probe, h = (h + 1) & mask) {
+        const uint32_t k = t.key[h];
+        if (k == key) return __ldcg(t.val + h);
+        if (k == OD_EMPTY) return 0.0;
+    }
+    return 0.0;
+}
+
+// d_i += a'_ik <Q_k, C'_i> / N_k for the rows i of column k (= row k), or the
+// rows the subset lists for column k; the entries of row i name their
+// neighbours' keys in edge_key (4 bytes per entry).  Warp per row.
+__device__ __forceinline__ void od_apply(const OdTable& t, uint32_t k0, int64_t Nk, const int64_t* __restrict__ rp,
+                                         const int32_t* __restrict__ col, const uint32_t* __restrict__ ekey,
+                                         const SubList& sub, double gamma, double* __restrict__ dacc) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int64_t* lp = sub.ptr ? sub.ptr : rp;
+    const int32_t* lrow = sub.ptr ? sub.row : col;
+    const double scale = (gamma * gamma) / (double)Nk;
+    for (int64_t p = lp[k0] + wid; p < lp[k0 + 1]; p += nwarp) {
+        const int32_t i = lrow[p];
+        double dot = 0.0;
+        for (int64_t q = rp[i] + lane; q < rp[i + 1]; q += 32) {
+            const double qv = od_get(t, __ldg(&ekey[q]));
+            if (__double_as_longlong(qv) != 0) dot += qv;   // exact zeros change no sum
+        }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, d);
+        if (lane == 0) atomicAdd(&dacc[i], dot * scale);
+    }
+}
+
+__device__ __forceinline__ void od_clear(const OdTable& t) {
+    const int cap = 1 << t.cap_log2;
+    for (int h = threadIdx.x; h < cap; h += blockDim.x) {
+        if (t.key[h] != OD_EMPTY) {
+            t.key[h] = OD_EMPTY;
+            __stcg(t.val + h, 0.0);
+        }
+    }
+}
+
+
 // Builds the SubList of the node subset nodes_dev[0..m) (device indices, in
 // range) of graph g on stream st; device memory comes from alloc.  Waits for
 // the stream once (the number of pairs sizes the lists).

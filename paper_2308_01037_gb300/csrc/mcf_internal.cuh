@@ -204,6 +204,10 @@ size_t scan_tmp_bytes(int64_t n);
 // Float64 SpMV y = beta * (A x) (+ alpha * z if z), A the graph's matrix (values or binary).
 mcf_status spmv_f64(const mcf_graph* g, const double* x, double* y, double beta, cudaStream_t st);
 
+// Host-side allocation-failure injection (mcf_inject_allocation_failure):
+// returns true when this device allocation is the one chosen to fail.
+bool injected_allocation_failure();
+
 // Stream-ordered scratch allocation helpers.
 struct Scratch {
     cudaStream_t st;
@@ -218,6 +222,7 @@ struct Scratch {
         if (n >= 48) return fail(MCF_ERR_OOM, "too many scratch buffers");
         size_t bytes = count * sizeof(T);
         if (bytes == 0) bytes = 16;
+        if (injected_allocation_failure()) return fail(MCF_ERR_OOM, "device allocation failed (injected)");
         void* q = nullptr;
         cudaError_t e = cudaMallocAsync(&q, bytes, st);
         if (e != cudaSuccess) {

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 
 #include "mcf_internal.cuh"
@@ -53,6 +54,18 @@ using namespace mcf;
 
 uint64_t mcf::kernel_runs_probe() { return this_unit_kernel_runs(); }
 
+// The allocation counter of mcf_inject_allocation_failure: -1 = off, else the
+// number of scratch allocations that still succeed before one fails.
+static std::atomic<long long> g_fail_after{-1};
+
+bool mcf::injected_allocation_failure() {
+    long long v = g_fail_after.load(std::memory_order_relaxed);
+    while (v >= 0) {
+        if (g_fail_after.compare_exchange_weak(v, v - 1, std::memory_order_relaxed)) return v == 0;
+    }
+    return false;
+}
+
 extern "C" {
 
 mcf_status mcf_gather_probe(int64_t array_bytes, int64_t reads, void* stream, double* reads_per_s) {
@@ -96,6 +109,12 @@ mcf_status mcf_gather_probe(int64_t array_bytes, int64_t reads, void* stream, do
     if (rc != MCF_OK) return rc;
     MCF_CUDA_TRY(cudaStreamSynchronize(st));
     *reads_per_s = (double)grid * threads * iters / (ms * 1e-3);
+    return MCF_OK;
+}
+
+mcf_status mcf_inject_allocation_failure(int64_t after) {
+    set_error("");
+    g_fail_after.store(after < 0 ? -1 : (long long)after);
     return MCF_OK;
 }
 

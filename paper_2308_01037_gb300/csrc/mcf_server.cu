@@ -72,7 +72,7 @@ struct mcf_server {
     std::vector<double> latencies;
     // global-timer windows (ns) of the completed batches' device work
     std::vector<std::pair<uint64_t, uint64_t>> windows;
-    int64_t submitted = 0, completed = 0, rejected = 0, batches = 0, steps = 0;
+    int64_t submitted = 0, completed = 0, rejected = 0, batches = 0, steps = 0, cancelled = 0;
     double plan_s = 0.0, run_s = 0.0;
     // the walk kernels' L2 fetch granularity, held for the server's life so
     // that concurrent batches do not switch the context-wide setting back and forth
@@ -287,6 +287,7 @@ mcf_status mcf_server_get_stats(mcf_server_t s, mcf_server_stats* out) {
     *out = mcf_server_stats{};
     out->submitted = s->submitted;
     out->completed = s->completed;
+    out->cancelled = s->cancelled;
     out->rejected = s->rejected;
     out->batches = s->batches;
     out->walk_steps = s->steps;
@@ -330,6 +331,29 @@ mcf_status mcf_server_get_stats(mcf_server_t s, mcf_server_stats* out) {
     out->max_concurrent_batches = most;
     out->plan_s = s->plan_s;
     out->run_s = s->run_s;
+    return MCF_OK;
+}
+
+mcf_status mcf_server_cancel(mcf_server_t s, uint64_t ticket) {
+    set_error("");
+    if (!s) return fail(MCF_ERR_INVALID_ARG, "server is NULL");
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        auto it = s->all.find(ticket);
+        if (it == s->all.end()) return fail(MCF_ERR_INVALID_ARG, "unknown ticket");
+        Request* r = it->second;
+        if (r->state != 0) return fail(MCF_ERR_INVALID_ARG, "the request is not queued (running or done)");
+        auto q = std::find(s->queue.begin(), s->queue.end(), r);
+        if (q == s->queue.end()) return fail(MCF_ERR_INVALID_ARG, "the request is not queued");
+        s->queue.erase(q);
+        r->state = 2;
+        r->status = MCF_ERR_CANCELLED;
+        r->t_done = Clock::now();
+        ++s->cancelled;
+        ++s->completed;
+    }
+    s->cv_done.notify_all();
+    s->cv_sched.notify_all();
     return MCF_OK;
 }
 

@@ -18,12 +18,6 @@
 
 namespace mcf {
 
-// Launch variants measured against each other (compile-time; the defaults are the measured best).
-#ifndef MCF_TC_ALIGN
-#define MCF_TC_ALIGN 0
-#endif
-constexpr bool TC_ALIGN = MCF_TC_ALIGN != 0;
-
 // r = A' v evaluated as gamma * sum_j (a_ij v_j), the sum in CSR order with
 // every product and sum rounded on its own (thread per row); v == nullptr
 // means v = 1, where a binary row gives gamma * deg exactly.
@@ -163,7 +157,8 @@ __global__ void __launch_bounds__(256, WALK_MINB) walk_action_kernel(
     const int32_t* __restrict__ starts, const int64_t* __restrict__ soff, const int64_t* __restrict__ goff,
     const uint32_t* __restrict__ chunk_s0,
     const double* __restrict__ zeta_g, int K, double wc, float wc32, uint2 key, uint32_t req, int grab,
-    double* __restrict__ acc, double* __restrict__ acc2, unsigned long long* __restrict__ counters) {
+    double* __restrict__ acc, double* __restrict__ acc2, double* __restrict__ wvals,
+    unsigned long long* __restrict__ counters) {
     MCF_KERNEL_ENTRY();
     using real = typename std::conditional<F64, double, float>::type;
     using rtype = typename std::conditional<F64, double, float2>::type;
@@ -186,7 +181,7 @@ __global__ void __launch_bounds__(256, WALK_MINB) walk_action_kernel(
     bool exhausted = false;
     // lane state
     bool active = false;
-    int64_t g = 0;
+    int64_t g = 0, gw = 0;   // walk id, and its index in the walked space
     uint32_t l = 0, node0 = 0;
     int k = 0;
     real W = (real)1;
@@ -231,6 +226,7 @@ __global__ void __launch_bounds__(256, WALK_MINB) walk_action_kernel(
             const int32_t s_new = __shfl_sync(FULL, cs, src);
             if (((idle >> lane) & 1u) && rank < avail) {
                 g = (int64_t)c * WARP_CHUNK + p + rank;
+                gw = g;
                 if (goff != soff) g = goff[s_new] + (g - soff[s_new]);   // node subset: full-run walk id
                 node0 = (uint32_t)starts[s_new];
                 l = node0;
@@ -280,10 +276,14 @@ __global__ void __launch_bounds__(256, WALK_MINB) walk_action_kernel(
                 if constexpr (!F64) if (!isfinite(W) || !isfinite(a32.hi)) flags |= 1u;
                 ++my_walks;
                 active = false;
+                if (wvals) {   // deterministic mode: the walk's value goes to its slot
+                    if constexpr (F64) wvals[gw] = a64;
+                    else wvals[gw] = walk_value(make_float2(a32.hi, a32.lo));
+                }
             }
         }
-        if constexpr (F64) rb_n = rb.push(done, node0, a64, rb_n, lane, lt_mask, acc, acc2);
-        else rb_n = rb.push(done, node0, make_float2(a32.hi, a32.lo), rb_n, lane, lt_mask, acc, acc2);
+        if constexpr (F64) rb_n = rb.push(done && !wvals, node0, a64, rb_n, lane, lt_mask, acc, acc2);
+        else rb_n = rb.push(done && !wvals, node0, make_float2(a32.hi, a32.lo), rb_n, lane, lt_mask, acc, acc2);
     }
     rb.flush(rb_n, lane, acc, acc2);
     unsigned long long ws = my_steps, ww = my_walks;
@@ -337,7 +337,8 @@ __global__ void __launch_bounds__(256, WALK_MINB) walk_tc_kernel(
     const int32_t* __restrict__ starts, const int64_t* __restrict__ soff, const int64_t* __restrict__ goff,
     const uint32_t* __restrict__ chunk_s0,
     const double* __restrict__ zeta_g, int K, float wc32, uint2 key, uint32_t req, int grab, int refill_min,
-    double* __restrict__ acc, double* __restrict__ acc2, unsigned long long* __restrict__ counters) {
+    double* __restrict__ acc, double* __restrict__ acc2, double* __restrict__ wvals,
+    unsigned long long* __restrict__ counters) {
     MCF_KERNEL_ENTRY();
     __shared__ float zeta[MCF_MAX_COEFFS];
     __shared__ WalkResults<float2> rbuf[256 / 32];
@@ -353,26 +354,18 @@ __global__ void __launch_bounds__(256, WALK_MINB) walk_tc_kernel(
     int32_t cs = 0;
     bool exhausted = false;
     bool active = false;
-    int64_t g = 0;
+    int64_t g = 0, gw = 0;   // walk id, and its index in the walked space
     uint32_t node0 = 0, off = 0, deg = 0;
     int k = 0;
     float W = 1.f;
     uint4 u = make_uint4(0u, 0u, 0u, 0u);
     F2Acc a32;
     uint32_t my_steps = 0, my_walks = 0, flags = 0;
-    uint32_t it = 0;
-    for (;; ++it) {
+    for (;;) {
         unsigned idle = __ballot_sync(FULL, !active);
-        if (TC_ALIGN) {
-            // walks start at iterations it = 0 mod 4 only, so a warp's lanes
-            // evaluate their Philox blocks (one per four steps) together
-            if (idle == FULL) it = (it + 3u) & ~3u;
-            if ((it & 3u) != 0u) idle = 0u;
-        } else {
-            // refill once at least refill_min lanes are idle (or all are): fewer
-            // refill passes against a few idle lanes for a step or two
-            if (idle != FULL && __popc(idle) < refill_min) idle = 0u;
-        }
+        // refill once at least refill_min lanes are idle (or all are): fewer
+        // refill passes against a few idle lanes for a step or two
+        if (idle != FULL && __popc(idle) < refill_min) idle = 0u;
         while (idle && !exhausted) {
             if (p >= valid) {
                 ++c;
@@ -407,6 +400,7 @@ __global__ void __launch_bounds__(256, WALK_MINB) walk_tc_kernel(
             const int32_t s_new = __shfl_sync(FULL, cs, src);
             if (((idle >> lane) & 1u) && rank < avail) {
                 g = (int64_t)c * WARP_CHUNK + p + rank;
+                gw = g;
                 if (goff != soff) g = goff[s_new] + (g - soff[s_new]);   // node subset: full-run walk id
                 node0 = (uint32_t)starts[s_new];
                 const uint2 od = nod[node0];
@@ -445,9 +439,10 @@ __global__ void __launch_bounds__(256, WALK_MINB) walk_tc_kernel(
                 if (!isfinite(W) || !isfinite(a32.hi)) flags |= 1u;
                 ++my_walks;
                 active = false;
+                if (wvals) wvals[gw] = walk_value(make_float2(a32.hi, a32.lo));   // deterministic mode
             }
         }
-        rb_n = rb.push(done, node0, make_float2(a32.hi, a32.lo), rb_n, lane, lt_mask, acc, acc2);
+        rb_n = rb.push(done && !wvals, node0, make_float2(a32.hi, a32.lo), rb_n, lane, lt_mask, acc, acc2);
     }
     rb.flush(rb_n, lane, acc, acc2);
     unsigned long long ws = my_steps, ww = my_walks;
@@ -696,7 +691,9 @@ __global__ void __launch_bounds__(256) walk_diag_kernel(
 // move along entries), and nodes of degree >= 1 have distinct row offsets.
 // The keys live in a shared-memory open-addressing table (no slot list: a
 // flush clears by scanning the table), the float64 values in a per-CTA
-// region of global memory updated by L2 reductions.
+// region of global memory updated by L2 reductions.  A start costs three CTA
+// barriers: after its walks, after its dot phase and after the clear (during
+// which the next start is fetched).
 //
 // One CTA serves one start column k at a time.  Its lanes take the N_k walks
 // from a shared counter and each lane starts the next walk as soon as its
@@ -707,82 +704,6 @@ __global__ void __launch_bounds__(256) walk_diag_kernel(
 // Eq. rand_funm_formula_diag, which is linear in Q_k), clears the table and
 // the paused walks go on from where they stopped.  The N_k step-0 visits
 // (weight 1 at k) are added once as N_k * zeta_2.
-constexpr uint32_t OD_EMPTY = 0xffffffffu;
-#ifndef MCF_DIAG_OD_ALIGN
-#define MCF_DIAG_OD_ALIGN 0
-#endif
-constexpr bool DIAG_OD_ALIGN = MCF_DIAG_OD_ALIGN != 0;
-
-struct OdTable {
-    uint32_t* key;     // shared: row offset of the node in each slot, OD_EMPTY when free
-    double* val;       // global, per CTA
-    int cap_log2;
-    int limit;         // largest number of keys admitted
-    int* count;        // shared
-};
-
-__device__ __forceinline__ int od_insert(const OdTable& t, uint32_t key) {
-    const uint32_t mask = (1u << t.cap_log2) - 1u;
-    uint32_t h = (key * 0x9E3779B1u) >> (32 - t.cap_log2);
-    for (uint32_t probe = 0; probe <= mask; ++probe, h = (h + 1) & mask) {
-        const uint32_t k = t.key[h];
-        if (k == key) return (int)h;
-        if (k == OD_EMPTY) {
-            if (*(volatile int*)t.count >= t.limit) return -1;
-            const uint32_t prev = atomicCAS(&t.key[h], OD_EMPTY, key);
-            if (prev == OD_EMPTY) {
-                atomicAdd(t.count, 1);
-                return (int)h;
-            }
-            if (prev == key) return (int)h;
-        }
-    }
-    return -1;
-}
-
-__device__ __forceinline__ double od_get(const OdTable& t, uint32_t key) {
-    const uint32_t mask = (1u << t.cap_log2) - 1u;
-    uint32_t h = (key * 0x9E3779B1u) >> (32 - t.cap_log2);
-    for (uint32_t probe = 0; probe <= mask; ++probe, h = (h + 1) & mask) {
-        const uint32_t k = t.key[h];
-        if (k == key) return __ldcg(t.val + h);
-        if (k == OD_EMPTY) return 0.0;
-    }
-    return 0.0;
-}
-
-// d_i += a'_ik <Q_k, C'_i> / N_k for the rows i of column k (= row k), or the
-// rows the subset lists for column k; the entries of row i name their
-// neighbours' keys in edge_key (4 bytes per entry).  Warp per row.
-__device__ __forceinline__ void od_apply(const OdTable& t, uint32_t k0, int64_t Nk, const int64_t* __restrict__ rp,
-                                         const int32_t* __restrict__ col, const uint32_t* __restrict__ ekey,
-                                         const SubList& sub, double gamma, double* __restrict__ dacc) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    const int64_t* lp = sub.ptr ? sub.ptr : rp;
-    const int32_t* lrow = sub.ptr ? sub.row : col;
-    const double scale = (gamma * gamma) / (double)Nk;
-    for (int64_t p = lp[k0] + wid; p < lp[k0 + 1]; p += nwarp) {
-        const int32_t i = lrow[p];
-        double dot = 0.0;
-        for (int64_t q = rp[i] + lane; q < rp[i + 1]; q += 32) {
-            const double qv = od_get(t, __ldg(&ekey[q]));
-            if (__double_as_longlong(qv) != 0) dot += qv;   // exact zeros change no sum
-        }
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, d);
-        if (lane == 0) atomicAdd(&dacc[i], dot * scale);
-    }
-}
-
-__device__ __forceinline__ void od_clear(const OdTable& t) {
-    const int cap = 1 << t.cap_log2;
-    for (int h = threadIdx.x; h < cap; h += blockDim.x) {
-        if (t.key[h] != OD_EMPTY) {
-            t.key[h] = OD_EMPTY;
-            __stcg(t.val + h, 0.0);
-        }
-    }
-}
 
 __global__ void __launch_bounds__(256) walk_diag_od_kernel(
     const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const uint2* __restrict__ nod,
@@ -816,13 +737,12 @@ __global__ void __launch_bounds__(256) walk_diag_od_kernel(
     const int64_t S = (int64_t)counters[C_STARTS];
     const bool visit0 = 1.0f > wc32;   // the step-0 visit (weight 1 at k), as in the walks
     uint32_t steps = 0, walks = 0, flags = 0;
+    if (threadIdx.x == 0) {
+        cur = (int64_t)atomicAdd(&counters[C_NEXT], 1ull);
+        next_walk = 0ull;
+    }
     __syncthreads();
     for (;;) {
-        if (threadIdx.x == 0) {
-            cur = (int64_t)atomicAdd(&counters[C_NEXT], 1ull);
-            next_walk = 0ull;
-        }
-        __syncthreads();
         const int64_t s = cur;
         if (s >= S) break;
         const uint32_t k0 = (uint32_t)starts[s];
@@ -830,10 +750,10 @@ __global__ void __launch_bounds__(256) walk_diag_od_kernel(
         const int64_t g0 = woff[k0];
         const uint2 od0 = nod[k0];
         if (threadIdx.x == 0 && visit0 && K >= 2) {
-            const int h = od_insert(t, od0.x);     // empty table: always succeeds
+            // the N_k step-0 visits, into the cleared table while the walks begin
+            const int h = od_insert_always(t, od0.x);
             atomicAdd(&t.val[h], (double)Nk * (double)zeta[2]);
         }
-        __syncthreads();
         // lane state
         bool active = false, paused = false, exhausted = false;
         int64_t g = 0;
@@ -841,19 +761,10 @@ __global__ void __launch_bounds__(256) walk_diag_od_kernel(
         int k = 0;
         float W = 1.f;
         uint4 u = make_uint4(0u, 0u, 0u, 0u);
-        // Walks start only at iterations it = 0 mod 4, so the lanes of a warp
-        // stay at the same step modulo 4 and evaluate their Philox blocks
-        // (one per four transitions) together instead of one lane group at a time.
-        uint32_t it = 0;
         for (;;) {
-            for (;; ++it) {
+            for (;;) {
                 // hand the next walks of this start to the idle lanes
-                unsigned idle = __ballot_sync(FULL, !active);
-                if (DIAG_OD_ALIGN) {
-                    if (idle && !exhausted && (it & 3u) != 0u && !__any_sync(FULL, active && !paused))
-                        it = (it + 3u) & ~3u;   // nothing runs until the next start point: go there at once
-                    if ((it & 3u) != 0u) idle = 0u;
-                }
+                const unsigned idle = __ballot_sync(FULL, !active);
                 if (idle && !exhausted) {
                     unsigned long long base = 0;
                     if (lane == __ffs(idle) - 1) base = atomicAdd(&next_walk, (unsigned long long)__popc(idle));
@@ -907,370 +818,16 @@ __global__ void __launch_bounds__(256) walk_diag_od_kernel(
             od_apply(t, k0, Nk, rp, col, ekey, sub, gamma, dacc);
             __syncthreads();
             od_clear(t);
-            if (threadIdx.x == 0) count = 0;
+            if (threadIdx.x == 0) {
+                count = 0;
+                if (!any_paused) {   // the start is done: take the next one
+                    cur = (int64_t)atomicAdd(&counters[C_NEXT], 1ull);
+                    next_walk = 0ull;
+                }
+            }
             __syncthreads();
             if (!any_paused) break;
             paused = false;   // the table is empty again: the paused walks go on
-        }
-    }
-    unsigned long long ws = steps, ww = walks;
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) {
-        ws += __shfl_down_sync(FULL, ws, d);
-        ww += __shfl_down_sync(FULL, ww, d);
-        flags |= __shfl_down_sync(FULL, flags, d);
-    }
-    if (lane == 0) {
-        atomicAdd(&counters[C_STEPS], ws);
-        atomicAdd(&counters[C_WALKS], ww);
-        if (flags) atomicOr(&counters[C_FLAGS], (unsigned long long)flags);
-    }
-}
-
-// ---------------------------------------------------------------- RandFunmDiag, two starts per CTA
-// The walks and visits of walk_diag_od_kernel (same rows Q_k, keys, Philox
-// streams and results), with two start columns in flight per CTA (slots 0
-// and 1, a key table each) and no CTA-wide barrier: a lane whose slot has
-// handed out all its walks takes walks of the other slot, and the dot phase
-// of a finished (or full) slot is shared out row by row to the warps while
-// the other slot's walks go on.
-//
-// Per slot, one 64-bit shared word holds the state (bits 62-63: 0 no more
-// starts, 1 walking, 2 dot phase), the walks paused on a full table (bits
-// 32-61) and the walks handed out and not finished (bits 0-31).  Every change
-// of the counts goes through this word, and the change that leaves every
-// handed-out walk paused (table full) or every walk of the start finished
-// switches the state to the dot phase in the same atomic operation, so
-// exactly one lane triggers each dot phase and no walk starts on a table
-// that is being read or cleared.  The warp that finishes the last row of a
-// dot phase clears the table, then lets the paused walks go on (a new flush
-// generation) or loads the next start column into the slot.  Waiting is
-// bounded: a warp that makes no progress for 2^24 iterations sets flag bit 2
-// and leaves.
-constexpr int OD2_SLOTS = 2;
-constexpr int OD2_ST_DONE = 0, OD2_ST_WALK = 1, OD2_ST_DOT = 2;
-constexpr uint32_t OD2_SPIN_LIMIT = 1u << 24;
-
-constexpr int OD2_ROW_BITS = 40;
-constexpr unsigned long long OD2_ROW_MASK = (1ull << OD2_ROW_BITS) - 1ull;
-
-struct Od2Slot {
-    unsigned long long word;       // state | paused | live
-    unsigned long long next_walk;  // walks handed out (may overshoot N_k)
-    unsigned long long dot_next;   // dot phase number (bits 40-63) | next row of it (bits 0-39)
-    unsigned long long dot_done;   // rows of the current dot phase finished
-    unsigned long long dot_seq;    // number of the current dot phase
-    long long Nk, g0;
-    long long dot_base, dot_rows;  // first row position and number of rows
-    unsigned int k0, off0, deg0;
-    int count;                     // keys in the slot's table
-    int gen;                       // flushes of the current start
-    int posted;                    // the dot phase's fields are valid
-    int final_;                    // the dot phase ends the start (else a flush)
-};
-
-__device__ __forceinline__ int od2_state(unsigned long long w) { return (int)(w >> 62); }
-__device__ __forceinline__ uint32_t od2_paused(unsigned long long w) { return (uint32_t)((w >> 32) & 0x3fffffffu); }
-__device__ __forceinline__ uint32_t od2_live(unsigned long long w) { return (uint32_t)w; }
-__device__ __forceinline__ unsigned long long od2_pack(int st, uint32_t paused, uint32_t live) {
-    return ((unsigned long long)st << 62) | ((unsigned long long)paused << 32) | (unsigned long long)live;
-}
-__device__ __forceinline__ unsigned long long od2_word(Od2Slot& sl) {
-    return *(volatile unsigned long long*)&sl.word;
-}
-
-// A walk of a slot leaves the running set: it paused on a full table, or
-// ended (or a reservation is given back).  Returns 1 when this change starts
-// a flush, 2 when it ends the start, else 0.
-__device__ __forceinline__ int od2_release(Od2Slot& sl, bool pause) {
-    unsigned long long o = od2_word(sl);
-    for (;;) {
-        int st = od2_state(o);
-        uint32_t p = od2_paused(o), l = od2_live(o);
-        if (pause) ++p;
-        else --l;
-        int trig = 0;
-        if (st == OD2_ST_WALK) {
-            if (p > 0 && p == l) trig = 1;
-            else if (!pause && l == 0 && p == 0 &&
-                     *(volatile unsigned long long*)&sl.next_walk >= (unsigned long long)*(volatile long long*)&sl.Nk)
-                trig = 2;
-            if (trig) st = OD2_ST_DOT;
-        }
-        const unsigned long long prev = atomicCAS(&sl.word, o, od2_pack(st, p, l));
-        if (prev == o) return trig;
-        o = prev;
-    }
-}
-
-// Sets the state (walking with no paused walks, or no more starts), keeping
-// the live count: a reservation that is on its way back may be counted in it.
-__device__ __forceinline__ void od2_set_state(Od2Slot& sl, int st) {
-    unsigned long long o = od2_word(sl);
-    for (;;) {
-        const unsigned long long prev = atomicCAS(&sl.word, o, od2_pack(st, 0u, od2_live(o)));
-        if (prev == o) return;
-        o = prev;
-    }
-}
-
-// Publishes the dot phase the calling lane triggered for slot sl.  Its rows
-// are handed out by one counter that also carries the phase's number, so a
-// warp that took a row index of an earlier, finished phase (past its last
-// row) recognises it and never processes a row twice or skips one.
-__device__ __forceinline__ void od2_post(Od2Slot& sl, int trig, const int64_t* __restrict__ rp, const SubList& sub) {
-    const uint32_t k0 = *(volatile unsigned int*)&sl.k0;
-    const int64_t b = sub.ptr ? sub.ptr[k0] : rp[k0];
-    const int64_t e = sub.ptr ? sub.ptr[k0 + 1] : rp[k0 + 1];
-    const unsigned long long seq = *(volatile unsigned long long*)&sl.dot_seq + 1ull;
-    *(volatile int*)&sl.final_ = trig == 2;
-    *(volatile long long*)&sl.dot_base = b;
-    *(volatile long long*)&sl.dot_rows = e - b;
-    *(volatile unsigned long long*)&sl.dot_done = 0ull;
-    *(volatile unsigned long long*)&sl.dot_seq = seq;
-    __threadfence_block();
-    atomicExch(&sl.dot_next, seq << OD2_ROW_BITS);
-    __threadfence_block();
-    *(volatile int*)&sl.posted = 1;
-}
-
-__global__ void __launch_bounds__(256) walk_diag_od2_kernel(
-    const int64_t* __restrict__ rp, const int32_t* __restrict__ col, const uint2* __restrict__ nod,
-    const uint2* __restrict__ eod, const uint32_t* __restrict__ ekey, const float* __restrict__ rm,
-    const int32_t* __restrict__ starts, const int64_t* __restrict__ woff, const int64_t* __restrict__ nw, SubList sub,
-    double gamma, const double* __restrict__ zeta_g, int K, float wc32, uint2 key, uint32_t req, int cap_log2,
-    double* __restrict__ qval, double* __restrict__ dacc, unsigned long long* __restrict__ counters) {
-    MCF_KERNEL_ENTRY();
-    extern __shared__ uint32_t od_keys[];
-    __shared__ float zeta[MCF_MAX_COEFFS];
-    __shared__ Od2Slot slot[OD2_SLOTS];
-    for (int k = threadIdx.x; k <= K; k += blockDim.x) zeta[k] = (float)zeta_g[k];
-    const int cap = 1 << cap_log2;
-    double* const val0 = qval + (int64_t)blockIdx.x * OD2_SLOTS * cap;
-    auto table = [&](int x) {
-        OdTable t;
-        t.key = od_keys + x * cap;
-        t.val = val0 + x * cap;
-        t.cap_log2 = cap_log2;
-        t.limit = cap - cap / 4 - (int)blockDim.x;
-        t.count = &slot[x].count;
-        return t;
-    };
-    for (int h = threadIdx.x; h < OD2_SLOTS * cap; h += blockDim.x) {
-        od_keys[h] = OD_EMPTY;
-        __stcg(val0 + h, 0.0);
-    }
-    const int64_t S = (int64_t)counters[C_STARTS];
-    const bool visit0 = 1.0f > wc32;
-    const double gg = gamma * gamma;
-    if (threadIdx.x < OD2_SLOTS) {
-        slot[threadIdx.x].word = od2_pack(OD2_ST_DOT, 0u, 0u);   // not open until loaded
-        slot[threadIdx.x].count = 0;
-        slot[threadIdx.x].posted = 0;
-        slot[threadIdx.x].dot_seq = 0ull;
-        slot[threadIdx.x].dot_next = 0ull;
-    }
-    __syncthreads();
-    // Loads the next start column into slot x (one thread; its table is empty).
-    auto load_start = [&](int x) {
-        Od2Slot& sl = slot[x];
-        const int64_t s = (int64_t)atomicAdd(&counters[C_NEXT], 1ull);
-        if (s >= S) {
-            __threadfence_block();
-            od2_set_state(sl, OD2_ST_DONE);
-            return;
-        }
-        const uint32_t k0 = (uint32_t)starts[s];
-        const uint2 od0 = nod[k0];
-        const int64_t Nk = nw[k0];
-        *(volatile unsigned int*)&sl.k0 = k0;
-        *(volatile unsigned int*)&sl.off0 = od0.x;
-        *(volatile unsigned int*)&sl.deg0 = od0.y;
-        *(volatile long long*)&sl.Nk = Nk;
-        *(volatile long long*)&sl.g0 = woff[k0];
-        *(volatile unsigned long long*)&sl.next_walk = 0ull;
-        *(volatile int*)&sl.gen = 0;
-        *(volatile int*)&sl.posted = 0;
-        *(volatile int*)&sl.count = 0;
-        if (visit0 && K >= 2) {
-            const OdTable t = table(x);
-            const int h = od_insert(t, od0.x);    // empty table: always succeeds
-            atomicAdd(&t.val[h], (double)Nk * (double)zeta[2]);
-        }
-        __threadfence_block();
-        od2_set_state(sl, OD2_ST_WALK);
-    };
-    // Clears slot y's table after its dot phase, then resumes or reloads it (one warp).
-    auto finish_dot = [&](int y) {
-        Od2Slot& sl = slot[y];
-        const OdTable t = table(y);
-        __threadfence_block();
-        for (int h = (int)(threadIdx.x & 31); h < cap; h += 32) {
-            if (t.key[h] != OD_EMPTY) {
-                t.key[h] = OD_EMPTY;
-                __stcg(t.val + h, 0.0);
-            }
-        }
-        __syncwarp();
-        __threadfence_block();
-        if ((threadIdx.x & 31) == 0) {
-            *(volatile int*)&sl.count = 0;
-            *(volatile int*)&sl.posted = 0;
-            if (*(volatile int*)&sl.final_) {
-                load_start(y);
-            } else {
-                od2_set_state(sl, OD2_ST_WALK);
-                __threadfence_block();
-                atomicAdd(&sl.gen, 1);
-            }
-        }
-        __syncwarp();
-    };
-    if (threadIdx.x < OD2_SLOTS) load_start(threadIdx.x);
-    __syncthreads();
-
-    const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    uint32_t steps = 0, walks = 0, flags = 0;
-    bool active = false, paused = false;
-    int x = (threadIdx.x >> 5) & 1, pgen = 0;
-    int64_t g = 0;
-    uint32_t off = 0, deg = 0;
-    int k = 0;
-    float W = 1.f;
-    uint4 u = make_uint4(0u, 0u, 0u, 0u);
-    uint32_t idle_iters = 0;
-    for (;;) {
-        bool progress = false;
-        // ---- the posted dot phases: one row per slot per iteration
-        for (int y = 0; y < OD2_SLOTS; ++y) {
-            Od2Slot& sl = slot[y];
-            int ready = 0;
-            if (lane == 0) ready = od2_state(od2_word(sl)) == OD2_ST_DOT && *(volatile int*)&sl.posted;
-            if (!__shfl_sync(FULL, ready, 0)) continue;
-            __threadfence_block();
-            unsigned long long rr = 0;
-            if (lane == 0) rr = atomicAdd(&sl.dot_next, 1ull);
-            rr = __shfl_sync(FULL, rr, 0);
-            __threadfence_block();
-            if ((rr >> OD2_ROW_BITS) != *(volatile unsigned long long*)&sl.dot_seq) continue;   // an earlier phase's
-            const unsigned long long r = rr & OD2_ROW_MASK;
-            const long long rows = *(volatile long long*)&sl.dot_rows;
-            if (rows == 0) {
-                // no rows to add (not expected: a start column has rows): just clear and go on
-                if (r == 0) finish_dot(y);
-                continue;
-            }
-            if (r >= (unsigned long long)rows) continue;
-            progress = true;
-            const OdTable t = table(y);
-            const int64_t pos = *(volatile long long*)&sl.dot_base + (int64_t)r;
-            const int32_t i = sub.ptr ? sub.row[pos] : col[pos];
-            double dot = 0.0;
-            for (int64_t q = rp[i] + lane; q < rp[i + 1]; q += 32) {
-                const double qv = od_get(t, __ldg(&ekey[q]));
-                if (__double_as_longlong(qv) != 0) dot += qv;   // exact zeros change no sum
-            }
-#pragma unroll
-            for (int d = 16; d > 0; d >>= 1) dot += __shfl_xor_sync(FULL, dot, d);
-            unsigned long long done = 0;
-            if (lane == 0) {
-                atomicAdd(&dacc[i], dot * (gg / (double)*(volatile long long*)&sl.Nk));
-                __threadfence_block();
-                done = atomicAdd(&sl.dot_done, 1ull);
-            }
-            done = __shfl_sync(FULL, done, 0);
-            if (done + 1 == (unsigned long long)rows) finish_dot(y);
-        }
-        // ---- paused walks go on once their slot's table is clear
-        if (paused && *(volatile int*)&slot[x].gen != pgen) {
-            __threadfence_block();
-            paused = false;
-        }
-        // ---- an idle lane takes a walk: from its slot first, else the other one
-        int trig = 0, tslot = 0;
-        for (int tries = 0; tries < OD2_SLOTS && !active && !trig; ++tries) {
-            const int y = (x + tries) % OD2_SLOTS;
-            Od2Slot& sl = slot[y];
-            const unsigned long long o = od2_word(sl);
-            if (od2_state(o) != OD2_ST_WALK || od2_paused(o) != 0 ||
-                *(volatile unsigned long long*)&sl.next_walk >= (unsigned long long)*(volatile long long*)&sl.Nk)
-                continue;
-            const unsigned long long prev = atomicAdd(&sl.word, 1ull);   // reserve: live + 1
-            if (od2_state(prev) == OD2_ST_WALK) {
-                const unsigned long long w = atomicAdd(&sl.next_walk, 1ull);
-                if (w < (unsigned long long)*(volatile long long*)&sl.Nk) {
-                    __threadfence_block();
-                    x = y;
-                    g = *(volatile long long*)&sl.g0 + (int64_t)w;
-                    off = *(volatile unsigned int*)&sl.off0;
-                    deg = *(volatile unsigned int*)&sl.deg0;
-                    k = 0;
-                    W = 1.f;
-                    active = true;
-                    progress = true;
-                    break;
-                }
-            }
-            trig = od2_release(sl, false);      // give the reservation back
-            tslot = y;
-        }
-        // ---- one step of every running walk
-        if (active && !paused) {
-            progress = true;
-            Od2Slot& sl = slot[x];
-            const OdTable t = table(x);
-            bool done = !(fabsf(W) > wc32);
-            if (!done && k >= 1) {
-                const int h = od_insert(t, off);
-                if (h < 0) {
-                    paused = true;
-                    pgen = *(volatile int*)&sl.gen;
-                    __threadfence_block();
-                    trig = od2_release(sl, true);
-                    tslot = x;
-                } else {
-                    atomicAdd(&t.val[h], (double)__fmul_rn(zeta[k + 2], W));
-                }
-            }
-            if (!done && !paused) {
-                if (k + 2 >= K || deg == 0) {
-                    done = true;
-                } else {
-                    uint32_t w0, w1;
-                    walk_words<false>(u, k, (uint32_t)g, (uint32_t)((uint64_t)g >> 32), req, key, w0, w1);
-                    const uint2 nx = load_od(eod + (int64_t)off + __umulhi(w0, deg), policy_evict_first());
-                    W = __fmul_rn(W, __ldg(rm + deg));
-                    off = nx.x;
-                    deg = nx.y;
-                    ++k;
-                    ++steps;
-                }
-            }
-            if (done) {
-                if (!isfinite(W)) flags |= 1u;
-                ++walks;
-                active = false;
-                __threadfence_block();
-                trig = od2_release(sl, false);
-                tslot = x;
-            }
-        }
-        if (trig) {
-            od2_post(slot[tslot], trig, rp, sub);
-            progress = true;
-        }
-        // ---- leave when no start is left and this warp holds no walk
-        int all_done = 1;
-        if (lane == 0)
-            for (int y = 0; y < OD2_SLOTS; ++y) all_done &= od2_state(od2_word(slot[y])) == OD2_ST_DONE;
-        all_done = __shfl_sync(FULL, all_done, 0);
-        if (all_done && !__any_sync(FULL, active)) break;
-        if (__any_sync(FULL, progress)) {
-            idle_iters = 0;
-        } else if (++idle_iters >= OD2_SPIN_LIMIT) {
-            flags |= 4u;
-            break;
         }
     }
     unsigned long long ws = steps, ww = walks;
@@ -1368,7 +925,7 @@ static mcf_status check_params(const mcf_graph* g, const mcf_params* p) {
     if (!(p->w_cutoff >= 0.0)) return fail(MCF_ERR_INVALID_ARG, "w_cutoff must be >= 0");
     if (p->precision != MCF_F64 && p->precision != MCF_F32W_F64ACC)
         return fail(MCF_ERR_INVALID_ARG, "unknown precision");
-    if (p->deterministic != 0) return fail(MCF_ERR_INVALID_ARG, "deterministic is reserved and must be 0");
+    if (p->deterministic != 0 && p->deterministic != 1) return fail(MCF_ERR_INVALID_ARG, "deterministic is 0 or 1");
     if (p->error_estimate != 0 && p->error_estimate != 1) return fail(MCF_ERR_INVALID_ARG, "error_estimate is 0 or 1");
     if (!(p->scale >= 0.0) || !isfinite(p->scale)) return fail(MCF_ERR_INVALID_ARG, "scale must be finite and >= 0");
     for (int k = 0; k < p->n_coeffs; ++k)
@@ -1480,12 +1037,12 @@ static mcf_status finish_stats(mcf_stats* stats, const unsigned long long* count
 
 template <bool F64, bool WEIGHTED>
 static void launch_action_walks(const mcf_graph* g, const Prep& P, uint32_t* chunk_s0, int K, double wc, uint2 key,
-                                uint32_t req, double* acc, double* acc2, cudaStream_t st) {
+                                uint32_t req, double* acc, double* acc2, cudaStream_t st, double* wvals = nullptr) {
     auto kern = walk_action_kernel<F64, WEIGHTED>;
     const int grid = persistent_grid(kern, 256, 0);
     ScopedL2Fetch fetch(L2_FETCH_BYTES);
     kern<<<grid, 256, 0, st>>>((const Rec<F64>*)P.rec, g->col_idx, g->went, P.starts, P.cof, P.soff, chunk_s0, P.zeta,
-                               K, wc, cutoff_f32(wc), key, req, WALK_GRAB, acc, acc2, P.counters);
+                               K, wc, cutoff_f32(wc), key, req, WALK_GRAB, acc, acc2, wvals, P.counters);
 }
 
 // Builds the graph's node_od / edge_od arrays on first use (binary, nnz < 2^32).
@@ -1548,11 +1105,42 @@ mcf_status ensure_edge_key(mcf_graph* g, cudaStream_t st) {
 }
 
 static void launch_tc_walks(const mcf_graph* g, const Prep& P, const float* rm, uint32_t* chunk_s0, int K, double wc,
-                            uint2 key, uint32_t req, double* acc, double* acc2, cudaStream_t st) {
+                            uint2 key, uint32_t req, double* acc, double* acc2, double* wvals, cudaStream_t st) {
     const int grid = persistent_grid(walk_tc_kernel, 256, 0);
     ScopedL2Fetch fetch(L2_FETCH_BYTES);
     walk_tc_kernel<<<grid, 256, 0, st>>>(g->node_od, g->edge_od, rm, P.starts, P.cof, P.soff, chunk_s0, P.zeta, K,
-                                         cutoff_f32(wc), key, req, WALK_GRAB, WALK_REFILL_MIN, acc, acc2, P.counters);
+                                         cutoff_f32(wc), key, req, WALK_GRAB, WALK_REFILL_MIN, acc, acc2, wvals,
+                                         P.counters);
+}
+
+// Deterministic mode: the sum (and sum of squares) of start s's walk values,
+// read in walk order with a fixed assignment to lanes and a fixed shuffle
+// tree (warp per start), so the same walks give bit-identical sums.
+__global__ void det_walk_sums(const unsigned long long* __restrict__ counters, const int32_t* __restrict__ starts,
+                              const int64_t* __restrict__ cof, const double* __restrict__ wvals,
+                              double* __restrict__ acc, double* __restrict__ acc2) {
+    MCF_KERNEL_ENTRY();
+    const int lane = threadIdx.x & 31;
+    const int64_t S = (int64_t)counters[C_STARTS];
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t s = warp; s < S; s += nwarps) {
+        double v = 0.0, v2 = 0.0;
+        for (int64_t w = cof[s] + lane; w < cof[s + 1]; w += 32) {
+            const double x = wvals[w];
+            v += x;
+            v2 += x * x;
+        }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            v += __shfl_xor_sync(0xffffffffu, v, d);
+            v2 += __shfl_xor_sync(0xffffffffu, v2, d);
+        }
+        if (lane == 0) {
+            acc[starts[s]] = v;
+            if (acc2) acc2[starts[s]] = v2;
+        }
+    }
 }
 
 static mcf_status solve_action(mcf_graph* g, const mcf_params* p, const double* v, double* y, mcf_stats* stats,
@@ -1651,6 +1239,9 @@ static mcf_status solve_action(mcf_graph* g, const mcf_params* p, const double* 
             }
             const uint2 key = philox_key(p->seed);
             const bool tc_path = ones && !f64 && !g->weighted && g->nnz < ((int64_t)1 << 32);
+            // deterministic mode: one float64 slot per walk, summed per start in walk order
+            double* wvals = nullptr;
+            if (p->deterministic) MCF_TRY(sc.get(&wvals, std::max<int64_t>(max_walks, 1)));
             if (tc_path) {
                 MCF_TRY(ensure_edge_od(g, st));
                 float* rm;
@@ -1658,16 +1249,22 @@ static mcf_status solve_action(mcf_graph* g, const mcf_params* p, const double* 
                 degree_table<<<grid_for(g->max_degree + 1, 256), 256, 0, st>>>(g->max_degree, gamma, rm);
                 const uint32_t rq = p->request_id;
                 const double wc = p->w_cutoff;
-                launch_tc_walks(g, P, rm, chunk_s0, K, wc, key, rq, acc, acc2, st);
+                launch_tc_walks(g, P, rm, chunk_s0, K, wc, key, rq, acc, acc2, wvals, st);
             } else if (f64 && g->weighted) {
-                launch_action_walks<true, true>(g, P, chunk_s0, K, p->w_cutoff, key, p->request_id, acc, acc2, st);
+                launch_action_walks<true, true>(g, P, chunk_s0, K, p->w_cutoff, key, p->request_id, acc, acc2, st, wvals);
             } else if (f64) {
-                launch_action_walks<true, false>(g, P, chunk_s0, K, p->w_cutoff, key, p->request_id, acc, acc2, st);
+                launch_action_walks<true, false>(g, P, chunk_s0, K, p->w_cutoff, key, p->request_id, acc, acc2, st,
+                                                 wvals);
             } else if (g->weighted) {
-                launch_action_walks<false, true>(g, P, chunk_s0, K, p->w_cutoff, key, p->request_id, acc, acc2, st);
+                launch_action_walks<false, true>(g, P, chunk_s0, K, p->w_cutoff, key, p->request_id, acc, acc2, st,
+                                                 wvals);
             } else {
-                launch_action_walks<false, false>(g, P, chunk_s0, K, p->w_cutoff, key, p->request_id, acc, acc2, st);
+                launch_action_walks<false, false>(g, P, chunk_s0, K, p->w_cutoff, key, p->request_id, acc, acc2, st,
+                                                  wvals);
             }
+            if (wvals)
+                det_walk_sums<<<grid_for((int64_t)n * 32, 256), 256, 0, st>>>(P.counters, P.starts, P.cof, wvals, acc,
+                                                                               acc2);
             if (stats) cudaEventRecord(e1, st);
         }
         finalize_q<<<grid_for(n, 256), 256, 0, st>>>(n, acc, P.nw);
@@ -1745,18 +1342,7 @@ static mcf_status launch_diag(const mcf_graph* g, const Prep& P, const SubList& 
 // start (64 .. 256); the key table holds about 16 visits per walk of a start,
 // between 2^10 and 2^DIAG_OD_CAP_LOG2 slots (4 bytes each in shared memory);
 // a start with more distinct visits adds and clears its partial row on the way.
-#ifndef MCF_DIAG_OD_CAP_LOG2
-#define MCF_DIAG_OD_CAP_LOG2 13
-#endif
-#ifndef MCF_DIAG_OD_MAX_THREADS
-#define MCF_DIAG_OD_MAX_THREADS 256
-#endif
-#ifndef MCF_DIAG_OD2
-#define MCF_DIAG_OD2 0
-#endif
-constexpr int DIAG_OD_CAP_LOG2 = MCF_DIAG_OD_CAP_LOG2;
-constexpr bool DIAG_OD2 = MCF_DIAG_OD2 != 0;
-constexpr int DIAG_OD_MAX_THREADS = MCF_DIAG_OD_MAX_THREADS;
+constexpr int DIAG_OD_CAP_LOG2 = 13;
 
 static mcf_status launch_diag_od(mcf_graph* g, const Prep& P, const SubList& sub, double gamma, int K, double wc,
                                  uint2 key, uint32_t req, int64_t nk_hint, double* dacc, Scratch& sc, cudaStream_t st) {
@@ -1765,32 +1351,12 @@ static mcf_status launch_diag_od(mcf_graph* g, const Prep& P, const SubList& sub
     float* rm;
     MCF_TRY(sc.get(&rm, (size_t)g->max_degree + 1));
     degree_table<<<grid_for(g->max_degree + 1, 256), 256, 0, st>>>(g->max_degree, gamma, rm);
-    int threads = DIAG_OD_MAX_THREADS;
+    int threads = 256;
     if (nk_hint > 0 && nk_hint <= 64) threads = 64;
-    else if (nk_hint > 0 && nk_hint <= 128) threads = std::min(128, threads);
+    else if (nk_hint > 0 && nk_hint <= 128) threads = 128;
     const int64_t want_slots = std::max<int64_t>(16 * std::max<int64_t>(nk_hint, 1), 4 * threads);
     int cap_log2 = 10;
     while (cap_log2 < DIAG_OD_CAP_LOG2 && ((int64_t)1 << cap_log2) < want_slots) ++cap_log2;
-    if (DIAG_OD2) {
-        // two start columns in flight per CTA, a table of 2^(cap_log2 - 1) slots each
-        const int c2 = std::max(10, cap_log2 - 1);
-        const size_t smem = (size_t)OD2_SLOTS * ((size_t)1 << c2) * sizeof(uint32_t);
-        MCF_CUDA_TRY(cudaFuncSetAttribute(walk_diag_od2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        const int grid = persistent_grid(walk_diag_od2_kernel, threads, smem);
-        double* qval;
-        MCF_TRY(sc.get(&qval, (size_t)grid * OD2_SLOTS << c2));
-        ScopedL2Fetch fetch(L2_FETCH_BYTES);
-        walk_diag_od2_kernel<<<grid, threads, smem, st>>>(g->row_ptr, g->col_idx, g->node_od, g->edge_od, g->edge_key,
-                                                          rm, P.starts, P.woff, P.nw, sub, gamma, P.zeta, K,
-                                                          cutoff_f32(wc), key, req, c2, qval, dacc, P.counters);
-        MCF_CUDA_TRY(cudaGetLastError());
-        // the kernel bounds its waits; a stall it reports (flag bit 2) is an error, not a result
-        unsigned long long fl = 0;
-        MCF_CUDA_TRY(cudaMemcpyAsync(&fl, &P.counters[C_FLAGS], sizeof(fl), cudaMemcpyDeviceToHost, st));
-        MCF_CUDA_TRY(cudaStreamSynchronize(st));
-        if (fl & 4ull) return fail(MCF_ERR_CUDA, "internal: the subgraph-centrality kernel stopped waiting (no progress)");
-        return MCF_OK;
-    }
     const size_t smem = ((size_t)1 << cap_log2) * sizeof(uint32_t);
     MCF_CUDA_TRY(cudaFuncSetAttribute(walk_diag_od_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = persistent_grid(walk_diag_od_kernel, threads, smem);
@@ -1855,6 +1421,8 @@ static mcf_status solve_diag(mcf_graph* g, const mcf_params* p, const int64_t* n
                              mcf_stats* stats) {
     set_error("");
     MCF_TRY(check_params(g, p));
+    if (p->deterministic)
+        return fail(MCF_ERR_UNSUPPORTED, "the deterministic mode covers RandFunmAction solves only");
     if (!d) return fail(MCF_ERR_INVALID_ARG, "d is NULL");
     if (nodes && n_nodes < 0) return fail(MCF_ERR_INVALID_ARG, "n_nodes must be >= 0");
     cudaStream_t st = (cudaStream_t)p->stream;
@@ -2122,6 +1690,8 @@ constexpr int64_t FULL_MAX_NODES = MCF_FULL_MAX_NODES;
 static mcf_status solve_full(mcf_graph* g, const mcf_params* p, double* F, mcf_stats* stats) {
     set_error("");
     MCF_TRY(check_params(g, p));
+    if (p->deterministic)
+        return fail(MCF_ERR_UNSUPPORTED, "the deterministic mode covers RandFunmAction solves only");
     if (!F) return fail(MCF_ERR_INVALID_ARG, "F is NULL");
     const int64_t n = g->n;
     if (n > FULL_MAX_NODES)
@@ -2276,6 +1846,8 @@ static mcf_status solve_mc_classic(mcf_graph* g, const mcf_params* p, const doub
     set_error("");
     MCF_TRY(check_params(g, p));
     if (!y) return fail(MCF_ERR_INVALID_ARG, "y is NULL");
+    if (p->deterministic)
+        return fail(MCF_ERR_UNSUPPORTED, "the deterministic mode covers RandFunmAction solves only");
     if (p->precision != MCF_F64) return fail(MCF_ERR_UNSUPPORTED, "the classical method runs in float64 only");
     if (p->walks_per_node < 1) return fail(MCF_ERR_INVALID_ARG, "walks_per_node (walks per entry) must be >= 1");
     if (nodes && n_nodes < 0) return fail(MCF_ERR_INVALID_ARG, "n_nodes must be >= 0");

@@ -66,7 +66,8 @@ class mcf_server_config(ctypes.Structure):
 
 class mcf_server_stats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("rejected", ctypes.c_int64),
-                ("batches", ctypes.c_int64), ("walk_steps", ctypes.c_int64), ("p50_ms", ctypes.c_double),
+                ("batches", ctypes.c_int64), ("cancelled", ctypes.c_int64), ("walk_steps", ctypes.c_int64),
+                ("p50_ms", ctypes.c_double),
                 ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
                 ("busy_s", ctypes.c_double), ("device_overlap_ms", ctypes.c_double),
                 ("max_concurrent_batches", ctypes.c_int64), ("plan_s", ctypes.c_double), ("run_s", ctypes.c_double)]
@@ -109,12 +110,14 @@ SIGNATURES = {
     "mcf_server_get_stats": ([_P, _P], ctypes.c_int),
     "mcf_server_destroy": ([_P], ctypes.c_int),
     "mcf_server_release": ([_P, ctypes.c_uint64], ctypes.c_int),
+    "mcf_server_cancel": ([_P, ctypes.c_uint64], ctypes.c_int),
     "mcf_query_footprint": ([_P, _P], ctypes.c_int),
     "mcf_batch_device_bytes": ([_P, _P], ctypes.c_int),
     "mcf_total_communicability_noalloc": ([_I64, _I64, _P, _P, _P, _P], ctypes.c_int),
     "mcf_gather_probe": ([_I64, _I64, _P, _P], ctypes.c_int),
     "mcf_second_moment_radius": ([_P, _D, _D, _I32, _P], ctypes.c_int),
     "mcf_kernel_launches": ([_P], ctypes.c_int),
+    "mcf_inject_allocation_failure": ([_I64], ctypes.c_int),
     "mcf_last_error": ([], ctypes.c_char_p),
     "mcf_version": ([], ctypes.c_char_p),
 }
@@ -212,11 +215,13 @@ def _stream_of(*arrays):
 
 
 def _params(coeffs, scale=0.0, n_walks=0, walks_per_node=0, w_cutoff=0.0, seed=0, request_id=0,
-            precision=MCF_F32W_F64ACC, stream=None, error_estimate=False, target_rel_err=0.0, max_walks=0):
+            precision=MCF_F32W_F64ACC, stream=None, error_estimate=False, target_rel_err=0.0, max_walks=0,
+            deterministic=False):
     c = np.ascontiguousarray(coeffs, dtype=np.float64)
     p = mcf_params(c.ctypes.data, len(c), float(scale), int(n_walks), int(walks_per_node), float(w_cutoff),
-                   int(seed) & 0xFFFFFFFFFFFFFFFF, int(request_id) & 0xFFFFFFFF, int(precision), 0,
-                   1 if error_estimate else 0, stream if stream else None, float(target_rel_err), int(max_walks))
+                   int(seed) & 0xFFFFFFFFFFFFFFFF, int(request_id) & 0xFFFFFFFF, int(precision),
+                   1 if deterministic else 0, 1 if error_estimate else 0, stream if stream else None,
+                   float(target_rel_err), int(max_walks))
     return p, c
 
 
@@ -396,7 +401,7 @@ def _query_struct(q):
     vp, kv = _ptr(q.get("v"), np.float64)
     npt, kn = _ptr(nodes, np.int64)
     pkw = {k: q[k] for k in ("scale", "n_walks", "walks_per_node", "w_cutoff", "seed", "request_id", "precision",
-                             "target_rel_err", "max_walks") if k in q}
+                             "target_rel_err", "max_walks", "deterministic") if k in q}
     p, kc = _params(q.get("coeffs", [1.0]), **pkw)
     st = mcf_query(g.handle, kind, int(q.get("katz_terms", 0)), float(q.get("katz_gamma", 0.0)), p, vp, npt,
                    int(0 if nodes is None else len(nodes)), op)
@@ -503,6 +508,11 @@ def mcf_server_wait(s: ServerHandle, ticket: int, timeout_s: float = -1.0, accep
     return out, lat.value
 
 
+def mcf_server_cancel(s: ServerHandle, ticket: int):
+    """Cancels a queued request (it completes with MCF_ERR_CANCELLED)."""
+    _check(load().mcf_server_cancel(s.handle, ctypes.c_uint64(ticket)))
+
+
 def mcf_server_release(s: ServerHandle, ticket: int):
     """Forgets a completed request."""
     _check(load().mcf_server_release(s.handle, ctypes.c_uint64(ticket)))
@@ -556,6 +566,11 @@ def mcf_kernel_launches() -> int:
     out = ctypes.c_uint64()
     _check(load().mcf_kernel_launches(ctypes.byref(out)))
     return int(out.value)
+
+
+def mcf_inject_allocation_failure(after: int):
+    """The next scratch allocation after ``after`` successful ones fails with MCF_ERR_OOM (< 0: off)."""
+    _check(load().mcf_inject_allocation_failure(int(after)))
 
 
 def mcf_last_error() -> str:

@@ -171,9 +171,9 @@ def test_subgraph_centrality_hashed_row_with_flushes(precision):
 
 @pytest.mark.timeout(600)
 def test_subgraph_centrality_subset_hashed_rows_neighbour_records():
-    """A node subset on a graph with >= 2^20 entries and n > 16384: hashed rows
-    Q_k, 16-byte neighbour records and the per-column lists of requested rows
-    together.  Nodes: the top hub, three of its neighbours, a low-degree node,
+    """A node subset on a graph with >= 2^20 entries and n > 16384: rows Q_k
+    keyed by row offset in a shared-memory table, 8-byte walk records and the
+    per-column lists of requested rows together.  Nodes: the top hub, three of its neighbours, a low-degree node,
     an isolated node if any, and a duplicate; only the columns adjacent to them
     are walked, and the dot phase of a hub column touches only the listed rows."""
     g = I.rmat(16, 16, seed=9)
