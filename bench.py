@@ -478,7 +478,9 @@ def run_serving(M, R, I, scales, n_requests, rate=200.0, seed=5, workers=6):
     total communicability, 30% Katz (gamma = 0.85 / max_i sum_k |a_ik|, the
     paper's setting), 20% subgraph centrality on 10^4 sampled nodes; walk
     budgets calibrated per graph and kind to 1e-3; p50/p99 latency from the
-    server's counters, device overlap of batches, errors on sampled graphs."""
+    server's counters, device overlap of batches, errors on sampled graphs;
+    the capacity of the server (all requests queued at once) against the
+    same requests solved one at a time."""
     t = time.time()
     pool = []
     c = exp_coeffs(30)
@@ -532,6 +534,29 @@ def run_serving(M, R, I, scales, n_requests, rate=200.0, seed=5, workers=6):
         M.mcf_server_release(srv, tk)
     st = M.mcf_server_get_stats(srv)
     srv.close()
+    # capacity, closed loop: the same requests all queued at once through the
+    # server, against the plain loop that solves them one at a time (each
+    # result read back to the host before the next request, as a client of
+    # the single-query calls does)
+    srv = M.mcf_server_create(hbm_budget_bytes=64 << 30, max_inflight=workers, max_batch=16, batch_window_ms=0.5)
+    t1 = time.perf_counter()
+    tickets = [M.mcf_server_submit(srv, q) for q in qs]
+    for tk in tickets:
+        M.mcf_server_wait(srv, tk)
+        M.mcf_server_release(srv, tk)
+    wall_served = time.perf_counter() - t1
+    srv.close()
+    for q in qs[:8]:
+        solve_single(M, q)
+    t1 = time.perf_counter()
+    for q in qs:
+        solve_single(M, q)
+    wall_single = time.perf_counter() - t1
+    capacity = {"served_solves_per_s": n_requests / wall_served,
+                "one_at_a_time_solves_per_s": n_requests / wall_single,
+                "speedup": wall_single / wall_served}
+    log(f"[bench] serving capacity: served {capacity['served_solves_per_s']:.1f}/s, one at a time "
+        f"{capacity['one_at_a_time_solves_per_s']:.1f}/s")
     # accuracy of sampled requests per kind: TC and Katz on graphs up to 2^22
     # nodes (whole vectors), SC on graphs up to 2^20 nodes (64 of the sampled nodes)
     errs = {"tc": [], "katz": [], "sc": []}
@@ -558,7 +583,7 @@ def run_serving(M, R, I, scales, n_requests, rate=200.0, seed=5, workers=6):
             "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"], "mean_ms": st["mean_ms"],
             "solves_per_s": st["completed"] / wall, "batches": st["batches"], "rejected": st["rejected"],
             "walk_steps_per_s": st["walk_steps"] / wall, "device_overlap_ms": st["device_overlap_ms"],
-            "max_concurrent_batches": st["max_concurrent_batches"], "wall_s": wall,
+            "max_concurrent_batches": st["max_concurrent_batches"], "wall_s": wall, "capacity": capacity,
             "worker_plan_s": st["plan_s"], "worker_run_s": st["run_s"],
             "max_rel_err_vs_fp64": {k: (max(e for _, e in v) if v else None) for k, v in errs.items()},
             "checked_graph_sizes": {k: sorted(n for n, _ in v) for k, v in errs.items()},

@@ -423,14 +423,12 @@ __global__ void __launch_bounds__(256) bwalk_diag_kernel(
     OdTable t;
     const int cap = 1 << cap_log2;
     t.key = od_keys;
+    t.filt = od_keys + cap;
     t.val = qval + (int64_t)blockIdx.x * cap;
     t.cap_log2 = cap_log2;
     t.limit = cap - cap / 4 - (int)blockDim.x;
     t.count = &count;
-    for (int h = threadIdx.x; h < cap; h += blockDim.x) {
-        od_keys[h] = OD_EMPTY;
-        __stcg(t.val + h, 0.0);
-    }
+    od_init(t);
     if (threadIdx.x == 0) count = 0;
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -531,7 +529,9 @@ __global__ void __launch_bounds__(256) bwalk_diag_kernel(
                 if (run) {
                     bool done = !(fabsf(W) > wc32);
                     if (!done && k >= 1) {
-                        const int h = od_insert(t, off);
+                        bool claimed;
+                        const int h = od_insert(t, off, claimed);
+                        od_count_claims(t, claimed);
                         if (h < 0) paused = true;
                         else atomicAdd(&t.val[h], (double)__fmul_rn(cq.zeta[k + 2], W));
                     }
@@ -720,10 +720,10 @@ static mcf_status balloc(mcf_batch* b, T** p, size_t count) {
 
 // Table size of the fused diag kernel for starts of about nk walks, as the
 // single-query kernel sizes it: about 16 visits per walk, 2^10 .. 2^13 slots
-// (4 bytes each in shared memory), each CTA with a region of as many float64
-// values in global memory.  Threads per CTA follow from it (64 for 2^10, 128
-// for 2^11, 256 above): a CTA serves one start at a time, so lanes beyond its
-// walks idle.  SC queries of a batch are grouped by this size, one launch per
+// (5 bytes each in shared memory: key and filter bits), each CTA with a
+// region of as many float64 values in global memory.  Threads per CTA follow
+// from it (64 for 2^10, 128 for 2^11, 256 above): a CTA serves one start at a
+// time, so lanes beyond its walks idle.  SC queries of a batch are grouped by this size, one launch per
 // group, so that a query with long starts does not shrink every CTA's
 // occupancy to its table.
 static int diag_cap_log2(int64_t nk) {
@@ -737,9 +737,9 @@ static int diag_cap_log2(int64_t nk) {
 static mcf_status diag_shape(int64_t nk, DiagShape* sh) {
     sh->cap_log2 = diag_cap_log2(nk);
     sh->threads = sh->cap_log2 == 10 ? 64 : (sh->cap_log2 == 11 ? 128 : 256);
-    sh->smem = ((size_t)1 << sh->cap_log2) * sizeof(uint32_t);
+    sh->smem = od_smem_bytes(sh->cap_log2);
     if (cudaFuncSetAttribute(bwalk_diag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(((size_t)1 << B_DIAG_CAP_LOG2) * sizeof(uint32_t))) != cudaSuccess) {
+                             (int)od_smem_bytes(B_DIAG_CAP_LOG2)) != cudaSuccess) {
         cudaGetLastError();
         return fail(MCF_ERR_CUDA, "diag kernel shared memory");
     }

@@ -415,21 +415,55 @@ mcf_status check_nodes_on_device(const int64_t* nodes_dev, int64_t m, int64_t n,
 // ---------------------------------------------------------------- RandFunmDiag rows keyed by row offset
 // Row Q_k of a symmetric binary graph keyed by the row offset of the visited
 // node (every visited node has degree >= 1, and such nodes have distinct row
-// offsets): keys in a shared-memory open-addressing table, float64 values in
-// a per-CTA region of global memory updated by L2 reductions.
+// offsets): keys in a shared-memory open-addressing table (linear probing),
+// float64 values in a per-CTA region of global memory updated by L2
+// reductions.  A one-hash bit filter beside the keys (8 bits per slot) holds
+// a bit for every key present: the dot phase looks up many absent keys, and
+// most of those end at the filter instead of walking a probe chain, which at
+// the table's fill limit averages several slots.
 constexpr uint32_t OD_EMPTY = 0xffffffffu;
 
 struct OdTable {
     uint32_t* key;     // shared: row offset of the node in each slot, OD_EMPTY when free
+    uint32_t* filt;    // shared: 2^cap_log2 / 4 words of filter bits
     double* val;       // global, per CTA
     int cap_log2;
     int limit;         // largest number of keys admitted
     int* count;        // shared
 };
 
-__device__ __forceinline__ int od_insert(const OdTable& t, uint32_t key) {
+// Shared memory of a table of 2^cap_log2 slots: keys, then filter words.
+__host__ __device__ constexpr size_t od_smem_bytes(int cap_log2) {
+    return ((size_t)1 << cap_log2) * sizeof(uint32_t) + ((size_t)1 << cap_log2);
+}
+
+__device__ __forceinline__ uint32_t od_fbit(const OdTable& t, uint32_t key) {
+    return (key * 0x2C1B3C6Du) >> (32 - (t.cap_log2 + 3));
+}
+
+__device__ __forceinline__ void od_mark(const OdTable& t, uint32_t key) {
+    const uint32_t f = od_fbit(t, key);
+    atomicOr(&t.filt[f >> 5], 1u << (f & 31u));
+}
+
+// Sets every key slot free and every filter bit to 0 (the table's first use).
+__device__ __forceinline__ void od_init(const OdTable& t) {
+    const int cap = 1 << t.cap_log2;
+    for (int h = threadIdx.x; h < cap; h += blockDim.x) {
+        t.key[h] = OD_EMPTY;
+        __stcg(t.val + h, 0.0);
+    }
+    for (int w = threadIdx.x; w < cap / 4; w += blockDim.x) t.filt[w] = 0u;
+}
+
+// Slot of key, inserted if absent and the table holds fewer than limit keys
+// (-1 otherwise).  claimed is set when this call took a new slot: the caller
+// adds the claims of its warp to *count in one atomic (count then lags by at
+// most one claim per thread, which the table's margin above limit absorbs).
+__device__ __forceinline__ int od_insert(const OdTable& t, uint32_t key, bool& claimed) {
     const uint32_t mask = (1u << t.cap_log2) - 1u;
     uint32_t h = (key * 0x9E3779B1u) >> (32 - t.cap_log2);
+    claimed = false;
     for (uint32_t probe = 0; probe <= mask; ++probe, h = (h + 1) & mask) {
         const uint32_t k = t.key[h];
         if (k == key) return (int)h;
@@ -437,13 +471,21 @@ __device__ __forceinline__ int od_insert(const OdTable& t, uint32_t key) {
             if (*(volatile int*)t.count >= t.limit) return -1;
             const uint32_t prev = atomicCAS(&t.key[h], OD_EMPTY, key);
             if (prev == OD_EMPTY) {
-                atomicAdd(t.count, 1);
+                claimed = true;
+                od_mark(t, key);
                 return (int)h;
             }
             if (prev == key) return (int)h;
         }
     }
     return -1;
+}
+
+// Adds the claims of the calling lanes (those executing together) to *count.
+__device__ __forceinline__ void od_count_claims(const OdTable& t, bool claimed) {
+    const unsigned am = __activemask();
+    const unsigned b = __ballot_sync(am, claimed);
+    if (b && (threadIdx.x & 31) == __ffs(b) - 1) atomicAdd(t.count, __popc(b));
 }
 
 // Inserts key regardless of the fill limit (the table keeps room for the
@@ -459,6 +501,7 @@ __device__ __forceinline__ int od_insert_always(const OdTable& t, uint32_t key) 
             const uint32_t prev = atomicCAS(&t.key[h], OD_EMPTY, key);
             if (prev == OD_EMPTY) {
                 atomicAdd(t.count, 1);
+                od_mark(t, key);
                 return (int)h;
             }
             if (prev == key) return (int)h;
@@ -468,6 +511,8 @@ __device__ __forceinline__ int od_insert_always(const OdTable& t, uint32_t key) 
 }
 
 __device__ __forceinline__ double od_get(const OdTable& t, uint32_t key) {
+    const uint32_t f = od_fbit(t, key);
+    if (!((t.filt[f >> 5] >> (f & 31u)) & 1u)) return 0.0;
     const uint32_t mask = (1u << t.cap_log2) - 1u;
     uint32_t h = (key * 0x9E3779B1u) >> (32 - t.cap_log2);
     for (uint32_t probe = 0; probe <= mask; ++probe, h = (h + 1) & mask) {
@@ -509,6 +554,7 @@ __device__ __forceinline__ void od_clear(const OdTable& t) {
             __stcg(t.val + h, 0.0);
         }
     }
+    for (int w = threadIdx.x; w < cap / 4; w += blockDim.x) t.filt[w] = 0u;
 }
 
 

@@ -722,14 +722,12 @@ __global__ void __launch_bounds__(256) walk_diag_od_kernel(
     OdTable t;
     const int cap = 1 << cap_log2;
     t.key = od_keys;
+    t.filt = od_keys + cap;
     t.val = qval + (int64_t)blockIdx.x * cap;
     t.cap_log2 = cap_log2;
     t.limit = cap - cap / 4 - (int)blockDim.x;
     t.count = &count;
-    for (int h = threadIdx.x; h < cap; h += blockDim.x) {
-        od_keys[h] = OD_EMPTY;
-        __stcg(t.val + h, 0.0);
-    }
+    od_init(t);
     if (threadIdx.x == 0) count = 0;
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -787,7 +785,9 @@ __global__ void __launch_bounds__(256) walk_diag_od_kernel(
                 if (run) {
                     bool done = !(fabsf(W) > wc32);
                     if (!done && k >= 1) {
-                        const int h = od_insert(t, off);
+                        bool claimed;
+                        const int h = od_insert(t, off, claimed);
+                        od_count_claims(t, claimed);
                         if (h < 0) paused = true;
                         else atomicAdd(&t.val[h], (double)__fmul_rn(zeta[k + 2], W));
                     }
@@ -1340,7 +1340,8 @@ static mcf_status launch_diag(const mcf_graph* g, const Prep& P, const SubList& 
 
 // Launch shape of walk_diag_od_kernel: threads per CTA follow the walks per
 // start (64 .. 256); the key table holds about 16 visits per walk of a start,
-// between 2^10 and 2^DIAG_OD_CAP_LOG2 slots (4 bytes each in shared memory);
+// between 2^10 and 2^DIAG_OD_CAP_LOG2 slots (5 bytes each in shared memory:
+// key and filter bits);
 // a start with more distinct visits adds and clears its partial row on the way.
 constexpr int DIAG_OD_CAP_LOG2 = 13;
 
@@ -1357,7 +1358,7 @@ static mcf_status launch_diag_od(mcf_graph* g, const Prep& P, const SubList& sub
     const int64_t want_slots = std::max<int64_t>(16 * std::max<int64_t>(nk_hint, 1), 4 * threads);
     int cap_log2 = 10;
     while (cap_log2 < DIAG_OD_CAP_LOG2 && ((int64_t)1 << cap_log2) < want_slots) ++cap_log2;
-    const size_t smem = ((size_t)1 << cap_log2) * sizeof(uint32_t);
+    const size_t smem = od_smem_bytes(cap_log2);
     MCF_CUDA_TRY(cudaFuncSetAttribute(walk_diag_od_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = persistent_grid(walk_diag_od_kernel, threads, smem);
     double* qval;
