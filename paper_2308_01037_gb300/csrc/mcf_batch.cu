@@ -409,7 +409,9 @@ struct CtaOdQuery {
     float zeta[MCF_MAX_COEFFS];
 };
 
-__global__ void __launch_bounds__(256) bwalk_diag_kernel(
+// MINB: as for walk_diag_od_kernel (2 for the 256-thread launches, else 0).
+template <int MINB>
+__global__ void __launch_bounds__(256, MINB) bwalk_diag_kernel(
     const BQuery* __restrict__ desc, const int64_t* __restrict__ qoff, int Q, const uint32_t* __restrict__ starts,
     const int64_t* __restrict__ soff, const int64_t* __restrict__ nw, const float* __restrict__ rm_all,
     const int64_t* __restrict__ rmoff, int q_lo, int q_hi, int cls, int cap_log2, double* __restrict__ qval,
@@ -738,12 +740,13 @@ static mcf_status diag_shape(int64_t nk, DiagShape* sh) {
     sh->cap_log2 = diag_cap_log2(nk);
     sh->threads = sh->cap_log2 == 10 ? 64 : (sh->cap_log2 == 11 ? 128 : 256);
     sh->smem = od_smem_bytes(sh->cap_log2);
-    if (cudaFuncSetAttribute(bwalk_diag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)od_smem_bytes(B_DIAG_CAP_LOG2)) != cudaSuccess) {
+    auto kern = sh->threads == 256 ? bwalk_diag_kernel<2> : bwalk_diag_kernel<0>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)od_smem_bytes(B_DIAG_CAP_LOG2)) !=
+        cudaSuccess) {
         cudaGetLastError();
         return fail(MCF_ERR_CUDA, "diag kernel shared memory");
     }
-    sh->grid = persistent_grid(bwalk_diag_kernel, sh->threads, sh->smem);
+    sh->grid = persistent_grid(kern, sh->threads, sh->smem);
     return MCF_OK;
 }
 
@@ -865,7 +868,8 @@ static mcf_status record(mcf_batch* b, cudaStream_t st) {
     if (Q > b->Q_tc) {
         for (size_t c = 0; c < b->diag.size(); ++c) {
             const DiagClass& dc = b->diag[c];
-            bwalk_diag_kernel<<<dc.sh.grid, dc.sh.threads, dc.sh.smem, st>>>(
+            auto kern = dc.sh.threads == 256 ? bwalk_diag_kernel<2> : bwalk_diag_kernel<0>;
+            kern<<<dc.sh.grid, dc.sh.threads, dc.sh.smem, st>>>(
                 b->desc, b->qoff, Q, b->starts, b->soff, b->nw, b->rm, b->rmoff, dc.q_lo, dc.q_hi, (int)c,
                 dc.sh.cap_log2, b->qval, b->acc, b->counters);
             MCF_CUDA_TRY(cudaGetLastError());
