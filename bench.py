@@ -61,7 +61,7 @@ WORKLOADS = {
 # reads a row offset pair 8 B + column index 4 B + r_l 4 B per transition;
 # subgraph centrality reads 12 B (no r_l) and reduces into the L2-resident row Q_k.
 ALGO_BYTES_PER_STEP = {"tc": 16, "sc": 12}
-KERNEL = {"tc": "walk_tc_kernel", "sc": "walk_diag_kernel"}
+KERNEL = {"tc": "walk_tc_kernel", "sc": "walk_diag_od_kernel"}
 # DRAM bytes (read + write) per walk step of walk_tc_kernel from one ncu
 # capture of the R-MAT scale 21 profiling case with the current kernel
 # (7.787e9 B over 264,240,439 steps of one launch); a launch of the larger
@@ -593,6 +593,47 @@ def run_serving(M, R, I, scales, n_requests, rate=200.0, seed=5, workers=6):
             "katz_gamma": "0.85 / max_i sum_k |a_ik| (Gershgorin, Section 4.5)"}
 
 
+def run_config1(M, I, reps=3):
+    """The plain method at the small size: Barabasi-Albert n = 1000, m = 3
+    (seed 0), A / lambda_max, exp truncated at K = 30, 1e5 walks per node,
+    float64 throughout; total communicability and subgraph centrality, time
+    per solve (CUDA events) and the relative l_inf error against dense
+    expm(A / lambda_max) (scipy, float64)."""
+    import torch
+    from scipy.linalg import expm
+
+    g = I.barabasi_albert(1000, 3, 0)
+    h = M.mcf_create_graph(g.n, g.row_ptr, g.col_idx)
+    lam = M.mcf_spectral_radius(h, tol=1e-12, max_iter=100000)
+    c = exp_coeffs(30)
+    A = np.zeros((g.n, g.n))
+    for i in range(g.n):
+        A[i, g.col_idx[g.row_ptr[i]:g.row_ptr[i + 1]]] = 1.0
+    E = expm(A / lam)
+    ref = {"tc": E.sum(axis=1), "sc": np.diag(E).copy()}
+    kw = dict(scale=1.0 / lam, walks_per_node=100_000, w_cutoff=0.0, seed=0, precision=M.MCF_F64)
+    out = torch.empty(g.n, dtype=torch.float64, device="cuda")
+    res = {"workload": "BA n=1000 m=3 seed 0, exp(A/lambda_max) truncated at K=30, 1e5 walks per node, float64",
+           "lambda_max": lam}
+    for kind, fn in (("tc", M.mcf_total_communicability), ("sc", M.mcf_subgraph_centrality)):
+        fn(h, c, out=out, request_id=1, **kw)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        steps = 0
+        for i in range(reps):
+            _, st = fn(h, c, out=out, request_id=2 + i, stats=True, **kw)
+            steps += st["walk_steps"]
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        y = out.cpu().numpy()
+        res[kind] = {"ms_per_solve": ms, "walk_steps_per_s": steps / reps / (ms / 1000.0),
+                     "rel_err_vs_dense_expm": float(np.abs(y - ref[kind]).max() / np.abs(ref[kind]).max())}
+    h.close()
+    return res
+
+
 def run_sc_config3(M, R, I, steps=2):
     """Subgraph centrality diag exp(A/lambda_max) of every node of the erased
     configuration model n = 2e6 (k^-2.5, mean degree 20), 2000 walks per node,
@@ -800,7 +841,7 @@ def main():
     ap.add_argument("--serve-scales", default="16-24")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--section", default="main",
-                    choices=["main", "funm_full", "mc_classic", "batched", "serving", "sc_config3"],
+                    choices=["main", "funm_full", "mc_classic", "batched", "serving", "sc_config3", "config1"],
                     help="run only that measurement (1 GPU) and print its JSON")
     ap.add_argument("--funm-n", type=int, default=16384, help="nodes of the dense RandFunm measurement")
     ap.add_argument("--ref-seconds", type=float, default=60.0,
@@ -823,6 +864,8 @@ def main():
             res = run_batched(M, R, I, args.batch_graphs, args.batch_log_n_max)
         elif args.section == "sc_config3":
             res = run_sc_config3(M, R, I)
+        elif args.section == "config1":
+            res = run_config1(M, I)
         else:
             lo, hi = (int(x) for x in args.serve_scales.split("-"))
             res = run_serving(M, R, I, list(range(lo, hi + 1)), args.serve_requests)
@@ -951,12 +994,15 @@ def main():
         # the library's own standard-error estimate of one solve (Section 3.5)
         _, st_se = solve(h, c, out=out, request_id=88, stats=True, error_estimate=True, **base)
         max_rel_se = st_se["max_rel_se"]
-    batched = serving = funm_full = mc_classic = sc3 = None
+    batched = serving = funm_full = mc_classic = sc3 = config1 = None
     if rank == 0 and world == 1 and not args.no_batch:
         from oracle import reference as R
         from paper_2308_01037_gb300 import inputs as I
 
         h.close()    # the sections below bring their own graphs
+        t = time.time()
+        config1 = run_config1(M, I)
+        log(f"[bench] section config1: {time.time() - t:.1f}s")
         t = time.time()
         sc3 = run_sc_config3(M, R, I)
         log(f"[bench] section sc_config3: {time.time() - t:.1f}s")
@@ -1005,7 +1051,8 @@ def main():
                          "frac_of_gather_ceiling": None if not gather else kernel_steps_per_s / gather},
             "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches,
             "cpu_baseline": cpu,
-            "subset": subset, "subgraph_centrality_config3": sc3, "batched": batched, "serving": serving,
+            "subset": subset, "config1": config1, "subgraph_centrality_config3": sc3, "batched": batched,
+            "serving": serving,
             "funm_full": funm_full,
             "mc_classic": mc_classic,
         }

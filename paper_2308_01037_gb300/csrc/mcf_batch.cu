@@ -216,19 +216,46 @@ __global__ void bq_mark(const BQuery* __restrict__ desc, int q0, int Q, uint8_t*
 // TC queries.  A warp serves one query at a time: before it starts on a chunk
 // of another query it lets its lanes finish their walks, then loads that
 // query's parameters into its shared slot.
-struct WarpQuery {
-    const uint2* nod;
+// The fields a walk step reads come first, in three 16-byte words that a
+// step loads with three vector loads (StepParams); the rest serve refills.
+struct __align__(16) WarpQuery {
     const uint2* eod;
     const float* rm;
-    int64_t walk_base;
-    int64_t walk_end;
-    int64_t node_off;
     uint2 key;
     uint32_t req;
     float wc32;
-    int32_t K;
     const float* zeta;   // float32 coefficients in global memory (L1-resident)
+    int32_t K;
+    int32_t pad;
+    const uint2* nod;
+    int64_t walk_base;
+    int64_t walk_end;
+    int64_t node_off;
 };
+
+struct StepParams {
+    const uint2* eod;
+    const float* rm;
+    uint2 key;
+    uint32_t req;
+    float wc32;
+    const float* zeta;
+    int32_t K;
+};
+
+__device__ __forceinline__ StepParams step_params(const WarpQuery& w) {
+    const uint4* v = reinterpret_cast<const uint4*>(&w);
+    const uint4 a = v[0], b = v[1], c = v[2];
+    StepParams p;
+    p.eod = reinterpret_cast<const uint2*>(((uint64_t)a.y << 32) | a.x);
+    p.rm = reinterpret_cast<const float*>(((uint64_t)a.w << 32) | a.z);
+    p.key = make_uint2(b.x, b.y);
+    p.req = b.z;
+    p.wc32 = __uint_as_float(b.w);
+    p.zeta = reinterpret_cast<const float*>(((uint64_t)c.y << 32) | c.x);
+    p.K = (int32_t)c.z;
+    return p;
+}
 
 template <int MINB>
 __global__ void __launch_bounds__(256, MINB) bwalk_tc_kernel(
@@ -261,6 +288,9 @@ __global__ void __launch_bounds__(256, MINB) bwalk_tc_kernel(
     uint32_t my_steps = 0, my_walks = 0, flags = 0;
     for (;;) {
         unsigned idle = __ballot_sync(FULL, !active);
+        // refill once at least WALK_REFILL_MIN lanes are idle (or all are), as
+        // the single-query kernel does: fewer refill passes for a few idle lanes
+        if (idle != FULL && __popc(idle) < WALK_REFILL_MIN) idle = 0u;
         while (idle && !exhausted) {
             if (p >= valid) {
                 if (!have_next) {
@@ -342,17 +372,18 @@ __global__ void __launch_bounds__(256, MINB) bwalk_tc_kernel(
             // go on (after the cutoff test): a read issued earlier is wasted
             // DRAM work at every walk's end, and the kernel is bound by the
             // rate of random DRAM reads.
-            const bool last = k + 2 >= Wq.K || deg == 0;
-            done = !(fabsf(W) > Wq.wc32);
+            const StepParams P = step_params(Wq);
+            const bool last = k + 2 >= P.K || deg == 0;
+            done = !(fabsf(W) > P.wc32);
             if (!done) {
-                const float t = __ldg(Wq.rm + deg);
-                a32.add(__fmul_rn(__fmul_rn(__ldg(Wq.zeta + k + 2), W), t));
+                const float t = __ldg(P.rm + deg);
+                a32.add(__fmul_rn(__fmul_rn(__ldg(P.zeta + k + 2), W), t));
                 if (last) {
                     done = true;
                 } else {
                     uint32_t w0, w1;
-                    walk_words<false>(u, k, (uint32_t)g, (uint32_t)((uint64_t)g >> 32), Wq.req, Wq.key, w0, w1);
-                    const uint2 nx = load_od(Wq.eod + (int64_t)off + __umulhi(w0, deg), policy_evict_first());
+                    walk_words<false>(u, k, (uint32_t)g, (uint32_t)((uint64_t)g >> 32), P.req, P.key, w0, w1);
+                    const uint2 nx = load_od(P.eod + (int64_t)off + __umulhi(w0, deg), policy_evict_first());
                     W = __fmul_rn(W, t);
                     off = nx.x;
                     deg = nx.y;
