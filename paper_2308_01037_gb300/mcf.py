@@ -291,12 +291,32 @@ def mcf_gershgorin(g: GraphHandle) -> float:
 
 
 def _output(out, m, like):
+    """The caller's output, else a new one: on the device of a CUDA ``like``,
+    otherwise host memory (page-locked when CUDA is present, see _host_output)."""
     if out is not None:
         return out
     if like is not None and _is_torch(like) and like.is_cuda:
         import torch
 
         return torch.empty(max(m, 0), dtype=torch.float64, device=like.device)
+    return _host_output(m)
+
+
+def _host_output(m):
+    """A float64 host array for a result the library writes in full.  With CUDA
+    present it lives in page-locked memory from torch's caching host allocator
+    (a numpy view, which keeps the block alive): the library's device-to-host
+    copy into it is a plain DMA, while a copy into pageable memory is staged by
+    the driver, serialises with other threads' pageable copies and, into a
+    fresh np.zeros array, first faults in every page (measured on the request
+    server with six workers: 370 against 200 solves/s)."""
+    try:
+        import torch
+
+        if torch.cuda.is_available():
+            return torch.empty(max(m, 0), dtype=torch.float64, pin_memory=True).numpy()
+    except (ImportError, RuntimeError):
+        pass
     return np.zeros(max(m, 0), dtype=np.float64)
 
 
