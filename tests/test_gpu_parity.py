@@ -87,6 +87,24 @@ def test_action_general_vector_device_buffers(rmat12):
     assert_parity(y, ref["y"])
 
 
+def test_default_host_outputs_are_page_locked(rmat12):
+    """Without an ``out``, host results come back in page-locked memory (the
+    library's device-to-host copy is then a plain DMA), as numpy arrays equal
+    to the device-output result of the same walks."""
+    g, h, gam = rmat12
+    c = R.exp_coeffs(20)
+    kw = dict(scale=gam, n_walks=50000, seed=3, precision=M.MCF_F32W_F64ACC)
+    y = M.mcf_total_communicability(h, c, **kw)
+    assert isinstance(y, np.ndarray) and torch.from_numpy(y).is_pinned()
+    yd = M.mcf_total_communicability(h, c, out=torch.empty(g.n, dtype=torch.float64, device="cuda"), **kw)
+    assert_parity(y, yd.cpu().numpy())
+    b = M.mcf_batch_create([dict(graph=h, kind=M.MCF_QUERY_TOTAL_COMMUNICABILITY, coeffs=c, **kw)])
+    (yb,) = M.mcf_batch_run(b)
+    b.close()
+    assert torch.from_numpy(yb).is_pinned()
+    assert_parity(yb, yd.cpu().numpy())
+
+
 def test_katz_explicit_terms(ba1000):
     g, h, gam = ba1000
     gk = 0.85 * gam
