@@ -205,9 +205,10 @@ __global__ void bq_mark(const BQuery* __restrict__ desc, int q0, int Q, uint8_t*
     MCF_KERNEL_ENTRY();
     const BQuery& d = desc[q0 + blockIdx.y];
     if (!d.subset) return;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < d.n_out; t += (int64_t)gridDim.x * blockDim.x) {
+    // one CTA per requested node, its threads over the node's row
+    for (int64_t t = blockIdx.x; t < d.n_out; t += gridDim.x) {
         const int64_t i = d.nodes[t];
-        for (int64_t p = d.rp[i]; p < d.rp[i + 1]; ++p) need[d.node_off + d.col[p]] = 1;
+        for (int64_t p = d.rp[i] + threadIdx.x; p < d.rp[i + 1]; p += blockDim.x) need[d.node_off + d.col[p]] = 1;
     }
 }
 
@@ -870,7 +871,7 @@ static mcf_status record(mcf_batch* b, cudaStream_t st) {
     if (b->NT == 0) return MCF_OK;
     const int Q = b->Q;
     if (Q > b->Q_tc)
-        bq_mark<<<dim3(64, Q - b->Q_tc), 256, 0, st>>>(b->desc, b->Q_tc, Q, b->need - b->NT_tc);
+        bq_mark<<<dim3(1024, Q - b->Q_tc), 256, 0, st>>>(b->desc, b->Q_tc, Q, b->need - b->NT_tc);
     bq_colnorm<<<dim3(B_RED_BLOCKS, Q), B_RED_THREADS, 0, st>>>(b->desc, b->colnorm, b->part);
     bq_sum<<<Q, B_RED_THREADS, 0, st>>>(b->part, B_RED_BLOCKS, b->tot);
     bq_alloc<<<grid_for(b->NT, 256), 256, 0, st>>>(b->desc, b->qoff, Q, b->NT, b->colnorm, b->tot,

@@ -533,12 +533,36 @@ __device__ __forceinline__ void od_apply(const OdTable& t, uint32_t k0, int64_t 
     const int64_t* lp = sub.ptr ? sub.ptr : rp;
     const int32_t* lrow = sub.ptr ? sub.row : col;
     const double scale = (gamma * gamma) / (double)Nk;
+    const int cap = 1 << t.cap_log2;
+    const int64_t long_row = 8 * (int64_t)cap + 32 * (int64_t)*t.count;
     for (int64_t p = lp[k0] + wid; p < lp[k0 + 1]; p += nwarp) {
         const int32_t i = lrow[p];
+        const int64_t rb = rp[i], re = rp[i + 1];
         double dot = 0.0;
-        for (int64_t q = rp[i] + lane; q < rp[i + 1]; q += 32) {
-            const double qv = od_get(t, __ldg(&ekey[q]));
-            if (__double_as_longlong(qv) != 0) dot += qv;   // exact zeros change no sum
+        if (re - rb > long_row) {
+            // a row much longer than the table (a hub): look each key of the
+            // table up in the row instead.  ekey is strictly increasing within
+            // a row (row offsets of distinct neighbours, all of degree >= 1),
+            // so a binary search finds it; the terms are the same as below.
+            for (int h = lane; h < cap; h += 32) {
+                const uint32_t key = t.key[h];
+                if (key == OD_EMPTY) continue;
+                int64_t lo = rb, hi = re;
+                while (lo < hi) {
+                    const int64_t mid = (lo + hi) >> 1;
+                    if (__ldg(&ekey[mid]) < key) lo = mid + 1;
+                    else hi = mid;
+                }
+                if (lo < re && __ldg(&ekey[lo]) == key) {
+                    const double qv = __ldcg(t.val + h);
+                    if (__double_as_longlong(qv) != 0) dot += qv;
+                }
+            }
+        } else {
+            for (int64_t q = rb + lane; q < re; q += 32) {
+                const double qv = od_get(t, __ldg(&ekey[q]));
+                if (__double_as_longlong(qv) != 0) dot += qv;   // exact zeros change no sum
+            }
         }
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, d);

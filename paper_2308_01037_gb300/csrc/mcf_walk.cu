@@ -863,13 +863,17 @@ __global__ void sub_claim(int64_t m, const int64_t* __restrict__ nodes, long lon
         atomicCAS((unsigned long long*)&first[nodes[t]], ~0ull, (unsigned long long)t);
 }
 
+// sub_count, sub_fill and mark_nodes give one CTA to each requested node and
+// let its threads share the node's row: a sampled hub (10^5 entries and more
+// on R-MAT graphs) would otherwise hold one thread for its whole row.
 __global__ void sub_count(int64_t m, const int64_t* __restrict__ nodes, const long long* __restrict__ first,
                           const int64_t* __restrict__ rp, const int32_t* __restrict__ col, int64_t* __restrict__ cnt) {
     MCF_KERNEL_ENTRY();
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t t = blockIdx.x; t < m; t += gridDim.x) {
         const int64_t i = nodes[t];
         if (first[i] != t) continue;
-        for (int64_t p = rp[i]; p < rp[i + 1]; ++p) atomicAdd((unsigned long long*)&cnt[col[p]], 1ull);
+        for (int64_t p = rp[i] + threadIdx.x; p < rp[i + 1]; p += blockDim.x)
+            atomicAdd((unsigned long long*)&cnt[col[p]], 1ull);
     }
 }
 
@@ -878,10 +882,10 @@ __global__ void sub_fill(int64_t m, const int64_t* __restrict__ nodes, const lon
                          const int64_t* __restrict__ ptr, int64_t* __restrict__ fill, int32_t* __restrict__ row,
                          float* __restrict__ sval) {
     MCF_KERNEL_ENTRY();
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t t = blockIdx.x; t < m; t += gridDim.x) {
         const int64_t i = nodes[t];
         if (first[i] != t) continue;
-        for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+        for (int64_t p = rp[i] + threadIdx.x; p < rp[i + 1]; p += blockDim.x) {
             const int32_t k = col[p];
             const int64_t pos = ptr[k] + (int64_t)atomicAdd((unsigned long long*)&fill[k], 1ull);
             row[pos] = (int32_t)i;
@@ -894,9 +898,9 @@ __global__ void sub_fill(int64_t m, const int64_t* __restrict__ nodes, const lon
 __global__ void mark_nodes(int64_t m, const int64_t* __restrict__ nodes, const int64_t* __restrict__ rp,
                            const int32_t* __restrict__ col, uint8_t* __restrict__ need) {
     MCF_KERNEL_ENTRY();
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t t = blockIdx.x; t < m; t += gridDim.x) {
         const int64_t i = nodes[t];
-        for (int64_t p = rp[i]; p < rp[i + 1]; ++p) need[col[p]] = 1;
+        for (int64_t p = rp[i] + threadIdx.x; p < rp[i + 1]; p += blockDim.x) need[col[p]] = 1;
     }
 }
 
@@ -1205,7 +1209,7 @@ static mcf_status solve_action(mcf_graph* g, const mcf_params* p, const double* 
         }
         MCF_TRY(sc.get(&need, n));
         MCF_CUDA_TRY(cudaMemsetAsync(need, 0, n, st));
-        mark_nodes<<<grid_for(m, 256), 256, 0, st>>>(m, nodes_dev, g->row_ptr, g->col_idx, need);
+        mark_nodes<<<grid_for(m * 256, 256), 256, 0, st>>>(m, nodes_dev, g->row_ptr, g->col_idx, need);
     }
     Prep P;
     MCF_TRY(prepare(g, p, gamma, v_dev, need, sc, P, st));
@@ -1412,7 +1416,7 @@ mcf_status build_subset_lists(const mcf_graph* g, const int64_t* nodes_dev, int6
     MCF_CUDA_TRY(cudaMemsetAsync(first, 0xff, n * sizeof(long long), st));
     MCF_CUDA_TRY(cudaMemsetAsync(cnt, 0, n * sizeof(int64_t), st));
     sub_claim<<<grid_for(m, 256), 256, 0, st>>>(m, nodes_dev, first);
-    sub_count<<<grid_for(m, 256), 256, 0, st>>>(m, nodes_dev, first, g->row_ptr, g->col_idx, cnt);
+    sub_count<<<grid_for(m * 256, 256), 256, 0, st>>>(m, nodes_dev, first, g->row_ptr, g->col_idx, cnt);
     MCF_TRY(scan_i64(cnt, ptr, n, ptr + n, stmp, sbytes, st));
     int64_t pairs = 0;
     MCF_CUDA_TRY(cudaMemcpyAsync(&pairs, ptr + n, sizeof(pairs), cudaMemcpyDeviceToHost, st));
@@ -1420,8 +1424,8 @@ mcf_status build_subset_lists(const mcf_graph* g, const int64_t* nodes_dev, int6
     MCF_TRY(alloc(&rowv, std::max<int64_t>(pairs, 1) * sizeof(int32_t)));
     if (g->values) MCF_TRY(alloc(&svalv, std::max<int64_t>(pairs, 1) * sizeof(float)));
     MCF_CUDA_TRY(cudaMemsetAsync(cnt, 0, n * sizeof(int64_t), st));
-    sub_fill<<<grid_for(m, 256), 256, 0, st>>>(m, nodes_dev, first, g->row_ptr, g->col_idx, g->values, ptr, cnt,
-                                               (int32_t*)rowv, (float*)svalv);
+    sub_fill<<<grid_for(m * 256, 256), 256, 0, st>>>(m, nodes_dev, first, g->row_ptr, g->col_idx, g->values, ptr,
+                                                     cnt, (int32_t*)rowv, (float*)svalv);
     MCF_CUDA_TRY(cudaGetLastError());
     *out = SubList{ptr, (const int32_t*)rowv, (const float*)svalv};
     return MCF_OK;
@@ -1475,7 +1479,7 @@ static mcf_status solve_diag(mcf_graph* g, const mcf_params* p, const int64_t* n
     }
     SubList sub{nullptr, nullptr, nullptr};
     if (nodes_dev) {
-        mark_nodes<<<grid_for(m, 256), 256, 0, st>>>(m, nodes_dev, g->row_ptr, g->col_idx, need);
+        mark_nodes<<<grid_for(m * 256, 256), 256, 0, st>>>(m, nodes_dev, g->row_ptr, g->col_idx, need);
         // per-column lists of the requested rows (Section 3.3: only the
         // columns k with a_ik != 0 for a requested i, and of each only those i)
         MCF_TRY(build_subset_lists(g, nodes_dev, m, st, [&](void** q, size_t bytes) {

@@ -217,6 +217,31 @@ def test_subgraph_centrality_subset_hashed_rows_neighbour_records():
     assert_parity(d2.cpu().numpy(), ref["d"])
 
 
+@pytest.mark.timeout(600)
+def test_subgraph_centrality_hub_rows_longer_than_the_table():
+    """A hub joined to all of 20,000 nodes of a random graph (n > 16384: rows
+    keyed by row offset): a row far longer than a start's table takes the
+    path that looks the table's keys up in the row.  Full solve and a node
+    subset holding the hub (twice), against the oracle."""
+    rng = np.random.default_rng(21)
+    n = 20001
+    a, b = rng.integers(1, n, size=60000), rng.integers(1, n, size=60000)
+    e = np.concatenate([np.stack([np.zeros(n - 1, dtype=np.int64), np.arange(1, n)], 1),
+                        np.stack([a[a != b], b[a != b]], 1)])
+    e = np.unique(np.sort(e, axis=1), axis=0)
+    g = I.from_edges(n, e, "star+er")
+    assert g.degree[0] == n - 1
+    gam = 1.0 / R.lambda_max(g)
+    h = upload(g)
+    c = R.exp_coeffs(30)
+    kw = dict(scale=gam, walks_per_node=4, w_cutoff=1e-6, seed=13, precision=M.MCF_F32W_F64ACC)
+    ref = E.diag(g, c, gamma=gam, walks_per_node=4, w_cutoff=1e-6, seed=13, precision=1)
+    assert_parity(M.mcf_subgraph_centrality(h, c, **kw), ref["d"])
+    nodes = np.array([0, 1, 2, 500, 0], dtype=np.int64)
+    refs = E.diag(g, c, gamma=gam, walks_per_node=4, w_cutoff=1e-6, seed=13, precision=1, nodes=nodes)
+    assert_parity(M.mcf_subgraph_centrality(h, c, nodes=nodes, **kw), refs["d"])
+
+
 def test_subgraph_centrality_subset_weighted_signed():
     """The per-column lists carry the entries a_ik of a weighted, signed A."""
     g = I.barabasi_albert(400, 3, 5)
