@@ -857,7 +857,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched, serving, dense RandFunm and classical-method measurements")
     ap.add_argument("--batch-graphs", type=int, default=256)
     ap.add_argument("--batch-log-n-max", type=float, default=6.0)
-    ap.add_argument("--serve-scales", default="16-24")
+    ap.add_argument("--serve-scales", default="16-26")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--section", default="main",
                     choices=["main", "funm_full", "mc_classic", "batched", "serving", "sc_config3", "config1"],

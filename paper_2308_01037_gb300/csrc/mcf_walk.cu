@@ -466,20 +466,62 @@ __global__ void finalize_q(int64_t n, double* __restrict__ acc, const int64_t* _
         acc[i] = nw[i] > 0 ? acc[i] / (double)nw[i] : 0.0;
 }
 
-// y = zeta_0 v + zeta_1 r + A' q (Algorithm 3, last step); a warp covers 32
-// consecutive rows (warp_row_sums).
-__global__ void action_epilogue(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-                                const float* __restrict__ val, double gamma, double z0, double z1,
-                                const double* __restrict__ v, const double* __restrict__ r,
-                                const double* __restrict__ q, double* __restrict__ y) {
+// y = zeta_0 v + zeta_1 r + A' q (Algorithm 3, last step).  A CTA takes
+// EPI_ROWS consecutive rows, whose entries are contiguous in the CSR arrays,
+// and streams them through shared memory EPI_CHUNK at a time: the threads
+// load the chunk's entries at a stride of the CTA (coalesced column reads,
+// one gather of q per entry), then every row adds up its part of the chunk:
+// a row of at most 32 entries by its own thread, in entry order, a longer
+// row by its warp.  A thread never sums a long row alone, so the power-law
+// rows of a warp do not leave the other lanes idle for the longest one.
+// Launched with EPI_ROWS threads.
+constexpr int EPI_ROWS = 256;
+constexpr int EPI_CHUNK = 2048;
+__global__ void __launch_bounds__(EPI_ROWS) action_epilogue(int64_t n, const int64_t* __restrict__ rp,
+                                                            const int32_t* __restrict__ col,
+                                                            const float* __restrict__ val, double gamma, double z0,
+                                                            double z1, const double* __restrict__ v,
+                                                            const double* __restrict__ r,
+                                                            const double* __restrict__ q, double* __restrict__ y) {
     MCF_KERNEL_ENTRY();
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t base = warp * 32; base < n; base += nwarps * 32) {
-        const double s = warp_row_sums<32>(base, n, rp, col, val, q);
-        const int64_t row = base + lane;
-        if (row < n) y[row] = z0 * (v ? v[row] : 1.0) + z1 * r[row] + gamma * s;
+    __shared__ double prod[EPI_CHUNK];
+    __shared__ int64_t off[EPI_ROWS + 1];
+    const unsigned FULL = 0xffffffffu;
+    const int tid = threadIdx.x, lane = tid & 31;
+    for (int64_t r0 = (int64_t)blockIdx.x * EPI_ROWS; r0 < n; r0 += (int64_t)gridDim.x * EPI_ROWS) {
+        const int nr = (int)min((int64_t)EPI_ROWS, n - r0);
+        for (int t = tid; t <= nr; t += EPI_ROWS) off[t] = rp[r0 + t];
+        __syncthreads();
+        const int64_t E0 = off[0], E1 = off[nr];
+        const int64_t rb = tid < nr ? off[tid] : 0, re = tid < nr ? off[tid + 1] : 0;
+        const bool is_long = re - rb > 32;
+        double s = 0.0;
+        for (int64_t c0 = E0; c0 < E1; c0 += EPI_CHUNK) {
+            const int64_t c1 = min(c0 + (int64_t)EPI_CHUNK, E1);
+#pragma unroll 4
+            for (int64_t e = c0 + tid; e < c1; e += EPI_ROWS)
+                prod[e - c0] = (val ? (double)val[e] : 1.0) * __ldg(&q[col[e]]);
+            __syncthreads();
+            if (!is_long)
+                for (int64_t p = max(rb, c0); p < min(re, c1); ++p) s += prod[p - c0];
+            unsigned longs = __ballot_sync(FULL, is_long && rb < c1 && re > c0);
+            while (longs) {
+                const int t = __ffs(longs) - 1;
+                longs &= longs - 1;
+                const int64_t a = max(__shfl_sync(FULL, rb, t), c0), b = min(__shfl_sync(FULL, re, t), c1);
+                double part = 0.0;
+                for (int64_t p = a + lane; p < b; p += 32) part += prod[p - c0];
+#pragma unroll
+                for (int d = 16; d > 0; d >>= 1) part += __shfl_xor_sync(FULL, part, d);
+                if (lane == t) s += part;
+            }
+            __syncthreads();
+        }
+        if (tid < nr) {
+            const int64_t row = r0 + tid;
+            y[row] = z0 * (v ? v[row] : 1.0) + z1 * r[row] + gamma * s;
+        }
+        __syncthreads();   // off[] is rewritten for the next rows
     }
 }
 
@@ -1286,8 +1328,8 @@ static mcf_status solve_action(mcf_graph* g, const mcf_params* p, const double* 
             action_epilogue_nodes<<<grid_for(m, 256), 256, 0, st>>>(m, nodes_dev, g->row_ptr, g->col_idx, g->values,
                                                                     gamma, z0, z1, v_dev, P.r, acc, y_dev);
         else
-            action_epilogue<<<grid_for(n, 256), 256, 0, st>>>(n, g->row_ptr, g->col_idx, g->values, gamma, z0, z1,
-                                                              v_dev, P.r, acc, y_dev);
+            action_epilogue<<<grid_for(n, EPI_ROWS), EPI_ROWS, 0, st>>>(n, g->row_ptr, g->col_idx, g->values, gamma,
+                                                                        z0, z1, v_dev, P.r, acc, y_dev);
         MCF_CUDA_TRY(cudaGetLastError());
     }
     unsigned long long* se_max = nullptr;
@@ -2124,7 +2166,8 @@ static mcf_status solve_tc_noalloc(int64_t n, int64_t nnz, const int64_t* row_pt
     }
     finalize_q<<<grid_for(n, 256), 256, 0, st>>>(n, acc, P.nw);
     const double z0 = p->coeffs[0], z1 = K >= 1 ? p->coeffs[1] : 0.0;
-    action_epilogue<<<grid_for(n, 256), 256, 0, st>>>(n, row_ptr, col_idx, nullptr, gamma, z0, z1, nullptr, P.r, acc, y);
+    action_epilogue<<<grid_for(n, EPI_ROWS), EPI_ROWS, 0, st>>>(n, row_ptr, col_idx, nullptr, gamma, z0, z1, nullptr,
+                                                                P.r, acc, y);
     MCF_CUDA_TRY(cudaGetLastError());
     return MCF_OK;
 }
