@@ -441,7 +441,8 @@ struct CtaOdQuery {
     float zeta[MCF_MAX_COEFFS];
 };
 
-// MINB: as for walk_diag_od_kernel (2 for the 256-thread launches, else 0).
+// MINB: as for walk_diag_od_kernel (4 for the 256-thread launches, which
+// ptxas then fits in 64 registers: four CTAs per SM; else 0).
 template <int MINB>
 __global__ void __launch_bounds__(256, MINB) bwalk_diag_kernel(
     const BQuery* __restrict__ desc, const int64_t* __restrict__ qoff, int Q, const uint32_t* __restrict__ starts,
@@ -639,6 +640,37 @@ __global__ void bq_finalize(int64_t NT_tc, double* __restrict__ acc, const int64
 // One warp per 32-entry output block of any query: TC rows
 // y_i = zeta_0 + zeta_1 gamma deg_i + gamma sum_j q_j, SC entries
 // d = zeta_0 + zeta_1 gamma a_ii + sum_k a'_ik <Q_k, C'_i>.
+// y = zeta_0 1 + zeta_1 r + A' q for the TC/Katz queries (global nodes
+// [0, NT_tc)): a CTA takes EPI_ROWS consecutive global nodes at a time and
+// sums the rows of each query they span with tile_row_sums.  Launched with
+// EPI_ROWS threads.
+__global__ void __launch_bounds__(EPI_ROWS) bq_epilogue_tc(const BQuery* __restrict__ desc,
+                                                           const int64_t* __restrict__ qoff, int Q_tc, int64_t NT_tc,
+                                                           const double* __restrict__ acc) {
+    MCF_KERNEL_ENTRY();
+    __shared__ double prod[EPI_CHUNK];
+    __shared__ int64_t off[EPI_ROWS + 1];
+    for (int64_t g0 = (int64_t)blockIdx.x * EPI_ROWS; g0 < NT_tc; g0 += (int64_t)gridDim.x * EPI_ROWS) {
+        const int64_t g1 = min(g0 + (int64_t)EPI_ROWS, NT_tc);
+        int q = find_le(qoff, Q_tc, g0);
+        for (int64_t u = g0; u < g1;) {
+            while (qoff[q + 1] <= u) ++q;   // queries of no nodes
+            const BQuery& d = desc[q];
+            const int64_t r0 = u - d.node_off;
+            const int nr = (int)(min(g1, qoff[q + 1]) - u);
+            const double s = tile_row_sums(r0, nr, d.rp, d.col, nullptr, acc + d.node_off, prod, off);
+            if ((int)threadIdx.x < nr) {
+                const int64_t row = r0 + threadIdx.x;
+                const double r = __dmul_rn(d.gamma, (double)(off[threadIdx.x + 1] - off[threadIdx.x]));
+                d.out[row] = d.z0 + d.z1 * r + d.gamma * s;
+            }
+            __syncthreads();   // off[] is rewritten for the next rows
+            u += nr;
+        }
+    }
+}
+
+// The subgraph-centrality outputs of a batch, 32 per warp.
 __global__ void bq_epilogue(const BQuery* __restrict__ desc, const int64_t* __restrict__ boff, int Q,
                             int64_t n_blocks, const double* __restrict__ acc) {
     MCF_KERNEL_ENTRY();
@@ -650,12 +682,7 @@ __global__ void bq_epilogue(const BQuery* __restrict__ desc, const int64_t* __re
         const BQuery& d = desc[q];
         const int64_t base = (b - d.blk_off) * 32;
         if (d.kind == 0) {
-            const double s = warp_row_sums<32>(base, d.n, d.rp, d.col, nullptr, acc + d.node_off);
-            const int64_t row = base + lane;
-            if (row < d.n) {
-                const double r = __dmul_rn(d.gamma, (double)(d.rp[row + 1] - d.rp[row]));
-                d.out[row] = d.z0 + d.z1 * r + d.gamma * s;
-            }
+            continue;   // bq_epilogue_tc
         } else {
             const int64_t t = base + lane;
             if (t < d.n_out) {
@@ -772,7 +799,7 @@ static mcf_status diag_shape(int64_t nk, DiagShape* sh) {
     sh->cap_log2 = diag_cap_log2(nk);
     sh->threads = sh->cap_log2 == 10 ? 64 : (sh->cap_log2 == 11 ? 128 : 256);
     sh->smem = od_smem_bytes(sh->cap_log2);
-    auto kern = sh->threads == 256 ? bwalk_diag_kernel<2> : bwalk_diag_kernel<0>;
+    auto kern = sh->threads == 256 ? bwalk_diag_kernel<4> : bwalk_diag_kernel<0>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)od_smem_bytes(B_DIAG_CAP_LOG2)) !=
         cudaSuccess) {
         cudaGetLastError();
@@ -900,14 +927,19 @@ static mcf_status record(mcf_batch* b, cudaStream_t st) {
     if (Q > b->Q_tc) {
         for (size_t c = 0; c < b->diag.size(); ++c) {
             const DiagClass& dc = b->diag[c];
-            auto kern = dc.sh.threads == 256 ? bwalk_diag_kernel<2> : bwalk_diag_kernel<0>;
+            auto kern = dc.sh.threads == 256 ? bwalk_diag_kernel<4> : bwalk_diag_kernel<0>;
             kern<<<dc.sh.grid, dc.sh.threads, dc.sh.smem, st>>>(
                 b->desc, b->qoff, Q, b->starts, b->soff, b->nw, b->rm, b->rmoff, dc.q_lo, dc.q_hi, (int)c,
                 dc.sh.cap_log2, b->qval, b->acc, b->counters);
             MCF_CUDA_TRY(cudaGetLastError());
         }
     }
-    bq_epilogue<<<grid_for(b->n_blocks * 32, 256), 256, 0, st>>>(b->desc, b->boff, Q, b->n_blocks, b->acc);
+    if (b->NT_tc > 0) {
+        bq_epilogue_tc<<<grid_for(b->NT_tc, EPI_ROWS), EPI_ROWS, 0, st>>>(b->desc, b->qoff, b->Q_tc, b->NT_tc, b->acc);
+        MCF_CUDA_TRY(cudaGetLastError());
+    }
+    if (Q > b->Q_tc)
+        bq_epilogue<<<grid_for(b->n_blocks * 32, 256), 256, 0, st>>>(b->desc, b->boff, Q, b->n_blocks, b->acc);
     MCF_CUDA_TRY(cudaGetLastError());
     return MCF_OK;
 }

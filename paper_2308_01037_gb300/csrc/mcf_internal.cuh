@@ -129,6 +129,54 @@ __device__ __forceinline__ double warp_row_sums(int64_t base, int64_t n, const i
     return s;
 }
 
+// sum_j a_ij x[j] for the nr <= EPI_ROWS consecutive rows r0 .. r0+nr-1 of a
+// CSR matrix, by a CTA of EPI_ROWS threads (all of them must call it): the
+// rows' entries are contiguous, so the CTA streams them through shared
+// memory EPI_CHUNK at a time (coalesced column reads, one gather of x per
+// entry), then each row adds up its part of the chunk, a row of at most 32
+// entries by its own thread in entry order and a longer row by its warp; no
+// thread sums a long row alone.  prod holds EPI_CHUNK doubles and off
+// EPI_ROWS + 1 offsets (shared).  Returns the sum of row r0 + threadIdx.x
+// (0 beyond nr).
+constexpr int EPI_ROWS = 256;
+constexpr int EPI_CHUNK = 2048;
+__device__ __forceinline__ double tile_row_sums(int64_t r0, int nr, const int64_t* __restrict__ rp,
+                                                const int32_t* __restrict__ col, const float* __restrict__ val,
+                                                const double* __restrict__ x, double* prod, int64_t* off) {
+    const unsigned FULL = 0xffffffffu;
+    const int tid = threadIdx.x, lane = tid & 31;
+    for (int t = tid; t <= nr; t += EPI_ROWS) off[t] = rp[r0 + t];
+    __syncthreads();
+    const int64_t E0 = off[0], E1 = off[nr];
+    const int64_t rb = tid < nr ? off[tid] : 0, re = tid < nr ? off[tid + 1] : 0;
+    const bool is_long = re - rb > 32;
+    double s = 0.0;
+    for (int64_t c0 = E0; c0 < E1; c0 += EPI_CHUNK) {
+        const int64_t c1 = c0 + EPI_CHUNK < E1 ? c0 + EPI_CHUNK : E1;
+#pragma unroll 4
+        for (int64_t e = c0 + tid; e < c1; e += EPI_ROWS) prod[e - c0] = (val ? (double)val[e] : 1.0) * __ldg(&x[col[e]]);
+        __syncthreads();
+        if (!is_long) {
+            const int64_t a = rb > c0 ? rb : c0, b = re < c1 ? re : c1;
+            for (int64_t p = a; p < b; ++p) s += prod[p - c0];
+        }
+        unsigned longs = __ballot_sync(FULL, is_long && rb < c1 && re > c0);
+        while (longs) {
+            const int t = __ffs(longs) - 1;
+            longs &= longs - 1;
+            const int64_t lb = __shfl_sync(FULL, rb, t), le = __shfl_sync(FULL, re, t);
+            const int64_t a = lb > c0 ? lb : c0, b = le < c1 ? le : c1;
+            double part = 0.0;
+            for (int64_t p = a + lane; p < b; p += 32) part += prod[p - c0];
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) part += __shfl_xor_sync(FULL, part, d);
+            if (lane == t) s += part;
+        }
+        __syncthreads();
+    }
+    return s;
+}
+
 // Row sums for 32 listed rows: lane t owns row rows[base + t] (t < m).
 template <int SHORT>
 __device__ __forceinline__ double warp_listed_row_sums(int64_t base, int64_t m, const int64_t* __restrict__ rows,

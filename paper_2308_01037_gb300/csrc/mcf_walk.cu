@@ -466,17 +466,9 @@ __global__ void finalize_q(int64_t n, double* __restrict__ acc, const int64_t* _
         acc[i] = nw[i] > 0 ? acc[i] / (double)nw[i] : 0.0;
 }
 
-// y = zeta_0 v + zeta_1 r + A' q (Algorithm 3, last step).  A CTA takes
-// EPI_ROWS consecutive rows, whose entries are contiguous in the CSR arrays,
-// and streams them through shared memory EPI_CHUNK at a time: the threads
-// load the chunk's entries at a stride of the CTA (coalesced column reads,
-// one gather of q per entry), then every row adds up its part of the chunk:
-// a row of at most 32 entries by its own thread, in entry order, a longer
-// row by its warp.  A thread never sums a long row alone, so the power-law
-// rows of a warp do not leave the other lanes idle for the longest one.
-// Launched with EPI_ROWS threads.
-constexpr int EPI_ROWS = 256;
-constexpr int EPI_CHUNK = 2048;
+// y = zeta_0 v + zeta_1 r + A' q (Algorithm 3, last step): a CTA takes
+// EPI_ROWS consecutive rows at a time (tile_row_sums).  Launched with
+// EPI_ROWS threads.
 __global__ void __launch_bounds__(EPI_ROWS) action_epilogue(int64_t n, const int64_t* __restrict__ rp,
                                                             const int32_t* __restrict__ col,
                                                             const float* __restrict__ val, double gamma, double z0,
@@ -486,39 +478,11 @@ __global__ void __launch_bounds__(EPI_ROWS) action_epilogue(int64_t n, const int
     MCF_KERNEL_ENTRY();
     __shared__ double prod[EPI_CHUNK];
     __shared__ int64_t off[EPI_ROWS + 1];
-    const unsigned FULL = 0xffffffffu;
-    const int tid = threadIdx.x, lane = tid & 31;
     for (int64_t r0 = (int64_t)blockIdx.x * EPI_ROWS; r0 < n; r0 += (int64_t)gridDim.x * EPI_ROWS) {
         const int nr = (int)min((int64_t)EPI_ROWS, n - r0);
-        for (int t = tid; t <= nr; t += EPI_ROWS) off[t] = rp[r0 + t];
-        __syncthreads();
-        const int64_t E0 = off[0], E1 = off[nr];
-        const int64_t rb = tid < nr ? off[tid] : 0, re = tid < nr ? off[tid + 1] : 0;
-        const bool is_long = re - rb > 32;
-        double s = 0.0;
-        for (int64_t c0 = E0; c0 < E1; c0 += EPI_CHUNK) {
-            const int64_t c1 = min(c0 + (int64_t)EPI_CHUNK, E1);
-#pragma unroll 4
-            for (int64_t e = c0 + tid; e < c1; e += EPI_ROWS)
-                prod[e - c0] = (val ? (double)val[e] : 1.0) * __ldg(&q[col[e]]);
-            __syncthreads();
-            if (!is_long)
-                for (int64_t p = max(rb, c0); p < min(re, c1); ++p) s += prod[p - c0];
-            unsigned longs = __ballot_sync(FULL, is_long && rb < c1 && re > c0);
-            while (longs) {
-                const int t = __ffs(longs) - 1;
-                longs &= longs - 1;
-                const int64_t a = max(__shfl_sync(FULL, rb, t), c0), b = min(__shfl_sync(FULL, re, t), c1);
-                double part = 0.0;
-                for (int64_t p = a + lane; p < b; p += 32) part += prod[p - c0];
-#pragma unroll
-                for (int d = 16; d > 0; d >>= 1) part += __shfl_xor_sync(FULL, part, d);
-                if (lane == t) s += part;
-            }
-            __syncthreads();
-        }
-        if (tid < nr) {
-            const int64_t row = r0 + tid;
+        const double s = tile_row_sums(r0, nr, rp, col, val, q, prod, off);
+        if ((int)threadIdx.x < nr) {
+            const int64_t row = r0 + threadIdx.x;
             y[row] = z0 * (v ? v[row] : 1.0) + z1 * r[row] + gamma * s;
         }
         __syncthreads();   // off[] is rewritten for the next rows
@@ -748,12 +712,14 @@ __global__ void __launch_bounds__(256) walk_diag_kernel(
 // (weight 1 at k) are added once as N_k * zeta_2.
 //
 // MINB is the launch-bounds occupancy hint: 0 (none) for the 64- and
-// 128-thread launches, 2 for the 256-thread launch of long starts.  With the
-// hint ptxas schedules the walk loop with about 63 registers instead of 47
+// 128-thread launches, 3 for the 256-thread launch of long starts.  With a
+// hint ptxas schedules the walk loop with about 60 registers instead of 47
 // (four CTAs per SM instead of five), which measured 1441 against 1625 ms per
 // solve at 2000 walks per start on the configuration model n = 2e6, while the
 // 128-thread launch of 100 walks per start runs faster without it (97 against
-// 116 ms).
+// 116 ms).  The hint must keep the kernel within 64 registers: at 67 (a hint
+// of 2 once the hub-row path of the dot phase was added) only three CTAs fit
+// on an SM and the same solve took 1854 ms.
 
 template <int MINB>
 __global__ void __launch_bounds__(256, MINB) walk_diag_od_kernel(
@@ -1414,7 +1380,7 @@ static mcf_status launch_diag_od(mcf_graph* g, const Prep& P, const SubList& sub
     int cap_log2 = 10;
     while (cap_log2 < DIAG_OD_CAP_LOG2 && ((int64_t)1 << cap_log2) < want_slots) ++cap_log2;
     const size_t smem = od_smem_bytes(cap_log2);
-    auto kern = threads == 256 ? walk_diag_od_kernel<2> : walk_diag_od_kernel<0>;
+    auto kern = threads == 256 ? walk_diag_od_kernel<3> : walk_diag_od_kernel<0>;   // <= 64 registers
     MCF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = persistent_grid(kern, threads, smem);
     double* qval;
