@@ -153,8 +153,15 @@ __device__ __forceinline__ double tile_row_sums(int64_t r0, int nr, const int64_
     double s = 0.0;
     for (int64_t c0 = E0; c0 < E1; c0 += EPI_CHUNK) {
         const int64_t c1 = c0 + EPI_CHUNK < E1 ? c0 + EPI_CHUNK : E1;
+        // the float64 pipe of this part, not memory, bounds the loop: a binary
+        // A stores x itself (no multiply by 1), leaving one add per entry
+        if (val) {
 #pragma unroll 4
-        for (int64_t e = c0 + tid; e < c1; e += EPI_ROWS) prod[e - c0] = (val ? (double)val[e] : 1.0) * __ldg(&x[col[e]]);
+            for (int64_t e = c0 + tid; e < c1; e += EPI_ROWS) prod[e - c0] = (double)val[e] * __ldg(&x[col[e]]);
+        } else {
+#pragma unroll 4
+            for (int64_t e = c0 + tid; e < c1; e += EPI_ROWS) prod[e - c0] = __ldg(&x[col[e]]);
+        }
         __syncthreads();
         if (!is_long) {
             const int64_t a = rb > c0 ? rb : c0, b = re < c1 ? re : c1;
