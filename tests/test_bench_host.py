@@ -77,3 +77,32 @@ def test_reference_arm_other_ranks_exit_without_work():
     out = subprocess.run(cmd, capture_output=True, text=True, timeout=120, cwd=ROOT, env=env)
     assert out.returncode == 0, out.stderr[-2000:]
     assert not [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+
+
+def test_bench_runs_the_oracle_only_in_its_baseline_and_reference_legs():
+    """Every import of oracle/ in bench.py sits in the CPU-baseline functions or
+    the reference arm; the accuracy figures use bench's own float64 series,
+    which equal the oracle's on a small graph."""
+    import ast
+
+    tree = ast.parse(open(os.path.join(ROOT, "bench.py")).read())
+    allowed = {"cpu_baseline", "cpu_baseline_all_cores", "_oracle_worker_init", "_oracle_worker_task", "run_reference"}
+    found = []
+    for fn in ast.walk(tree):
+        if isinstance(fn, ast.FunctionDef):
+            for node in ast.walk(fn):
+                if isinstance(node, (ast.Import, ast.ImportFrom)):
+                    mod = node.module if isinstance(node, ast.ImportFrom) else node.names[0].name
+                    if mod and mod.split(".")[0] == "oracle":
+                        found.append(fn.name)
+    top = [n for n in tree.body if isinstance(n, (ast.Import, ast.ImportFrom))
+           and ((n.module if isinstance(n, ast.ImportFrom) else n.names[0].name) or "").split(".")[0] == "oracle"]
+    assert not top and found and set(found) <= allowed, found
+    g = I.rmat(9, 8, seed=2)
+    c = bench.exp_coeffs(20)
+    lam = R.lambda_max(g)
+    np.testing.assert_allclose(bench.F64Ref.series_action(g, c, 1.0 / lam), R.series_action(g, c, 1.0 / lam),
+                               rtol=1e-14)
+    nodes = np.array([0, 3, 100])
+    np.testing.assert_allclose(bench.F64Ref.series_diag(g, c, nodes, 1.0 / lam),
+                               R.series_diag(g, c, nodes, 1.0 / lam), rtol=1e-14)
