@@ -25,7 +25,7 @@ def lib():
     return M.load()
 
 
-def test_header_declares_the_survey_boundary():
+def test_header_declares_the_core_entry_points():
     names = declared_entry_points()
     for required in ("mcf_create_graph", "mcf_destroy_graph", "mcf_spectral_radius", "mcf_action",
                      "mcf_total_communicability", "mcf_subgraph_centrality", "mcf_katz", "mcf_last_error"):
